@@ -1,0 +1,347 @@
+"""Convolution in the oracle: the plain definition, the slot layout, and the
+homomorphic layer of Sec. 3.1 (padded convolution + Walsh-Hadamard output
+packing) with the rotations of Sec. 2.3 hoisted.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Readings of the paper (also listed in the design doc):
+  * Layout (Sec. 2.4 pads the input; Sec. 3.1 packs c_n channels per
+    ciphertext).  A slot row (N/2 slots) holds whole zero-padded halo
+    tiles ("blocks") of (T_h + 2P) x (T_w + 2P) slots, row-major with width
+    W_b = T_w + 2P.  Tap (dy, dx) is then a left rotation by dy*W_b + dx.
+    With c_n = 2, row 0 of input ciphertext j carries channel 2j and row 1
+    channel 2j+1; with c_n = 1 both rows carry channel j for different tiles.
+  * Hadamard scalars (Eq. 1) are used without the 1/2: s0 = v0 + v1,
+    s1 = v0 - v1, so the output decrypts to 2k * conv (k from Sec. 3.2.1).
+  * Output-channel alignment (Sec. 3.1 rotates partial sums) is applied on
+    the input side: the row swap is composed with every tap rotation
+    (diagonal d = 1), which gives the same slots.
+  * Stride S > 1 computes the stride-1 result on tiles whose origins are
+    multiples of S and keeps every S-th position at decode.
+  * Channel counts are padded with zero channels to a multiple of c_n.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import bfv
+from .params import Params
+
+
+def conv_plain(act: np.ndarray, weights: np.ndarray, stride: int, pad: int, depthwise: bool, t: int) -> np.ndarray:
+    """The definition the layer must reproduce: cross-correlation, no bias,
+    zero padding, out[i][o][y][x] = sum_{c,dy,dx} w[o][c][dy][dx] *
+    in[i][c][y*S + dy - P][x*S + dx - P], reduced mod t into [0, t)."""
+    I, C, H, W = act.shape
+    O, Cw, kh, kw = weights.shape
+    Ho = (H + 2 * pad - kh) // stride + 1
+    Wo = (W + 2 * pad - kw) // stride + 1
+    x = np.zeros((I, C, H + 2 * pad, W + 2 * pad), dtype=np.int64)
+    x[:, :, pad:pad + H, pad:pad + W] = act
+    out = np.zeros((I, O, Ho, Wo), dtype=np.int64)
+    for dy in range(kh):
+        for dx in range(kw):
+            win = x[:, :, dy:dy + stride * (Ho - 1) + 1:stride, dx:dx + stride * (Wo - 1) + 1:stride]
+            if depthwise:
+                out += win * weights[:, 0, dy, dx].reshape(1, O, 1, 1)
+            else:
+                out += np.einsum("icyx,oc->ioyx", win, weights[:, :, dy, dx])
+            out %= t
+    return out % t
+
+
+@dataclass
+class Layout:
+    N: int
+    C_in: int
+    C_out: int
+    H: int
+    W: int
+    kh: int
+    stride: int
+    depthwise: bool
+    n_images: int
+    c_n: int
+    P: int = 0
+    T_h: int = 0
+    T_w: int = 0
+
+    def __post_init__(self):
+        if self.kh % 2 != 1:
+            raise ValueError("odd square kernels only")
+        if self.depthwise and self.C_in != self.C_out:
+            raise ValueError("depthwise needs C_in == C_out")
+        self.P = (self.kh - 1) // 2
+        self.T_h, self.T_w = choose_tile(self.N // 2, self.H, self.W, self.P, self.stride)
+
+    # geometry -------------------------------------------------------------
+    @property
+    def W_b(self):
+        return self.T_w + 2 * self.P
+
+    @property
+    def block_slots(self):
+        return (self.T_h + 2 * self.P) * self.W_b
+
+    @property
+    def blocks_per_row(self):
+        return (self.N // 2) // self.block_slots
+
+    @property
+    def n_ty(self):
+        return -(-self.H // self.T_h)
+
+    @property
+    def n_tx(self):
+        return -(-self.W // self.T_w)
+
+    @property
+    def units(self):
+        return self.n_images * self.n_ty * self.n_tx
+
+    @property
+    def units_per_ct(self):
+        """blocks of distinct tiles per ciphertext: one row's worth (c_n = 2) or both rows (c_n = 1)"""
+        return self.blocks_per_row * (2 if self.c_n == 1 else 1)
+
+    @property
+    def row_units(self):
+        return -(-self.units // self.units_per_ct)
+
+    @property
+    def in_groups(self):
+        return -(-self.C_in // self.c_n)
+
+    @property
+    def out_groups(self):
+        return -(-self.C_out // self.c_n)
+
+    @property
+    def n_ct_in(self):
+        return self.row_units * self.in_groups
+
+    @property
+    def n_ct_out(self):
+        return self.row_units * self.out_groups
+
+    @property
+    def Ho(self):
+        return (self.H - 1) // self.stride + 1
+
+    @property
+    def Wo(self):
+        return (self.W - 1) // self.stride + 1
+
+    def taps(self):
+        """(dy, dx) offsets, row-major over the kernel window."""
+        return [(dy, dx) for dy in range(-self.P, self.P + 1) for dx in range(-self.P, self.P + 1)]
+
+    # slot placement -------------------------------------------------------
+    def slot_of(self, u_local: int, yl: int, xl: int) -> tuple[int, int]:
+        """(row, slot index within the row) of block-local position (yl, xl)
+        of the u_local-th tile held by a ciphertext."""
+        B = self.blocks_per_row
+        row, b = (0, u_local) if self.c_n == 2 else (u_local // B, u_local % B)
+        return row, b * self.block_slots + yl * self.W_b + xl
+
+    def unit_coords(self, unit: int) -> tuple[int, int, int]:
+        img, rest = divmod(unit, self.n_ty * self.n_tx)
+        ty, tx = divmod(rest, self.n_tx)
+        return img, ty, tx
+
+
+def choose_tile(half: int, H: int, W: int, P: int, S: int) -> tuple[int, int]:
+    """Interior tile size (T_h, T_w) whose padded block fits one slot row.
+    Whole image if it fits; else full-width strips of a multiple of S rows;
+    else square-ish tiles with sides a multiple of S."""
+    if (H + 2 * P) * (W + 2 * P) <= half:
+        return H, W
+    if (W + 2 * P) * (S + 2 * P) <= half:
+        Th = ((half // (W + 2 * P) - 2 * P) // S) * S
+        return min(Th, H), W
+    Tw = S
+    while Tw + S <= W and (Tw + S + 2 * P) ** 2 <= half:
+        Tw += S
+    Th = ((half // (Tw + 2 * P) - 2 * P) // S) * S
+    if Th < S or (Tw + 2 * P) * (S + 2 * P) > half:
+        raise ValueError("kernel too large for the ring degree")
+    return min(Th, H), Tw
+
+
+def pack_slots(lay: Layout, act: np.ndarray) -> np.ndarray:
+    """Input activations [I][C_in][H][W] -> slot vectors [n_ct_in][N]."""
+    N, half, P = lay.N, lay.N // 2, lay.P
+    out = np.zeros((lay.n_ct_in, N), dtype=np.int64)
+    for unit in range(lay.units):
+        ru, u_local = divmod(unit, lay.units_per_ct)
+        img, ty, tx = lay.unit_coords(unit)
+        for j in range(lay.in_groups):
+            ct = ru * lay.in_groups + j
+            for yl in range(lay.T_h + 2 * P):
+                Y = ty * lay.T_h + yl - P
+                if Y < 0 or Y >= lay.H:
+                    continue
+                for xl in range(lay.W_b):
+                    X = tx * lay.T_w + xl - P
+                    if X < 0 or X >= lay.W:
+                        continue
+                    row, pos = lay.slot_of(u_local, yl, xl)
+                    if lay.c_n == 2:
+                        for r in range(2):
+                            c = 2 * j + r
+                            if c < lay.C_in:
+                                out[ct, r * half + pos] = act[img, c, Y, X]
+                    else:
+                        out[ct, row * half + pos] = act[img, j, Y, X]
+    return out
+
+
+def unpack_slots(lay: Layout, slots: np.ndarray) -> np.ndarray:
+    """Output slot vectors [n_ct_out][N] -> [I][C_out][Ho][Wo] (valid positions only)."""
+    half, P, S = lay.N // 2, lay.P, lay.stride
+    out = np.zeros((lay.n_images, lay.C_out, lay.Ho, lay.Wo), dtype=np.int64)
+    for unit in range(lay.units):
+        ru, u_local = divmod(unit, lay.units_per_ct)
+        img, ty, tx = lay.unit_coords(unit)
+        for g in range(lay.out_groups):
+            ct = ru * lay.out_groups + g
+            for yl in range(P, P + lay.T_h):
+                Y = ty * lay.T_h + yl - P
+                if Y >= lay.H or Y % S:
+                    continue
+                for xl in range(P, P + lay.T_w):
+                    X = tx * lay.T_w + xl - P
+                    if X >= lay.W or X % S:
+                        continue
+                    row, pos = lay.slot_of(u_local, yl, xl)
+                    if lay.c_n == 2:
+                        for r in range(2):
+                            c = 2 * g + r
+                            if c < lay.C_out:
+                                out[img, c, Y // S, X // S] = slots[ct, r * half + pos]
+                    else:
+                        out[img, g, Y // S, X // S] = slots[ct, row * half + pos]
+    return out
+
+
+# ---------------------------------------------------------------- keys used
+def rotation_plan(P: Params, lay: Layout):
+    """List of (tap index, d, Galois element) for every rotated copy of an
+    input ciphertext; Galois element 1 is the identity (no key switch)."""
+    rows = []
+    diag = (0, 1) if (lay.c_n == 2 and not lay.depthwise) else (0,)
+    for ti, (dy, dx) in enumerate(lay.taps()):
+        g_tap = bfv.rotation_element(P, dy * lay.W_b + dx)
+        for d in diag:
+            g = g_tap if d == 0 else (g_tap * bfv.row_swap_element(P)) % (2 * P.N)
+            rows.append((ti, d, g))
+    return rows
+
+
+def galois_elements(P: Params, lay: Layout) -> list[int]:
+    return sorted({g for _, _, g in rotation_plan(P, lay) if g != 1})
+
+
+# ---------------------------------------------------------------- the layer
+def hadamard_scalars(lay: Layout, weights: np.ndarray, g: int, j: int, ti: int, d: int) -> tuple[int, int]:
+    """(s0, s1) = (v0 + v1, v0 - v1) for output pair g, input pair j, tap ti,
+    diagonal d (Eq. 1 without the 1/2).  Row 0 of the output is channel 2g,
+    row 1 is 2g+1; diagonal d = 1 sees the input rows swapped."""
+    kw = lay.kh
+    dy, dx = divmod(ti, kw)
+
+    def w(o, i):
+        if o >= lay.C_out or i >= lay.C_in:
+            return 0
+        if lay.depthwise:
+            return int(weights[o, 0, dy, dx]) if o == i else 0
+        return int(weights[o, i, dy, dx])
+
+    if d == 0:
+        v0, v1 = w(2 * g, 2 * j), w(2 * g + 1, 2 * j + 1)
+    else:
+        v0, v1 = w(2 * g, 2 * j + 1), w(2 * g + 1, 2 * j)
+    return v0 + v1, v0 - v1
+
+
+def output_scale(P: Params, lay: Layout) -> int:
+    """The factor the layer's output carries: 2k with packing, 1 without."""
+    return (2 * P.k) % P.t if lay.c_n == 2 else 1
+
+
+def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk: dict,
+            out_cts: list[int] | None = None) -> np.ndarray:
+    """Homomorphic convolution of one layer.
+
+    For every input ciphertext: decompose once, then one hoisted rotation per
+    (tap, diagonal).  For every output ciphertext: CMult by the integer
+    scalars and HAdd over input ciphertexts, taps and diagonals (reduced
+    eagerly: the residues equal those of the lazy form), then with packing
+    out = k * A0 + PMult(A1, [k, -k]) (Sec. 3.1, Sec. 3.2.1).
+
+    `out_cts` restricts the work to a subset of output ciphertexts (the
+    others are left zero), for sampled comparisons at full size."""
+    plan = rotation_plan(P, lay)
+    n_out = lay.n_ct_out
+    todo = range(n_out) if out_cts is None else sorted(set(out_cts))
+    need_ru = sorted({c // lay.out_groups for c in todo})
+    out = np.zeros((n_out, 2, P.L, P.N), dtype=np.uint64)
+    pk = bfv.hadamard_plaintext(P) if lay.c_n == 2 else None
+
+    for ru in need_ru:
+        # rotated copies of this row-unit's input ciphertexts
+        rot = {}
+        needed_j = range(lay.in_groups)
+        if lay.depthwise:
+            needed_j = sorted({c % lay.out_groups for c in todo if c // lay.out_groups == ru})
+        for j in needed_j:
+            ct = cts_in[ru * lay.in_groups + j]
+            digits = bfv.decompose(P, ct)
+            for ti, d, g in plan:
+                rot[(j, ti, d)] = ct.copy() if g == 1 else bfv.rotate_hoisted(P, ct, digits, ksk[g], g)
+        for c in todo:
+            if c // lay.out_groups != ru:
+                continue
+            g_out = c % lay.out_groups
+            if lay.c_n == 2:
+                A0 = np.zeros((2, P.L, P.N), dtype=np.uint64)
+                A1 = np.zeros((2, P.L, P.N), dtype=np.uint64)
+                js = [g_out] if lay.depthwise else range(lay.in_groups)
+                for j in js:
+                    for ti, d, _ in plan:
+                        s0, s1 = hadamard_scalars(lay, weights, g_out, j, ti, d)
+                        if s0:
+                            bfv.cmult_add(P, A0, rot[(j, ti, d)], s0)
+                        if s1:
+                            bfv.cmult_add(P, A1, rot[(j, ti, d)], s1)
+                res = bfv.cmult(P, A0, P.k)
+                res = bfv.hadd(P, res, bfv.pmult(P, A1, pk))
+            else:
+                res = np.zeros((2, P.L, P.N), dtype=np.uint64)
+                js = [g_out] if lay.depthwise else range(lay.in_groups)
+                for j in js:
+                    for ti, _, _ in plan:
+                        dy, dx = divmod(ti, lay.kh)
+                        f = int(weights[g_out, 0 if lay.depthwise else j, dy, dx]) \
+                            if (g_out < lay.C_out and j < lay.C_in) else 0
+                        if f:
+                            bfv.cmult_add(P, res, rot[(j, ti, 0)], f)
+            out[c] = res
+    return out
+
+
+# ------------------------------------------------------------ client helpers
+def encrypt_image(P: Params, lay: Layout, s: np.ndarray, act: np.ndarray, seed: int) -> np.ndarray:
+    slots = pack_slots(lay, act)
+    return np.stack([bfv.encrypt(P, s, bfv.encode(P, slots[c]), seed, c) for c in range(lay.n_ct_in)])
+
+
+def decrypt_image(P: Params, lay: Layout, s: np.ndarray, cts_out: np.ndarray, unscale: bool = True) -> np.ndarray:
+    slots = np.stack([bfv.decode(P, bfv.decrypt(P, s, cts_out[c])) for c in range(lay.n_ct_out)])
+    out = unpack_slots(lay, slots)
+    if unscale:
+        inv = pow(output_scale(P, lay), -1, P.t)
+        out = (out * inv) % P.t
+    return out

@@ -96,6 +96,7 @@ static int bern_exp_small(rng_t* r, u64 n, u64 d) { /* n <= d */
     return (int)(K & 1);
 }
 static int bern_exp(rng_t* r, u64 n, u64 d) {
+    if (n <= d) return bern_exp_small(r, n, d); /* gamma in [0, 1] */
     u64 whole = n / d;
     for (u64 i = 0; i < whole; i++)
         if (!bern_exp_small(r, 1, 1)) return 0;

@@ -1,0 +1,311 @@
+"""Throughput of encrypted convolution on the GB300 (one JSON line on stdout).
+
+Workload: the 19 3x3 convolutions of a ResNet-20 on 32x32 inputs, one image
+per GPU, N = 8192, L = 3 RNS limbs of 50 bits, t = 1032193, Hyena packing
+(c_n = 2), plain per-layer kernels.  A step runs all 19 layers once through
+he_conv_forward on fresh synthetic ciphertexts resident in HBM.  value =
+layers/s over all ranks; modMAC/s is reported beside it.  e2e repeats the
+step through he_conv_forward_host with pinned host buffers (copies inside
+the timed region).  --impl reference times the CPU oracle instead.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under
+torch.distributed.run (one process per GPU, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+N_RING, L_LIMBS, LIMB_BITS = 8192, 3, 50
+WORKLOAD = "resnet20-3x3-stack, 32x32, 1 image/GPU, N=8192, L=3x50-bit, t=1032193, c_n=2"
+METRIC = "HE-conv layers/s (ResNet-20 stack, bit-exact)"
+L2_BYTES = 129 * 2**20
+
+
+def layer_descs():
+    return [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
+                 n_images=1, c_n=2) for s in synth.resnet20_convs()]
+
+
+def modmacs(spec, lay, n_rot, L, l, N):
+    """Algorithmic modular multiply-accumulates of one layer (conv MAC + key switch)."""
+    K = n_rot if spec["depthwise"] else lay.in_groups * n_rot
+    conv = lay.row_units * lay.out_groups * (2 if spec["c_n"] == 2 else 1) * K * 2 * L * N
+    ks = lay.n_ct_in * lay.n_galois * 2 * L * l * L * N
+    return conv, ks
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 2 + i and r[2 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle (CPU) sample
+def oracle_sample(reps=1):
+    """The CPU oracle on one whole layer of the stack (16 -> 16 channels, 32x32):
+    returns (seconds per layer, description).  Single-threaded."""
+    from oracle import bfv, conv
+    from oracle import params as prm
+
+    P = prm.make_params(N=N_RING, L=L_LIMBS, w=50)
+    spec = layer_descs()[1]
+    lay = conv.Layout(N=N_RING, **spec)
+    s = bfv.keygen(P, synth.SEED_KEYS)
+    ksk = {g: bfv.galois_key(P, s, g, synth.SEED_KEYS) for g in conv.galois_elements(P, lay)}
+    act = synth.activations((1, spec["C_in"], spec["H"], spec["W"]), P.t, label=1)
+    wt = synth.weights((spec["C_out"], spec["C_in"], 3, 3), label=1)
+    cts = conv.encrypt_image(P, lay, s, act, synth.SEED_ENC)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        conv.he_conv(P, lay, wt, cts, ksk)
+        times.append(time.perf_counter() - t0)
+    return times, "one whole ResNet-20 layer (16->16 channels, 32x32, N=8192, L=3) per step, 1 thread"
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    times, desc = oracle_sample(reps=steps + warm)
+    t = sum(times[warm:])
+    value = steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1000 * t / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2311_12519_gb300 import hyena as H
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    p = H.he_params_create(N_RING, L_LIMBS, limb_bits=LIMB_BITS, decomp_bits=0, est_mac_terms=64 * 9)
+    info = H.he_params_info(p)
+    N, L, l = info.N, info.L, info.l
+    sk = H.he_keygen(p, synth.SEED_KEYS)
+    specs = layer_descs()
+    descs = [H.conv_desc(**s) for s in specs]
+    gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
+    gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
+    plans, d_ins, d_outs, h_ins, h_outs = [], [], [], [], []
+    ws_max, conv_mm, ks_mm, in_bytes, out_bytes = 0, 0, 0, 0, 0
+    stage_bytes = {"ntt_in": 0, "keyswitch": 0, "mac": 0, "ntt_out": 0}
+    for i, (s, d) in enumerate(zip(specs, descs)):
+        act = synth.activations((1, s["C_in"], s["H"], s["W"]), info.t, label=i + 1000 * rank)
+        wt = synth.weights((s["C_out"], s["C_in"], s["kh"], s["kh"]), label=i)
+        cts = H.he_encrypt_image(p, sk, d, act, synth.SEED_ENC + 7919 * rank, info)
+        plan = H.he_conv_plan(p, gk, d, wt)
+        n_in, n_out, ws = H.he_conv_sizes(plan)
+        lay = H.he_layout_for_layer(p, d)
+        n_rot = s["kh"] ** 2 * 2
+        cm, km = modmacs(s, lay, n_rot, L, l, N)
+        conv_mm += cm
+        ks_mm += km
+        ctb = 2 * L * N * 8
+        # algorithmic bytes of each stage (one read of every input, one write of every output)
+        stage_bytes["ntt_in"] += lay.n_ct_in * ctb + lay.n_ct_in * (2 * L + L * l * L) * N * 8
+        stage_bytes["keyswitch"] += (lay.n_ct_in * lay.n_galois * (L * l * L * N * 8 + L * N * 8 + ctb)
+                                     + lay.n_galois * L * l * 2 * L * N * 8)
+        stage_bytes["mac"] += lay.n_ct_in * n_rot * ctb + lay.n_ct_out * ctb
+        stage_bytes["ntt_out"] += 2 * lay.n_ct_out * ctb
+        plans.append(plan)
+        h_in = torch.from_numpy(cts.reshape(-1).view(np.int64)).pin_memory()
+        h_ins.append(h_in)
+        h_outs.append(torch.empty(n_out, dtype=torch.int64).pin_memory())
+        d_ins.append(h_in.to(dev))
+        d_outs.append(torch.empty(n_out, dtype=torch.int64, device=dev))
+        ws_max = max(ws_max, ws)
+        in_bytes += n_in * 8
+        out_bytes += n_out * 8
+    d_ws = torch.empty(ws_max // 8 + 1, dtype=torch.int64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    n_layers = len(plans)
+    sp = stream.cuda_stream
+
+    def step():
+        for plan, a, b in zip(plans, d_ins, d_outs):
+            H.he_conv_forward(plan, a.data_ptr(), b.data_ptr(), d_ws.data_ptr(), sp)
+
+    def step_host():
+        for plan, a, b, ha, hb in zip(plans, d_ins, d_outs, h_ins, h_outs):
+            H.he_conv_forward_host(plan, ha.data_ptr(), hb.data_ptr(), a.data_ptr(), b.data_ptr(), d_ws.data_ptr(),
+                                   sp)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        # timed region: K steps, L2 flushed before each (outside the events)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        H.he_profile_enable(True)
+        H.he_profile_collect()
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        H.he_profile_enable(False)
+        stages = H.he_profile_collect()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        # end to end through host buffers
+        for _ in range(2):
+            step_host()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+    if world > 1:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_s = t.tolist()
+    if rank != 0:
+        return
+    ms_step = ms / args.steps
+    layers_per_s = world * n_layers * args.steps / (ms / 1000)
+    # dominant stage and its roofline
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    top = max(stages, key=lambda k: stages[k][0])
+    top_ms, top_launches = stages[top]
+    per_launch_s = top_ms / 1000 / max(1, top_launches)
+    if top == "mac":
+        # CUDA-core integer roof: 2 IMAD.WIDE per modMAC, 64 IMAD lanes per SM per clock issue
+        # at half rate for the 64-bit wide form -> 32 wide products per SM per clock
+        alu_peak = 152 * 2.07e9 * 32 / 2 / 1e12  # TmodMAC/s
+        achieved = conv_mm * args.steps / (top_ms / 1000) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TmodMAC/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_mac",
+                "peak_source": "derived: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 2 per modMAC"}
+    else:
+        achieved = stage_bytes[top] * args.steps / (top_ms / 1000) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": top, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["ms_per_launch"] = per_launch_s * 1000
+    roof["stage_share"] = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        times, desc = oracle_sample(reps=1)
+        cpu = {"value": 1.0 / times[0], "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": METRIC, "value": layers_per_s, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "layers_per_step": n_layers, "images_per_gpu": 1,
+                   "l2": "flushed before each timed step (256 MiB write)", "decomp_bits": info.w,
+                   "parallelism": f"replicas x{world} (independent images, no collective)"},
+        "modmac_per_s": (conv_mm + ks_mm) * world * args.steps / (ms / 1000),
+        "modmac_per_step": {"conv": conv_mm, "keyswitch": ks_mm},
+        "e2e": {"value": world * n_layers * args.steps / e2e_s, "unit": "layers/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": out_bytes},
+        "gpu_launches": 4 * n_layers * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hyena", choices=["hyena", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Ciphertexts are compared word for word (exact modular arithmetic, so the bar
+is bit-exactness), and outputs are decrypted against the plain convolution.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import bfv, conv  # noqa: E402
+from oracle import params as prm  # noqa: E402
+from paper_2311_12519_gb300 import hyena as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).reshape(-1).view(np.int64)).cuda()
+
+
+def from_dev(t, shape):
+    return t.cpu().numpy().view(np.uint64).reshape(shape)
+
+
+def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0):
+    plan = H.he_conv_plan(p, gk, d, w, mac_groups=mac_groups)
+    n_in, n_out, ws = H.he_conv_sizes(plan)
+    assert n_in == cts.size
+    d_in = to_dev(cts)
+    d_out = torch.full((n_out,), -1, dtype=torch.int64, device="cuda")
+    d_ws = torch.empty(ws // 8 + 1, dtype=torch.int64, device="cuda")
+    s = stream or torch.cuda.current_stream()
+    H.he_conv_forward(plan, d_in.data_ptr(), d_out.data_ptr(), d_ws.data_ptr(), s.cuda_stream)
+    torch.cuda.synchronize()
+    assert (from_dev(d_in, cts.shape) == cts).all(), "input modified"
+    out = from_dev(d_out, (n_out // (2 * L * N), 2, L, N))
+    H.he_plan_destroy(plan)
+    return out
+
+
+class Setup:
+    def __init__(self, N, L, w):
+        self.N, self.L, self.w = N, L, w
+        self.p = H.he_params_create(N, L, decomp_bits=w)
+        self.info = H.he_params_info(self.p)
+        self.P = prm.make_params(N=N, L=L, w=w)
+        self.sk = H.he_keygen(self.p, synth.SEED_KEYS)
+        self.s = bfv.keygen(self.P, synth.SEED_KEYS)
+        self._ksk = {}
+
+    def oracle_keys(self, gs):
+        for g in gs:
+            if g not in self._ksk:
+                self._ksk[g] = bfv.galois_key(self.P, self.s, g, synth.SEED_KEYS)
+        return self._ksk
+
+    def layer(self, spec, label=0, sample=None, mac_groups=0):
+        N, L = self.N, self.L
+        d = H.conv_desc(**spec)
+        ol = conv.Layout(N=N, **spec)
+        act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), self.P.t, label=label)
+        wt = synth.weights((spec["C_out"], 1 if spec["depthwise"] else spec["C_in"], spec["kh"], spec["kh"]),
+                           label=label)
+        gs = H.he_layer_galois(self.p, d)
+        gk = H.he_galois_keys(self.p, self.sk, gs, synth.SEED_KEYS)
+        cts = H.he_encrypt_image(self.p, self.sk, d, act, synth.SEED_ENC, self.info)
+        ref_in = conv.encrypt_image(self.P, ol, self.s, act, synth.SEED_ENC)
+        assert (cts == ref_in).all()
+        out = gpu_layer(self.p, gk, d, wt, cts, L, N, mac_groups=mac_groups)
+        ref = conv.he_conv(self.P, ol, wt, ref_in, self.oracle_keys(gs), out_cts=sample)
+        idx = range(len(out)) if sample is None else sample
+        for c in idx:
+            assert (out[c] == ref[c]).all(), f"ciphertext {c} differs from the oracle"
+        dec = H.he_decrypt_image(self.p, self.sk, d, out)
+        plain = conv.conv_plain(act, wt, spec["stride"], (spec["kh"] - 1) // 2, spec["depthwise"], self.P.t)
+        assert (dec == plain).all(), "decryption differs from the plain convolution"
+        H.he_galkeys_destroy(gk)
+        return out
+
+
+@pytest.fixture(scope="module")
+def small():
+    return Setup(1024, 2, 25)
+
+
+# ---------------------------------------------------------------- NTT
+@pytest.mark.parametrize("N,L,w", [(1024, 2, 25), (4096, 2, 25), (8192, 3, 50), (16384, 6, 50)])
+def test_ntt_round_trip_and_negacyclic_product(N, L, w):
+    p = H.he_params_create(N, L, decomp_bits=w)
+    P = prm.make_params(N=N, L=L, w=w)
+    rng = np.random.default_rng(N + L)
+    a = np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in P.q])
+    b = np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in P.q])
+    da, db = to_dev(a), to_dev(b)
+    H.he_ntt_forward(p, da.data_ptr(), L)
+    H.he_ntt_forward(p, db.data_ptr(), L)
+    torch.cuda.synchronize()
+    A, B = from_dev(da, (L, N)), from_dev(db, (L, N))
+    # pointwise product in the NTT domain, then back: the negacyclic product
+    C = np.stack([(A[k].astype(object) * B[k].astype(object) % P.q[k]).astype(np.uint64) for k in range(L)])
+    dc = to_dev(C)
+    H.he_ntt_inverse(p, dc.data_ptr(), L)
+    H.he_ntt_inverse(p, da.data_ptr(), L)
+    torch.cuda.synchronize()
+    assert (from_dev(da, (L, N)) == a).all()
+    from oracle import _clib
+    for k in range(min(L, 2)):
+        ref = np.zeros(N, dtype=np.uint64)
+        _clib.lib().orc_negacyclic_mul(a[k].copy(), b[k].copy(), ref, N, P.q[k], P.psi[k])
+        assert (from_dev(dc, (L, N))[k] == ref).all()
+    H.he_params_destroy(p)
+
+
+# ---------------------------------------------------------------- rotation
+@pytest.mark.parametrize("N,L,w,step,swap", [(1024, 2, 25, 1, False), (1024, 2, 25, -7, True), (4096, 2, 25, 35, False),
+                                             (8192, 3, 50, -1, True)])
+def test_rotation_matches_oracle(N, L, w, step, swap):
+    S = Setup(N, L, w)
+    g = bfv.rotation_element(S.P, step)
+    if swap:
+        g = g * bfv.row_swap_element(S.P) % (2 * N)
+    gk = H.he_galois_keys(S.p, S.sk, [g], synth.SEED_KEYS)
+    n_ct = 3
+    slots = [synth.activations((N,), S.P.t, label=i) for i in range(n_ct)]
+    cts = np.stack([H.he_encrypt_slots(S.p, S.sk, slots[i], synth.SEED_ENC, i, S.info) for i in range(n_ct)])
+    d_in, d_out = to_dev(cts), torch.empty(cts.size, dtype=torch.int64, device="cuda")
+    d_ws = torch.empty(H.he_rotate_workspace_bytes(S.p, n_ct) // 8 + 1, dtype=torch.int64, device="cuda")
+    H.he_rotate(S.p, gk, g, d_in.data_ptr(), d_out.data_ptr(), n_ct, d_ws.data_ptr())
+    out = from_dev(d_out, cts.shape)
+    ksk = S.oracle_keys([g])[g]
+    half = N // 2
+    for i in range(n_ct):
+        assert (out[i] == bfv.hrot(S.P, cts[i], ksk, g)).all()
+        a, b = np.roll(slots[i][:half], -step), np.roll(slots[i][half:], -step)
+        assert (H.he_decrypt_slots(S.p, S.sk, out[i], N) == np.concatenate([b, a] if swap else [a, b])).all()
+
+
+# ---------------------------------------------------------------- layers, small ring
+SMALL = [
+    dict(C_in=3, C_out=5, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=2),
+    dict(C_in=4, C_out=4, H=7, W=9, kh=3, stride=1, depthwise=False, n_images=3, c_n=1),
+    dict(C_in=4, C_out=4, H=7, W=9, kh=3, stride=1, depthwise=True, n_images=3, c_n=2),
+    dict(C_in=3, C_out=3, H=7, W=9, kh=3, stride=2, depthwise=True, n_images=2, c_n=1),
+    dict(C_in=4, C_out=6, H=9, W=10, kh=3, stride=2, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=2, C_out=2, H=30, W=40, kh=3, stride=1, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=2, C_out=3, H=12, W=200, kh=3, stride=1, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=6, C_out=4, H=5, W=5, kh=1, stride=1, depthwise=False, n_images=2, c_n=2),
+    dict(C_in=5, C_out=3, H=6, W=6, kh=1, stride=1, depthwise=False, n_images=1, c_n=1),
+    dict(C_in=2, C_out=2, H=6, W=6, kh=5, stride=1, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=1, C_out=1, H=1, W=1, kh=3, stride=1, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=20, C_out=18, H=5, W=5, kh=3, stride=1, depthwise=False, n_images=5, c_n=2),
+]
+
+
+@pytest.mark.parametrize("spec", SMALL)
+def test_layer_small_ring(small, spec):
+    small.layer(spec)
+
+
+@pytest.mark.parametrize("groups", [1, 2, 4, 8])
+def test_mac_group_tiling_is_invisible(small, groups):
+    spec = dict(C_in=6, C_out=22, H=5, W=5, kh=3, stride=1, depthwise=False, n_images=2, c_n=2)
+    small.layer(spec, mac_groups=groups)
+
+
+# ---------------------------------------------------------------- the 16-channel layer, N = 4096
+def test_single_layer_16_channels():
+    S = Setup(4096, 2, 25)
+    S.layer(dict(C_in=16, C_out=16, H=16, W=16, kh=3, stride=1, depthwise=False, n_images=1, c_n=2))
+
+
+# ---------------------------------------------------------------- ResNet-20 shapes at N = 8192, L = 3
+@pytest.fixture(scope="module")
+def resnet():
+    return Setup(8192, 3, 50)
+
+
+@pytest.mark.parametrize("li,sample", [(0, None), (1, None), (7, [0, 9]), (13, [3, 30])])
+def test_resnet20_layers(resnet, li, sample):
+    sh = synth.resnet20_convs()[li]
+    spec = dict(C_in=sh.C_in, C_out=sh.C_out, H=sh.H, W=sh.W, kh=sh.k, stride=sh.stride, depthwise=False,
+                n_images=1, c_n=2)
+    resnet.layer(spec, label=li, sample=sample)
+
+
+# ---------------------------------------------------------------- largest ring
+def test_largest_ring_depthwise_and_pointwise():
+    S = Setup(16384, 4, 50)
+    S.layer(dict(C_in=4, C_out=4, H=40, W=40, kh=3, stride=2, depthwise=True, n_images=2, c_n=2), sample=[0, 3])
+    S.layer(dict(C_in=6, C_out=4, H=20, W=20, kh=1, stride=1, depthwise=False, n_images=3, c_n=2), sample=[1])
+
+
+# ---------------------------------------------------------------- streams and repeats
+def test_repeat_on_side_stream_and_host_path(small):
+    spec = dict(C_in=4, C_out=6, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=2)
+    d = H.conv_desc(**spec)
+    act = synth.activations((2, 4, 6, 6), small.P.t)
+    wt = synth.weights((6, 4, 3, 3))
+    gk = H.he_galois_keys(small.p, small.sk, H.he_layer_galois(small.p, d), synth.SEED_KEYS)
+    cts = H.he_encrypt_image(small.p, small.sk, d, act, synth.SEED_ENC, small.info)
+    s = torch.cuda.Stream()
+    a = gpu_layer(small.p, gk, d, wt, cts, 2, 1024, stream=s)
+    b = gpu_layer(small.p, gk, d, wt, cts, 2, 1024)
+    assert (a == b).all()
+    plan = H.he_conv_plan(small.p, gk, d, wt)
+    n_in, n_out, ws = H.he_conv_sizes(plan)
+    h_out = np.zeros(n_out, dtype=np.uint64)
+    d_in = torch.empty(n_in, dtype=torch.int64, device="cuda")
+    d_out = torch.empty(n_out, dtype=torch.int64, device="cuda")
+    d_ws = torch.empty(ws // 8 + 1, dtype=torch.int64, device="cuda")
+    H.he_conv_forward_host(plan, np.ascontiguousarray(cts.reshape(-1)), h_out, d_in.data_ptr(), d_out.data_ptr(),
+                           d_ws.data_ptr())
+    assert (h_out.reshape(a.shape) == a).all()
+    H.he_plan_destroy(plan)

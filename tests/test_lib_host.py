@@ -1,0 +1,139 @@
+"""Host-side checks of the C-ABI library (no GPU): every declared symbol is
+exported, and the client-side code (parameters, keys, encryption, layout,
+decryption) agrees bit for bit with the independent oracle."""
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bfv, conv
+from oracle import params as prm
+from paper_2311_12519_gb300 import hyena as H
+
+
+def _declared():
+    src = open(H._build.os.path.join(H._build.os.path.dirname(H._build.HERE), "include", "hyena.h")).read()
+    return sorted(set(re.findall(r"\b(he_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    H.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", H.library_path()], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if " T " in line)
+    missing = [s for s in _declared() if s not in exported]
+    assert not missing, missing
+    lib = H.load()
+    for s in _declared():
+        assert hasattr(lib, s)
+
+
+@pytest.mark.parametrize("N,L,w", [(1024, 2, 25), (4096, 2, 25), (8192, 3, 50), (16384, 4, 50)])
+def test_params_match_oracle(N, L, w):
+    p = H.he_params_create(N, L, decomp_bits=w)
+    info = H.he_params_info(p)
+    P = prm.make_params(N=N, L=L, w=w)
+    assert info.t == P.t and info.zeta == P.zeta and info.h == P.h % P.t and info.k == P.k
+    assert info.kh == P.kh and info.l == P.l
+    assert [info.q[i] for i in range(L)] == P.q
+    assert abs(info.log2_delta - np.log2(float(P.delta))) < 1e-6
+    H.he_params_destroy(p)
+
+
+def test_param_selection_reproduces_worked_example():
+    # n = 2048 with Gazelle's p = 307201 -> h = 84248 (centred, up to sign), k = 11 (Sec. 3.2.1)
+    p = H.he_params_create(2048, 1, t=307201, decomp_bits=25)
+    info = H.he_params_info(p)
+    assert min(info.h, 307201 - info.h) == 84248 and info.k == 11
+    assert abs(info.kh) == 5125
+    H.he_params_destroy(p)
+
+
+def test_auto_decomposition_base():
+    # L = 2 (q ~ 2^100) cannot afford w = 50 for 16-channel 3x3 layers; L = 3 can
+    p = H.he_params_create(4096, 2, est_mac_terms=16 * 9)
+    assert H.he_params_info(p).w == 25
+    p3 = H.he_params_create(8192, 3, est_mac_terms=64 * 9)
+    assert H.he_params_info(p3).w == 50
+
+
+def test_errors():
+    with pytest.raises(H.HyenaError) as e:
+        H.he_params_create(1000, 2, decomp_bits=25)
+    assert e.value.code == H.HE_EINVAL
+    with pytest.raises(H.HyenaError) as e:
+        H.he_params_create(4096, 2, t=1032191, decomp_bits=25)
+    assert e.value.code == H.HE_EINVAL
+    p = H.he_params_create(1024, 2, decomp_bits=25)
+    with pytest.raises(H.HyenaError) as e:
+        H.he_layout_for_layer(p, H.conv_desc(4, 4, 8, 8, kh=2))
+    assert e.value.code == H.HE_EINVAL
+    with pytest.raises(H.HyenaError) as e:
+        H.he_layout_for_layer(p, H.conv_desc(4, 4, 8, 8, n_images=0))
+    assert e.value.code == H.HE_EINVAL
+    # a plan without its Galois keys is refused before any device work
+    sk = H.he_keygen(p, 1)
+    d = H.conv_desc(4, 4, 8, 8)
+    gk = H.he_galois_keys(p, sk, H.he_layer_galois(p, d)[:-1], 1)
+    with pytest.raises(H.HyenaError) as e:
+        H.he_conv_plan(p, gk, d, np.ones((4, 4, 3, 3)))
+    assert e.value.code == H.HE_EMISSINGKEY
+    gk2 = H.he_galois_keys(p, sk, H.he_layer_galois(p, d), 1)
+    with pytest.raises(H.HyenaError) as e:
+        H.he_conv_plan(p, gk2, d, np.full((4, 4, 3, 3), 20000))
+    assert e.value.code == H.HE_EINVAL
+
+
+def test_keys_and_ciphertexts_match_oracle():
+    N, L, w = 1024, 2, 25
+    p = H.he_params_create(N, L, decomp_bits=w)
+    info = H.he_params_info(p)
+    P = prm.make_params(N=N, L=L, w=w)
+    sk = H.he_keygen(p, 7)
+    s = bfv.keygen(P, 7)
+    assert (H.he_seckey_export(sk, N) == s).all()
+    for g in (3, 2 * N - 1, bfv.rotation_element(P, -5)):
+        gk = H.he_galois_keys(p, sk, [g], 11)
+        assert (H.he_galkeys_export(gk, g, info) == bfv.galois_key(P, s, g, 11)).all()
+    slots = synth.activations((N,), P.t)
+    for idx in (0, 9):
+        ct = H.he_encrypt_slots(p, sk, slots, 3, idx, info)
+        assert (ct == bfv.encrypt(P, s, bfv.encode(P, slots), 3, idx)).all()
+        assert (H.he_decrypt_slots(p, sk, ct, N) == slots).all()
+
+
+LAYERS = [
+    dict(C_in=3, C_out=5, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=2),
+    dict(C_in=4, C_out=4, H=7, W=9, kh=3, stride=1, depthwise=False, n_images=3, c_n=1),
+    dict(C_in=4, C_out=4, H=7, W=9, kh=3, stride=2, depthwise=True, n_images=3, c_n=2),
+    dict(C_in=2, C_out=2, H=30, W=40, kh=3, stride=1, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=2, C_out=2, H=12, W=200, kh=3, stride=2, depthwise=False, n_images=1, c_n=2),
+    dict(C_in=6, C_out=4, H=5, W=5, kh=1, stride=1, depthwise=False, n_images=2, c_n=2),
+    dict(C_in=2, C_out=2, H=6, W=6, kh=5, stride=1, depthwise=False, n_images=1, c_n=2),
+]
+
+
+@pytest.mark.parametrize("spec", LAYERS)
+def test_layout_and_image_encryption_match_oracle(spec):
+    N, L, w = 1024, 2, 25
+    p = H.he_params_create(N, L, decomp_bits=w)
+    info = H.he_params_info(p)
+    P = prm.make_params(N=N, L=L, w=w)
+    d = H.conv_desc(**{k: spec[k] for k in ("C_in", "C_out", "H", "W", "kh", "stride", "depthwise", "n_images",
+                                            "c_n")})
+    lay = H.he_layout_for_layer(p, d)
+    ol = conv.Layout(N=N, **spec)
+    assert (lay.T_h, lay.T_w, lay.blocks_per_row, lay.n_ct_in, lay.n_ct_out, lay.Ho, lay.Wo) == \
+        (ol.T_h, ol.T_w, ol.blocks_per_row, ol.n_ct_in, ol.n_ct_out, ol.Ho, ol.Wo)
+    assert list(H.he_layer_galois(p, d)) == conv.galois_elements(P, ol)
+    assert lay.scale == conv.output_scale(P, ol)
+    act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), P.t)
+    sk = H.he_keygen(p, 1)
+    s = bfv.keygen(P, 1)
+    ct = H.he_encrypt_image(p, sk, d, act, 2, info)
+    assert (ct == conv.encrypt_image(P, ol, s, act, 2)).all()
+    # decrypting the (unrotated) input through the output path reads the input back
+    if spec["kh"] == 3 and spec["stride"] == 1 and spec["C_in"] == spec["C_out"]:
+        back = H.he_decrypt_image(p, sk, d, ct, unscale=False)
+        assert (back == act).all()

@@ -2,8 +2,7 @@
 output-channel packing (Hyena, arXiv 2311.12519).
 
 The compute path is libhyena.so (hand-written sm_103a CUDA + host C++); this
-package only builds it and binds its C ABI (hyena.py).  PyTorch, where used
-by callers, provides device memory and streams.
+package only builds it (build.py) and binds its C ABI (hyena.py).  PyTorch,
+where used by callers, provides device memory and streams.
 """
-from . import hyena  # noqa: F401
-from .build import build  # noqa: F401
+from . import build, hyena  # noqa: F401

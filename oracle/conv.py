@@ -286,6 +286,8 @@ def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk
     plan = rotation_plan(P, lay)
     n_out = lay.n_ct_out
     todo = range(n_out) if out_cts is None else sorted(set(out_cts))
+    if any(c < 0 or c >= n_out for c in todo):
+        raise ValueError(f"output ciphertext index out of range [0, {n_out})")
     need_ru = sorted({c // lay.out_groups for c in todo})
     out = np.zeros((n_out, 2, P.L, P.N), dtype=np.uint64)
     pk = bfv.hadamard_plaintext(P) if lay.c_n == 2 else None

@@ -191,6 +191,29 @@ int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_
                          uint64_t* d_out, void* d_workspace, void* stream);
 void he_plan_destroy(he_plan* plan);
 
+/* Size of the static device scratch used by he_conv_forward_noalloc (32 MiB). */
+#define HE_NOALLOC_MAX_SCRATCH_BYTES 33554432u
+
+/* he_conv_forward without any device allocation by anyone.  The paper has no
+ * counterpart to this call; it exists for callers that cannot call cudaMalloc
+ * or take a workspace buffer from an allocator -- for example code that runs
+ * inside a memory pool that already owns all device memory, a service whose
+ * device allocations are frozen after start-up, or a latency-bound path where
+ * an allocation (which may synchronise the device) is not acceptable.
+ *
+ * The workspace is a file-scope device array of HE_NOALLOC_MAX_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits.  Layers
+ * whose he_conv_sizes workspace exceeds it are rejected with HE_EINVAL (use
+ * he_conv_forward).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The call performs no cudaMalloc, cudaFree
+ * or other allocation.  All calls share the one array and it keeps the last
+ * call's contents (every word a kernel reads is written earlier in the same
+ * call, so nothing needs clearing); calls whose work overlaps on the GPU --
+ * on different streams, or from different threads -- race on it.  The
+ * caller still owns d_in and d_out; per-stage event timing is not recorded. */
+int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in, uint64_t* d_out, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Single steps, for tests (device pointers, stream-ordered)          */
 /* ------------------------------------------------------------------ */

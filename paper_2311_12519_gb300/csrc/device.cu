@@ -317,9 +317,9 @@ struct StageTimer {
     cudaStream_t s;
     cudaEvent_t a = nullptr, b = nullptr;
     bool on;
-    StageTimer(int st, cudaStream_t str) : stage(st), s(str) {
+    StageTimer(int st, cudaStream_t str, bool allowed = true) : stage(st), s(str) {
         std::lock_guard<std::mutex> lk(g_prof.mu);
-        on = g_prof.on;
+        on = g_prof.on && allowed;
         if (on) {
             a = g_prof.get();
             b = g_prof.get();
@@ -656,7 +656,7 @@ static void launch_mac(const he_plan* P, const u64* R, u64* O, cudaStream_t s) {
     check_launch("k_mac");
 }
 
-static void forward_impl(const he_plan* P, const u64* d_in, u64* d_out, void* ws, cudaStream_t s) {
+static void forward_impl(const he_plan* P, const u64* d_in, u64* d_out, void* ws, cudaStream_t s, bool timed = true) {
     const he_params* p = P->p;
     if (((uintptr_t)d_in | (uintptr_t)d_out | (uintptr_t)ws) & 15) fail(HE_EINVAL, "device pointers must be 16-byte aligned");
     int dev = -1;
@@ -668,19 +668,19 @@ static void forward_impl(const he_plan* P, const u64* d_in, u64* d_out, void* ws
     u64* O = (u64*)(base + P->off_O);
     const he_layout& lay = P->lay;
     {
-        StageTimer t(HE_STAGE_NTT_IN, s);
+        StageTimer t(HE_STAGE_NTT_IN, s, timed);
         launch_ntt_inputs(p, P->kp, d_in, R, D, lay.n_ct_in, P->n_rot, P->rot_id, s);
     }
     {
-        StageTimer t(HE_STAGE_KEYSWITCH, s);
+        StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
         launch_keyswitch(p, P->kp, D, R, P->d_ksk, P->d_rots, P->n_ks, lay.n_ct_in, P->n_rot, P->rot_id, s);
     }
     {
-        StageTimer t(HE_STAGE_MAC, s);
+        StageTimer t(HE_STAGE_MAC, s, timed);
         launch_mac(P, R, O, s);
     }
     {
-        StageTimer t(HE_STAGE_NTT_OUT, s);
+        StageTimer t(HE_STAGE_NTT_OUT, s, timed);
         const size_t ctw = 2ull * p->L * p->N;
         launch_intt(p, P->kp, O, ctw, d_out, ctw, lay.n_ct_out, s);
     }
@@ -707,6 +707,46 @@ extern "C" int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, u
 }
 
 extern "C" void he_plan_destroy(he_plan* plan) { delete plan; }
+
+// ================================================================== allocation-free forward
+// Scratch for he_conv_forward_noalloc.  A file-scope device array: the CUDA
+// runtime reserves it on every device that loads this library, for the life
+// of the process, so the entry point itself never allocates.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HE_NOALLOC_MAX_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::vector<std::pair<int, void*>> g_noalloc_addr;  // (device, device address of g_noalloc_scratch)
+
+// Device address of the scratch array on the current device.  In host code
+// the name g_noalloc_scratch is only a host-side stand-in, so the address is
+// looked up once per device with that device current.
+void* noalloc_scratch() {
+    int dev = -1;
+    CUDA_OK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    for (auto& e : g_noalloc_addr)
+        if (e.first == dev) return e.second;
+    void* ptr = nullptr;
+    CUDA_OK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    if (!ptr) fail(HE_ECUDA, "cudaGetSymbolAddress returned a null scratch address");
+    g_noalloc_addr.push_back({dev, ptr});
+    return ptr;
+}
+}  // namespace
+
+extern "C" int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in, uint64_t* d_out, void* stream) {
+    return guard([&] {
+        if (!plan || !d_in || !d_out) fail(HE_EINVAL, "null argument");
+        if (plan->ws_bytes > (size_t)HE_NOALLOC_MAX_SCRATCH_BYTES)
+            fail(HE_EINVAL, "layer needs " + std::to_string(plan->ws_bytes) + " bytes of scratch; the static scratch holds " +
+                                std::to_string((size_t)HE_NOALLOC_MAX_SCRATCH_BYTES) + " (use he_conv_forward)");
+        void* ws = noalloc_scratch();
+        // every scratch word a kernel reads was written earlier in the same call,
+        // so nothing has to be cleared between calls
+        forward_impl(plan, d_in, d_out, ws, (cudaStream_t)stream, /*timed=*/false);
+    });
+}
 
 // ================================================================== single steps
 extern "C" int he_ntt_forward(const he_params* p, uint64_t* d, int n, void* stream) {

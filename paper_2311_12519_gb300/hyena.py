@@ -99,6 +99,7 @@ def load(build_if_stale: bool = True):
         "he_conv_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "he_conv_forward_host": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp]),
         "he_plan_destroy": (None, [vp]),
+        "he_conv_forward_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
         "he_ntt_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_ntt_inverse": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_rotate_workspace_bytes": (ctypes.c_int, [vp, ctypes.c_int, P(sz)]),
@@ -265,6 +266,15 @@ def he_conv_forward_host(plan, h_in, h_out, d_in, d_out, d_ws, stream=0):
 
 def he_plan_destroy(plan):
     load().he_plan_destroy(plan)
+
+
+HE_NOALLOC_MAX_SCRATCH_BYTES = 33554432
+
+
+def he_conv_forward_noalloc(plan, d_in, d_out, stream=0):
+    """he_conv_forward with the library's static device scratch instead of a
+    caller workspace, for callers that cannot allocate device memory."""
+    _check(load().he_conv_forward_noalloc(plan, _ptr(d_in), _ptr(d_out), stream or None), "he_conv_forward_noalloc")
 
 
 # ---------------------------------------------------------------------- single steps

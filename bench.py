@@ -48,6 +48,29 @@ def modmacs(spec, lay, n_rot, L, l, N):
     return conv, ks
 
 
+# ------------------------------------------------------------------ ranks
+def rank_inputs(rank):
+    """Per-rank workload: rank r encrypts its own image (activation labels and
+    encryption seed depend on r); weights and keys are shared by all ranks."""
+    return {"act_label": 1000 * rank, "enc_seed": synth.SEED_ENC + 7919 * rank}
+
+
+def reduce_max(values, device, world):
+    """Max over ranks of the timed values (barrier + max timing; no data-path collective)."""
+    if world <= 1:
+        return list(values)
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def layers_per_second(world, n_layers, steps, seconds):
+    """Whole-job throughput: every rank runs n_layers layers per step on its own image."""
+    return world * n_layers * steps / seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -149,9 +172,10 @@ def run_gpu(args, rank, world):
     ws_max, conv_mm, ks_mm, in_bytes, out_bytes = 0, 0, 0, 0, 0
     stage_bytes = {"ntt_in": 0, "keyswitch": 0, "mac": 0, "ntt_out": 0}
     for i, (s, d) in enumerate(zip(specs, descs)):
-        act = synth.activations((1, s["C_in"], s["H"], s["W"]), info.t, label=i + 1000 * rank)
+        ri = rank_inputs(rank)
+        act = synth.activations((1, s["C_in"], s["H"], s["W"]), info.t, label=i + ri["act_label"])
         wt = synth.weights((s["C_out"], s["C_in"], s["kh"], s["kh"]), label=i)
-        cts = H.he_encrypt_image(p, sk, d, act, synth.SEED_ENC + 7919 * rank, info)
+        cts = H.he_encrypt_image(p, sk, d, act, ri["enc_seed"], info)
         plan = H.he_conv_plan(p, gk, d, wt)
         n_in, n_out, ws = H.he_conv_sizes(plan)
         lay = H.he_layout_for_layer(p, d)
@@ -225,14 +249,11 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         barrier()
-    if world > 1:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_s = t.tolist()
+    ms, e2e_s = reduce_max([ms, e2e_s], dev, world)
     if rank != 0:
         return
     ms_step = ms / args.steps
-    layers_per_s = world * n_layers * args.steps / (ms / 1000)
+    layers_per_s = layers_per_second(world, n_layers, args.steps, ms / 1000)
     # dominant stage and its roofline
     peaks = {}
     try:
@@ -270,7 +291,8 @@ def run_gpu(args, rank, world):
                    "parallelism": f"replicas x{world} (independent images, no collective)"},
         "modmac_per_s": (conv_mm + ks_mm) * world * args.steps / (ms / 1000),
         "modmac_per_step": {"conv": conv_mm, "keyswitch": ks_mm},
-        "e2e": {"value": world * n_layers * args.steps / e2e_s, "unit": "layers/s", "h2d_bytes_per_step": in_bytes,
+        "e2e": {"value": layers_per_second(world, n_layers, args.steps, e2e_s), "unit": "layers/s",
+                "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes},
         "gpu_launches": 4 * n_layers * args.steps,
         "roofline": roof,

@@ -164,8 +164,9 @@ int he_decrypt_slots(const he_params* p, const he_seckey* sk, const uint64_t* ct
 /* Server side: one convolution layer on the GPU                      */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    uint32_t mac_groups;     /* output channel groups per MAC block (0 -> default) */
-    uint32_t reserved[7];
+    uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block (0 -> default) */
+    uint32_t mac_impl;       /* 0 auto, 1 CUDA-core MAC, 2 tensor-core MAC (HE_EINVAL if not exact) */
+    uint32_t reserved[6];
 } he_tune;
 
 /* Uploads the layer's Galois keys (NTT form), the Hadamard scalars
@@ -189,6 +190,13 @@ int he_conv_forward(const he_plan* plan, const uint64_t* d_in, uint64_t* d_out, 
  * d_out to h_out, and synchronises the stream before returning. */
 int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_out, uint64_t* d_in,
                          uint64_t* d_out, void* d_workspace, void* stream);
+/* Synchronises the device and returns HE_ETIMEOUT if a bounded wait inside
+ * an earlier forward of this plan gave up (the outputs are then invalid). */
+int he_conv_status(const he_plan* plan);
+/* *mac_impl = 1 (CUDA-core MAC) or 2 (tensor-core MAC) for this plan.  The
+ * tensor-core form (fp16 10-bit chunks, fp32 sums) is chosen automatically
+ * when it is exact: no depthwise, |s| <= 16 and at most 2048 terms. */
+int he_conv_info(const he_plan* plan, int* mac_impl);
 void he_plan_destroy(he_plan* plan);
 
 /* Size of the static device scratch used by he_conv_forward_noalloc (32 MiB). */

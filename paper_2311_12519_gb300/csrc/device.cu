@@ -11,6 +11,7 @@
 //                     with 64-bit split accumulators; one reduction per sum;
 //                     epilogue k*A0 + A1 * NTT(P_k) (the [k,-k] PMult)
 //   4. k_intt         inverse NTT to coefficient form
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,51 +59,188 @@ __device__ __forceinline__ u64 bred(u64 lo, u64 hi, const LimbC& m) {
 }
 __device__ __forceinline__ u64 bred128(u128 x, const LimbC& m) { return bred((u64)x, (u64)(x >> 64), m); }
 __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const LimbC& m) { return bred(a * b, __umul64hi(a, b), m); }
-__device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wsh, u64 q) {
-    u64 qt = __umul64hi(a, wsh);
-    u64 r = a * w - qt * q;
-    return r >= q ? r - q : r;
-}
 __device__ __forceinline__ u64 addq(u64 a, u64 b, u64 q) {
     u64 s = a + b;
     return s >= q ? s - q : s;
 }
-__device__ __forceinline__ u64 subq(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
-// ------------------------------------------------------------------ NTT in shared memory
-// Forward: Cooley-Tukey, natural -> bit-reversed, twiddle psi^rev(m+i) for group i of stage m.
-__device__ void ntt_fwd_smem(u64* a, u32 N, u32 logN, const u64* tw, const u64* tw_sh, u64 q) {
-    for (u32 m = 1, logt = logN - 1; m < N; m <<= 1, logt--) {
-        const u32 t = 1u << logt;
-        for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            u32 i = b >> logt, j = b & (t - 1);
-            u32 i1 = (i << (logt + 1)) + j, i2 = i1 + t;
-            u64 U = a[i1], V = shoup(a[i2], __ldg(tw + m + i), __ldg(tw_sh + m + i), q);
-            a[i1] = addq(U, V, q);
-            a[i2] = subq(U, V, q);
+// ------------------------------------------------------------------ NTT
+// One CTA transforms one limb-polynomial of N words.  The slot index has
+// log2 N bits; a "window" is 4 consecutive bit positions [lo, lo+4).  Each
+// thread holds, in registers, the 16 elements whose indices differ only in
+// the window, runs every butterfly stage of those bit positions, and
+// exchanges through shared memory between windows: 3-4 round trips instead
+// of log2 N.  Butterflies keep Harvey's lazy ranges ([0,4q) forward, [0,2q)
+// inverse; q < 2^58 leaves the headroom) and Shoup products with
+// precomputed w' = floor(w 2^64 / q).
+//
+// Forward (Cooley-Tukey, natural -> bit-reversed): the stage on bit p pairs
+// indices that differ in bit p, group i = index >> (p+1), twiddle
+// psi^rev(2^(logN-1-p) + i).  Inverse (Gentleman-Sande) runs the bits in the
+// opposite order with psi^-rev(...) at the same position.
+constexpr int NTT_E = 16;
+constexpr int NTT_MAX_THREADS = 256;
+
+__device__ __forceinline__ u32 spad(u32 i) { return i + (i >> 5); }  // one pad word per 32
+__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wsh, u64 q) {
+    return a * w - __umul64hi(a, wsh) * q;  // in [0, 2q)
+}
+
+template <int PE_TOP>
+__device__ __forceinline__ void fwd_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo, u32 logN, const u64* __restrict__ tw,
+                                           const u64* __restrict__ tws, u64 q, u64 q2) {
+#pragma unroll
+    for (int pe = PE_TOP; pe >= 0; pe--) {
+        const u32 off = 1u << (logN - 1 - (lo + pe));
+#pragma unroll
+        for (int e = 0; e < NTT_E; e++) {
+            if (e & (1 << pe)) continue;
+            const int e2 = e | (1 << pe);
+            const u32 i = off + ((u32)(e >> (pe + 1)) | (base_hi << (3 - pe)));
+            const u64 W = __ldg(tw + i), Ws = __ldg(tws + i);
+            u64 X = x[e];
+            X = X >= q2 ? X - q2 : X;
+            const u64 T = shoup_lazy(x[e2], W, Ws, q);
+            x[e] = X + T;
+            x[e2] = X - T + q2;
         }
-        __syncthreads();
     }
 }
-// Inverse: Gentleman-Sande, bit-reversed -> natural, twiddle psi^-rev(h+i); no 1/N scaling.
-__device__ void ntt_inv_smem(u64* a, u32 N, u32 logN, const u64* itw, const u64* itw_sh, u64 q) {
-    for (u32 h = N / 2, logt = 0; h >= 1; h >>= 1, logt++) {
-        const u32 t = 1u << logt;
-        for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            u32 i = b >> logt, j = b & (t - 1);
-            u32 i1 = (i << (logt + 1)) + j, i2 = i1 + t;
-            u64 U = a[i1], V = a[i2];
-            a[i1] = addq(U, V, q);
-            a[i2] = shoup(subq(U, V, q), __ldg(itw + h + i), __ldg(itw_sh + h + i), q);
+
+template <int PE_BOT>
+__device__ __forceinline__ void inv_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo, u32 logN, const u64* __restrict__ itw,
+                                           const u64* __restrict__ itws, u64 q, u64 q2) {
+#pragma unroll
+    for (int pe = PE_BOT; pe <= 3; pe++) {
+        const u32 off = 1u << (logN - 1 - (lo + pe));
+#pragma unroll
+        for (int e = 0; e < NTT_E; e++) {
+            if (e & (1 << pe)) continue;
+            const int e2 = e | (1 << pe);
+            const u32 i = off + ((u32)(e >> (pe + 1)) | (base_hi << (3 - pe)));
+            const u64 W = __ldg(itw + i), Ws = __ldg(itws + i);
+            const u64 X = x[e], Y = x[e2];
+            const u64 S = X + Y;
+            x[e] = S >= q2 ? S - q2 : S;
+            x[e2] = shoup_lazy(X - Y + q2, W, Ws, q);
         }
-        __syncthreads();
     }
 }
+
+// index of element e of set `set` in window [lo, lo+4)
+__device__ __forceinline__ u32 win_base(u32 set, u32 lo) { return ((set >> lo) << (lo + 4)) | (set & ((1u << lo) - 1)); }
+
+// Forward NTT of one polynomial: load(i) gives coefficient i in [0, 4q); store(i, v) receives slot i in [0, q).
+template <class Load, class Store>
+__device__ void ntt_forward_block(u64* sm, u32 N, u32 logN, const u64* tw, const u64* tws, u64 q, Load load,
+                                  Store store) {
+    const u64 q2 = 2 * q;
+    const u32 sets = N / NTT_E;
+    u64 x[NTT_E];
+    // first window: bits [logN-4, logN), loaded straight from global (coalesced: stride N/16)
+    u32 lo = logN - 4;
+    for (u32 set = threadIdx.x; set < sets; set += blockDim.x) {
+#pragma unroll
+        for (int e = 0; e < NTT_E; e++) x[e] = load(set | ((u32)e << lo));
+        fwd_window<3>(x, 0, lo, logN, tw, tws, q, q2);
+        if (lo == 0) {
+#pragma unroll
+            for (int e = 0; e < NTT_E; e++) {
+                u64 v = x[e];
+                v = v >= q2 ? v - q2 : v;
+                store(set | ((u32)e << lo), v >= q ? v - q : v);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < NTT_E; e++) sm[spad(set | ((u32)e << lo))] = x[e];
+        }
+    }
+    while (lo > 0) {
+        const u32 nlo = lo > 4 ? lo - 4 : 0;
+        const int pe_top = (int)(lo - 1 - nlo);
+        __syncthreads();
+        for (u32 set = threadIdx.x; set < sets; set += blockDim.x) {
+            const u32 base = win_base(set, nlo);
+#pragma unroll
+            for (int e = 0; e < NTT_E; e++) x[e] = sm[spad(base | ((u32)e << nlo))];
+            const u32 bh = base >> (nlo + 4);
+            switch (pe_top) {
+                case 3: fwd_window<3>(x, bh, nlo, logN, tw, tws, q, q2); break;
+                case 2: fwd_window<2>(x, bh, nlo, logN, tw, tws, q, q2); break;
+                case 1: fwd_window<1>(x, bh, nlo, logN, tw, tws, q, q2); break;
+                default: fwd_window<0>(x, bh, nlo, logN, tw, tws, q, q2); break;
+            }
+            if (nlo == 0) {
+#pragma unroll
+                for (int e = 0; e < NTT_E; e++) {
+                    u64 v = x[e];
+                    v = v >= q2 ? v - q2 : v;
+                    store(base | (u32)e, v >= q ? v - q : v);
+                }
+            } else {
+                // a set writes back exactly the positions it read, and sets are disjoint
+#pragma unroll
+                for (int e = 0; e < NTT_E; e++) sm[spad(base | ((u32)e << nlo))] = x[e];
+            }
+        }
+        lo = nlo;
+    }
+}
+
+// Inverse NTT (with the 1/N factor): load(i) gives slot i in [0, 2q); store(i, v) receives coefficient i in [0, q).
+template <class Load, class Store>
+__device__ void ntt_inverse_block(u64* sm, u32 N, u32 logN, const u64* itw, const u64* itws, u64 q, u64 ninv,
+                                  u64 ninv_sh, Load load, Store store) {
+    const u64 q2 = 2 * q;
+    const u32 sets = N / NTT_E;
+    u64 x[NTT_E];
+    u32 lo = 0;  // windows [0,4), [4,8), ...; the last one is [logN-4, logN) starting at the first unfinished bit
+    bool first = true;
+    while (true) {
+        const u32 wlo = (lo + 4 <= logN) ? lo : logN - 4;
+        const int pe_bot = (int)(lo - wlo);
+        const bool last = wlo + 4 >= logN;
+        if (!first) __syncthreads();
+        for (u32 set = threadIdx.x; set < sets; set += blockDim.x) {
+            const u32 base = win_base(set, wlo);
+            if (first) {
+#pragma unroll
+                for (int e = 0; e < NTT_E; e++) x[e] = load(base | ((u32)e << wlo));
+            } else {
+#pragma unroll
+                for (int e = 0; e < NTT_E; e++) x[e] = sm[spad(base | ((u32)e << wlo))];
+            }
+            const u32 bh = base >> (wlo + 4);
+            switch (pe_bot) {
+                case 0: inv_window<0>(x, bh, wlo, logN, itw, itws, q, q2); break;
+                case 1: inv_window<1>(x, bh, wlo, logN, itw, itws, q, q2); break;
+                case 2: inv_window<2>(x, bh, wlo, logN, itw, itws, q, q2); break;
+                default: inv_window<3>(x, bh, wlo, logN, itw, itws, q, q2); break;
+            }
+            if (last) {
+#pragma unroll
+                for (int e = 0; e < NTT_E; e++) {
+                    u64 v = shoup_lazy(x[e], ninv, ninv_sh, q);
+                    store(base | ((u32)e << wlo), v >= q ? v - q : v);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < NTT_E; e++) sm[spad(base | ((u32)e << wlo))] = x[e];
+            }
+        }
+        if (last) break;
+        first = false;
+        lo = wlo + 4;
+    }
+}
+
+__host__ __device__ constexpr size_t ntt_smem_bytes(u32 N) { return ((size_t)N + N / 32) * 8; }
 
 // Step 1: forward NTT of the inputs.  blockIdx.x = ciphertext c; blockIdx.y =
 // job: y < 2L -> polynomial y/L, limb y%L into R[c][rot_id]; otherwise digit
-// dd = (y-2L)/L of c1 lifted into limb (y-2L)%L, into D[c][dd].
-__global__ void k_ntt_inputs(const u64* __restrict__ in, u64* __restrict__ R, u64* __restrict__ D, KP kp,
+// dd = (y-2L)/L of c1 lifted into limb (y-2L)%L, into D[c][dd].  Digits are
+// below 2^w <= 2^s < 2q, inside the forward transform's input range.
+__global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_inputs(const u64* __restrict__ in, u64* __restrict__ R, u64* __restrict__ D, KP kp,
                              u32 n_rot, u32 rot_id) {
     extern __shared__ u64 sm[];
     const u32 N = kp.N, L = kp.L, l = kp.l;
@@ -111,7 +249,7 @@ __global__ void k_ntt_inputs(const u64* __restrict__ in, u64* __restrict__ R, u6
     const u64* src;
     u64* dst;
     u32 limb, shift = 0;
-    bool digit = false;
+    u64 mask = ~0ull;
     if (y < 2 * L) {
         limb = y % L;
         src = in + c * ctw + (size_t)y * N;
@@ -122,52 +260,39 @@ __global__ void k_ntt_inputs(const u64* __restrict__ in, u64* __restrict__ R, u6
         src = in + c * ctw + (size_t)(L + dd / l) * N;
         dst = D + (((size_t)c * L * l + dd) * L + limb) * N;
         shift = kp.w * (dd % l);
-        digit = true;
+        mask = (kp.w >= 64) ? ~0ull : ((1ull << kp.w) - 1);
     }
     const LimbC m = kp.limb[limb];
-    const u64 mask = (kp.w >= 64) ? ~0ull : ((1ull << kp.w) - 1);
-    for (u32 x = threadIdx.x; x < N; x += blockDim.x) {
-        u64 v = src[x];
-        if (digit) {
-            v = (shift >= 64) ? 0 : ((v >> shift) & mask);
-            v = v >= m.q ? v - m.q : v;
-        }
-        sm[x] = v;
-    }
-    __syncthreads();
-    ntt_fwd_smem(sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q);
-    for (u32 x = threadIdx.x; x < N; x += blockDim.x) dst[x] = sm[x];
+    ntt_forward_block(
+        sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q,
+        [&](u32 i) { return shift >= 64 ? 0ull : (__ldg(src + i) >> shift) & mask; },
+        [&](u32 i, u64 v) { dst[i] = v; });
 }
 
 // Plain batched NTT: polynomial blockIdx.x of [n][N], limb = index % L.
-__global__ void k_ntt_plain(u64* __restrict__ a, KP kp, int inverse) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_plain(u64* __restrict__ a, KP kp, int inverse) {
     extern __shared__ u64 sm[];
     const u32 N = kp.N, limb = blockIdx.x % kp.L;
     u64* poly = a + (size_t)blockIdx.x * N;
     const LimbC m = kp.limb[limb];
-    for (u32 x = threadIdx.x; x < N; x += blockDim.x) sm[x] = poly[x];
-    __syncthreads();
-    if (!inverse) {
-        ntt_fwd_smem(sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q);
-        for (u32 x = threadIdx.x; x < N; x += blockDim.x) poly[x] = sm[x];
-    } else {
-        ntt_inv_smem(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q);
-        for (u32 x = threadIdx.x; x < N; x += blockDim.x) poly[x] = shoup(sm[x], m.ninv, m.ninv_sh, m.q);
-    }
+    if (!inverse)
+        ntt_forward_block(sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q,
+                          [&](u32 i) { return poly[i]; }, [&](u32 i, u64 v) { poly[i] = v; });
+    else
+        ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
+                          m.ninv_sh, [&](u32 i) { return poly[i]; }, [&](u32 i, u64 v) { poly[i] = v; });
 }
 
 // Step 4: inverse NTT of ciphertexts.  blockIdx.x = ciphertext, blockIdx.y = polynomial*L + limb.
-__global__ void k_intt(const u64* __restrict__ src, size_t src_ct_stride, u64* __restrict__ dst,
+__global__ void __launch_bounds__(NTT_MAX_THREADS) k_intt(const u64* __restrict__ src, size_t src_ct_stride, u64* __restrict__ dst,
                        size_t dst_ct_stride, KP kp) {
     extern __shared__ u64 sm[];
     const u32 N = kp.N, limb = blockIdx.y % kp.L;
     const u64* s = src + blockIdx.x * src_ct_stride + (size_t)blockIdx.y * N;
     u64* d = dst + blockIdx.x * dst_ct_stride + (size_t)blockIdx.y * N;
     const LimbC m = kp.limb[limb];
-    for (u32 x = threadIdx.x; x < N; x += blockDim.x) sm[x] = s[x];
-    __syncthreads();
-    ntt_inv_smem(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q);
-    for (u32 x = threadIdx.x; x < N; x += blockDim.x) d[x] = shoup(sm[x], m.ninv, m.ninv_sh, m.q);
+    ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
+                      m.ninv_sh, [&](u32 i) { return __ldg(s + i); }, [&](u32 i, u64 v) { d[i] = v; });
 }
 
 // Step 2: hoisted key switch.  Thread = NTT slot x of limb blockIdx.y;
@@ -216,11 +341,16 @@ __global__ void k_keyswitch(const u64* __restrict__ D, u64* __restrict__ R, cons
 // reduced once.  PACKED: rows r = 0, 1 of the Walsh-Hadamard pair and the
 // epilogue out = k*[A0] + [A1] * NTT(P_k); otherwise out = [A0].
 constexpr int MAC_THREADS = 256;
-constexpr int MAC_KC = 256;
+constexpr int MAC_KC = 128;
 
 __device__ __forceinline__ u64 reduce_split(i64 lo, i64 hi, const LimbC& m) {
     i128 a = ((i128)hi << 25) + (i128)lo + ((i128)m.q << 32);
     return bred128((u128)a, m);
+}
+
+// acc += a * b with one 32x32 -> 64-bit signed multiply-add
+__device__ __forceinline__ void mad_wide(i64& acc, int a, int b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
 template <int GT, bool PACKED, bool DW>
@@ -229,49 +359,49 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const u64* __restrict__ R, 
                                                      KP kp, u32 in_groups, u32 out_groups, u32 n_rot, u32 K,
                                                      u64 kmul) {
     constexpr int NR = PACKED ? 2 : 1;
-    __shared__ int16_t ss[GT][NR][MAC_KC];
+    constexpr int NS = GT * NR;            // scalars used per term
+    constexpr int NSP = (NS + 3) & ~3;     // padded to whole int4 loads
+    __shared__ __align__(16) int ss[MAC_KC][NSP];
     const u32 N = kp.N, L = kp.L;
     const u32 x = blockIdx.x * MAC_THREADS + threadIdx.x;
     const u32 g0 = blockIdx.y * GT;
     const u32 z = blockIdx.z, k = z % L, p = (z / L) & 1, ru = z / (2 * L);
     const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
-    i64 lo[GT][NR], hi[GT][NR];
+    i64 lo[NS], hi[NS];
 #pragma unroll
-    for (int g = 0; g < GT; g++)
-#pragma unroll
-        for (int r = 0; r < NR; r++) lo[g][r] = hi[g][r] = 0;
+    for (int i = 0; i < NS; i++) lo[i] = hi[i] = 0;
 
     for (u32 kc0 = 0; kc0 < K; kc0 += MAC_KC) {
         const u32 kcn = min((u32)MAC_KC, K - kc0);
-        for (u32 idx = threadIdx.x; idx < (u32)(GT * NR * MAC_KC); idx += MAC_THREADS) {
-            u32 g = idx / (NR * MAC_KC), r = (idx / MAC_KC) % NR, kk = idx % MAC_KC;
-            int16_t v = 0;
-            if (kk < kcn && g0 + g < out_groups) v = scal[((size_t)(g0 + g) * NR + r) * K + kc0 + kk];
-            ss[g][r][kk] = v;
+        // scalars of this chunk, [term][group * NR + row] as int32
+        for (u32 idx = threadIdx.x; idx < (u32)(MAC_KC * NSP); idx += MAC_THREADS) {
+            u32 kk = idx / NSP, c = idx % NSP, g = c / NR, r = c % NR;
+            int v = 0;
+            if (kk < kcn && c < (u32)NS && g0 + g < out_groups) v = scal[((size_t)(g0 + g) * NR + r) * K + kc0 + kk];
+            ss[kk][c] = v;
         }
         __syncthreads();
         if (x < N) {
+            const u64* base = R + ((size_t)p * L + k) * N + x;
+#pragma unroll 2
             for (u32 kk = 0; kk < kcn; kk++) {
                 const u32 kg = kc0 + kk;
-                u32 ct, rot;
-                if (DW) {
-                    ct = ru * in_groups + g0;
-                    rot = kg;
-                } else {
-                    ct = ru * in_groups + kg / n_rot;
-                    rot = kg % n_rot;
-                }
-                const u64 v = R[((size_t)ct * n_rot + rot) * ctw + ((size_t)p * L + k) * N + x];
+                const u32 ct = DW ? ru * in_groups + g0 : ru * in_groups + kg / n_rot;
+                const u32 rot = DW ? kg : kg % n_rot;
+                const u64 v = __ldg(base + ((size_t)ct * n_rot + rot) * ctw);
                 const int vl = (int)(v & 0x1FFFFFFull), vh = (int)(v >> 25);
+                int sv[NSP];
 #pragma unroll
-                for (int g = 0; g < GT; g++)
+                for (int i = 0; i < NSP; i += 4) {
+                    int4 q4 = *reinterpret_cast<const int4*>(&ss[kk][i]);
+                    sv[i] = q4.x, sv[i + 1] = q4.y, sv[i + 2] = q4.z, sv[i + 3] = q4.w;
+                }
 #pragma unroll
-                    for (int r = 0; r < NR; r++) {
-                        const int s = ss[g][r][kk];
-                        lo[g][r] += (i64)s * vl;
-                        hi[g][r] += (i64)s * vh;
-                    }
+                for (int i = 0; i < NS; i++) {
+                    mad_wide(lo[i], sv[i], vl);
+                    mad_wide(hi[i], sv[i], vh);
+                }
             }
         }
         __syncthreads();
@@ -281,12 +411,235 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const u64* __restrict__ R, 
 #pragma unroll
     for (int g = 0; g < GT; g++) {
         if (g0 + g >= out_groups) break;
-        u64 out = reduce_split(lo[g][0], hi[g][0], m);
+        u64 out = reduce_split(lo[g * NR], hi[g * NR], m);
         if (PACKED) {
-            u64 a1 = reduce_split(lo[g][1], hi[g][1], m);
+            u64 a1 = reduce_split(lo[g * NR + 1], hi[g * NR + 1], m);
             out = addq(mulmod(kmul, out, m), mulmod(a1, pkv, m), m.q);
         }
         OUTN[((size_t)(ru * out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core MAC (tcgen05)
+// The same contraction on the 5th-generation tensor cores.  Per CTA tile:
+//   D_c[n][m] = sum_kk (x_c(n, kk) - 512) * s(m, kk),  c = 0..4,
+// n = 128 NTT slots (MMA M), m = output rows (g, r) (MMA N, <= 96),
+// kk = (input ciphertext, rotation) terms (MMA K), x_c = 10-bit chunk c of the
+// residue.  Operands are fp16 (exact integers), accumulators fp32 in TMEM:
+// |s| <= 16 and |x_c - 512| <= 512 keep every partial sum below 2^24 for
+// K <= 2048 terms, so the fp32 sums are exact integers.  The epilogue forms
+//   A = sum_c 2^(10c) (D_c + 512 S),  S = sum_kk s,
+// (each chunk's sum plus 512 S stays below 2^25), reduces it once mod q_k,
+// and applies the [k,-k] PMult as in k_mac.
+// Shared-memory operands use the no-swizzle K-major canonical layout: 8x16-byte
+// core matrices, LBO = 128 B between core matrices along K, SBO = 1024 B
+// between core matrices along M/N (a 64-term K tile is 8 core matrices wide).
+constexpr int TC_THREADS = 256;
+constexpr int TC_MTILE = 128;     // NTT slots per CTA (MMA M)
+constexpr int TC_KTILE = 64;      // terms per pipeline stage
+constexpr int TC_CHUNKS = 5;      // 10-bit chunks of a residue < 2^50
+constexpr int TC_NMAX = 96;       // output rows per CTA (MMA N <= 96 so 5 N <= 512 TMEM columns)
+constexpr int TC_KMAX = 2048;     // exactness bound on terms for |s| <= 16
+constexpr int TC_SMAX = 16;
+constexpr u32 TC_A_CHUNK_BYTES = TC_MTILE * TC_KTILE * 2;          // 16 KB
+constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 80 KB
+constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 12 KB
+constexpr u32 TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr u32 TC_SMEM_BYTES = 2 * TC_STAGE_BYTES + 64;             // + mbarriers and TMEM address
+constexpr u32 TC_TMEM_COLS = 512;
+constexpr long long TC_SPIN_LIMIT = 1ll << 22;                     // bounded mbarrier waits
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, kk) inside a K-major no-swizzle tile with 64-term rows
+__device__ __forceinline__ u32 kmajor_off(u32 row, u32 kk) {
+    return (row >> 3) * 1024u + (kk >> 3) * 128u + (row & 7u) * 16u + (kk & 7u) * 2u;
+}
+
+__device__ __forceinline__ u64 smem_desc(u32 saddr) {
+    u64 d = 0;
+    d |= (u64)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (u64)(128u >> 4) << 16;                   // leading byte offset (K direction)
+    d |= (u64)(1024u >> 4) << 32;                  // stride byte offset (M/N direction)
+    d |= (u64)1 << 46;                             // fixed 0b001 at bits 46-48
+    return d;                                      // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: D f32, A and B f16, both K-major, N>>3 at 17, M>>4 at 24
+__host__ __device__ constexpr u32 tc_idesc(u32 M, u32 N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
+    for (long long i = 0; i < TC_SPIN_LIMIT; i++) {
+        u32 ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_mac_tc(const u64* __restrict__ R, u64* __restrict__ OUTN, const __half* __restrict__ sc16,
+             const int* __restrict__ bias, const u64* __restrict__ pk, KP kp, u32 in_groups, u32 out_groups,
+             u32 n_rot, u32 K, u32 Kpad, u32 n_rows, u32 rows_per_cta, u64 kmul, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    constexpr int NR = PACKED ? 2 : 1;
+    const u32 N = kp.N, L = kp.L;
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const u32 n0 = blockIdx.x * TC_MTILE;
+    const u32 row0 = blockIdx.y * rows_per_cta;
+    const u32 nrows = min(rows_per_cta, n_rows - row0);          // rows of this CTA (multiple of 16)
+    const u32 z = blockIdx.z, k = z % L, p = (z / L) & 1, ru = z / (2 * L);
+    const LimbC m = kp.limb[k];
+    const size_t ctw = 2ull * L * N;
+    u64* bars = reinterpret_cast<u64*>(tsm + 2 * TC_STAGE_BYTES);
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + 2 * TC_STAGE_BYTES + 32);
+    const u32 bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const u32 tmem = *tmem_slot;
+    const u32 idesc = tc_idesc(TC_MTILE, nrows);
+    const u32 n_tiles = Kpad / TC_KTILE;
+    bool ok = true;
+
+    const u64* Rbase = R + ((size_t)p * L + k) * N + n0;
+    for (u32 t = 0; t < n_tiles; t++) {
+        const u32 st = t & 1;
+        unsigned char* A = tsm + st * TC_STAGE_BYTES;
+        unsigned char* B = A + TC_A_BYTES;
+        if (t >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((t - 2) >> 1) & 1);  // stage free again
+        const u32 kk0 = t * TC_KTILE;
+        // A: thread covers slot nl = tid % 128 and term octets o = tid/128, tid/128 + 2, ...
+        {
+            const u32 nl = tid & (TC_MTILE - 1);
+            for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
+                u64 v[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const u32 kk = kk0 + o * 8 + e;
+                    v[e] = 0;
+                    if (kk < K) {
+                        const u32 ct = ru * in_groups + kk / n_rot, rot = kk % n_rot;
+                        v[e] = __ldg(Rbase + (size_t)(ct * n_rot + rot) * ctw + nl);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < TC_CHUNKS; c++) {
+                    u32 w[4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        // fp16 bits of 1024 + x are 0x6400 | x; subtracting 1536 gives x - 512 exactly
+                        const u32 x0 = 0x6400u | (u32)((v[e] >> (10 * c)) & 0x3FF);
+                        const u32 x1 = 0x6400u | (u32)((v[e + 1] >> (10 * c)) & 0x3FF);
+                        __half2 h = *reinterpret_cast<const __half2*>(&(const u32&)(x0 | (x1 << 16)));
+                        h = __hsub2(h, __float2half2_rn(1536.0f));
+                        w[e / 2] = *reinterpret_cast<u32*>(&h);
+                    }
+                    *reinterpret_cast<uint4*>(A + c * TC_A_CHUNK_BYTES + kmajor_off(nl, o * 8)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+        // B: scalar rows row0.. of this CTA, 64 terms, from the plan's fp16 table [n_rows][Kpad]
+        for (u32 i = tid; i < nrows * (TC_KTILE / 8); i += TC_THREADS) {
+            const u32 r = i / (TC_KTILE / 8), o = i % (TC_KTILE / 8);
+            const uint4 q4 = *reinterpret_cast<const uint4*>(sc16 + (size_t)(row0 + r) * Kpad + kk0 + o * 8);
+            *reinterpret_cast<uint4*>(B + kmajor_off(r, o * 8)) = q4;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const u32 a_base = smem_u32(A), b_base = smem_u32(B);
+#pragma unroll
+            for (int c = 0; c < TC_CHUNKS; c++) {
+#pragma unroll
+                for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                    const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
+                    const u64 bd = smem_desc(b_base + ks * 256);
+                    const u32 acc = (t > 0 || ks > 0) ? 1u : 0u;
+                    const u32 dt = tmem + (u32)(c * nrows);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                st ? bar1 : bar0));
+        }
+    }
+    // wait for the last commit (it covers every earlier MMA of the issuing thread)
+    if (n_tiles > 0 && ok) ok = mbar_wait(((n_tiles - 1) & 1) ? bar1 : bar0, ((n_tiles - 1) >> 1) & 1);
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (slots n0 + 32 (w%4) + lane); the two warp
+    // halves split the 16-column blocks of output rows
+    if (ok) {
+        const u32 sp = warp & 3, half = warp >> 2;
+        const u32 nl = sp * 32 + lane, x = n0 + nl;
+        const u64 pkv = PACKED ? pk[(size_t)k * N + x] : 0;
+        for (u32 cb = half * 16; cb < nrows; cb += 32) {
+            u32 d[TC_CHUNKS][16];
+#pragma unroll
+            for (int c = 0; c < TC_CHUNKS; c++) {
+                const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]), "=r"(d[c][5]),
+                      "=r"(d[c][6]), "=r"(d[c][7]), "=r"(d[c][8]), "=r"(d[c][9]), "=r"(d[c][10]), "=r"(d[c][11]),
+                      "=r"(d[c][12]), "=r"(d[c][13]), "=r"(d[c][14]), "=r"(d[c][15])
+                    : "r"(ta));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            u64 red[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const long long b = bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
+                const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
+                                     (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
+                                     (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
+                const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
+                                     (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
+                const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+                red[j] = bred128((u128)a, m);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j += NR) {
+                const u32 row = row0 + cb + j;
+                const u32 g = row / NR;
+                if (g >= out_groups) continue;
+                u64 out = red[j];
+                if (PACKED) out = addq(mulmod(kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                OUTN[((size_t)(ru * out_groups + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
     }
 }
 
@@ -356,7 +709,7 @@ KP make_kp(const he_params* p) {
     return kp;
 }
 
-u32 ntt_threads(u32 N) { return std::min<u32>(512, N / 2); }
+u32 ntt_threads(u32 N) { return std::min<u32>(NTT_MAX_THREADS, N / NTT_E); }
 
 template <class K>
 void allow_smem(K kernel, size_t bytes) {
@@ -365,7 +718,7 @@ void allow_smem(K kernel, size_t bytes) {
 
 void launch_ntt_plain(const he_params* p, const KP& kp, u64* d, int n, int inverse, cudaStream_t s) {
     if (n <= 0) return;
-    size_t smem = (size_t)p->N * 8;
+    size_t smem = ntt_smem_bytes(p->N);
     allow_smem(k_ntt_plain, smem);
     k_ntt_plain<<<n, ntt_threads(p->N), smem, s>>>(d, kp, inverse);
     check_launch("k_ntt_plain");
@@ -397,7 +750,7 @@ void launch_keyswitch(const he_params* p, const KP& kp, const u64* D, u64* R, co
 void launch_ntt_inputs(const he_params* p, const KP& kp, const u64* in, u64* R, u64* D, u32 n_ct, u32 n_rot,
                        u32 rot_id, cudaStream_t s) {
     if (!n_ct) return;
-    size_t smem = (size_t)p->N * 8;
+    size_t smem = ntt_smem_bytes(p->N);
     allow_smem(k_ntt_inputs, smem);
     dim3 grid(n_ct, 2 * p->L + p->L * p->l * p->L);
     k_ntt_inputs<<<grid, ntt_threads(p->N), smem, s>>>(in, R, D, kp, n_rot, rot_id);
@@ -407,7 +760,7 @@ void launch_ntt_inputs(const he_params* p, const KP& kp, const u64* in, u64* R, 
 void launch_intt(const he_params* p, const KP& kp, const u64* src, size_t src_stride, u64* dst, size_t dst_stride,
                  u32 n_ct, cudaStream_t s) {
     if (!n_ct) return;
-    size_t smem = (size_t)p->N * 8;
+    size_t smem = ntt_smem_bytes(p->N);
     allow_smem(k_intt, smem);
     dim3 grid(n_ct, 2 * p->L);
     k_intt<<<grid, ntt_threads(p->N), smem, s>>>(src, src_stride, dst, dst_stride, kp);
@@ -484,6 +837,11 @@ struct he_plan {
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
     bool packed = false, dw = false;
     u32 mac_groups = 8;
+    bool use_tc = false;
+    u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0;
+    __half* d_sc16 = nullptr;
+    int* d_bias = nullptr;
+    int* d_err = nullptr;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
     int16_t* d_scal = nullptr;
@@ -498,6 +856,9 @@ struct he_plan {
         cudaFree(d_rots);
         cudaFree(d_scal);
         cudaFree(d_pk);
+        cudaFree(d_sc16);
+        cudaFree(d_bias);
+        cudaFree(d_err);
         cudaSetDevice(cur);
     }
 };
@@ -605,6 +966,37 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
         CUDA_OK(cudaStreamSynchronize(s));
         if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
         if (P->dw) P->mac_groups = 1;
+        CUDA_OK(cudaMalloc(&P->d_err, sizeof(int)));
+        CUDA_OK(cudaMemset(P->d_err, 0, sizeof(int)));
+        // tensor-core contraction: exact while |s| <= 16 and K <= 2048 (fp32 sums below 2^24)
+        int max_abs_s = 0;
+        for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
+        const u32 impl = tune ? tune->mac_impl : 0;
+        const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && P->K <= (u32)TC_KMAX;
+        if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, K <= 2048 and a non-depthwise layer");
+        P->use_tc = tc_ok && impl != 1;
+        if (P->use_tc) {
+            const u32 rows = lay.out_groups * NR;
+            P->tc_rows = (rows + 15) / 16 * 16;
+            P->tc_rows_per_cta = std::min<u32>(TC_NMAX, P->tc_rows);
+            P->tc_kpad = (P->K + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
+            std::vector<__half> h16((size_t)P->tc_rows * P->tc_kpad, __float2half(0.0f));
+            std::vector<int> bias(P->tc_rows, 0);
+            for (u32 g = 0; g < lay.out_groups; g++)
+                for (u32 r = 0; r < NR; r++) {
+                    long long S = 0;
+                    for (u32 kk = 0; kk < P->K; kk++) {
+                        int v = sc[((size_t)g * NR + r) * P->K + kk];
+                        h16[(size_t)(g * NR + r) * P->tc_kpad + kk] = __float2half((float)v);
+                        S += v;
+                    }
+                    bias[g * NR + r] = (int)(512 * S);
+                }
+            CUDA_OK(cudaMalloc(&P->d_sc16, h16.size() * sizeof(__half)));
+            CUDA_OK(cudaMemcpy(P->d_sc16, h16.data(), h16.size() * sizeof(__half), cudaMemcpyHostToDevice));
+            CUDA_OK(cudaMalloc(&P->d_bias, bias.size() * sizeof(int)));
+            CUDA_OK(cudaMemcpy(P->d_bias, bias.data(), bias.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
         // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
         const size_t ctw = 2ull * p->L * p->N;
         P->off_R = 0;
@@ -633,8 +1025,22 @@ static void launch_mac_t(const he_plan* P, const u64* R, u64* O, cudaStream_t s)
                                                         P->lay.out_groups, P->n_rot, P->K, P->p->k);
 }
 
+template <bool PACKED>
+static void launch_mac_tc(const he_plan* P, const u64* R, u64* O, cudaStream_t s) {
+    const he_params* p = P->p;
+    allow_smem(k_mac_tc<PACKED>, TC_SMEM_BYTES);
+    dim3 grid(p->N / TC_MTILE, (P->tc_rows + P->tc_rows_per_cta - 1) / P->tc_rows_per_cta, P->lay.row_units * 2 * p->L);
+    k_mac_tc<PACKED><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(R, O, P->d_sc16, P->d_bias, P->d_pk, P->kp,
+                                                              P->lay.in_groups, P->lay.out_groups, P->n_rot, P->K,
+                                                              P->tc_kpad, P->tc_rows, P->tc_rows_per_cta, P->p->k,
+                                                              P->d_err);
+}
+
 static void launch_mac(const he_plan* P, const u64* R, u64* O, cudaStream_t s) {
-    if (P->dw) {
+    if (P->use_tc) {
+        if (P->packed) launch_mac_tc<true>(P, R, O, s);
+        else launch_mac_tc<false>(P, R, O, s);
+    } else if (P->dw) {
         if (P->packed) launch_mac_t<1, true, true>(P, R, O, s);
         else launch_mac_t<1, false, true>(P, R, O, s);
     } else if (P->packed) {
@@ -703,6 +1109,22 @@ extern "C" int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, u
         forward_impl(plan, d_in, d_out, d_ws, s);
         CUDA_OK(cudaMemcpyAsync(h_out, d_out, plan->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
+    });
+}
+
+extern "C" int he_conv_status(const he_plan* plan) {
+    return guard([&] {
+        if (!plan) fail(HE_EINVAL, "null plan");
+        int v = 0;
+        CUDA_OK(cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v) fail(HE_ETIMEOUT, "a bounded device wait in the tensor-core MAC gave up");
+    });
+}
+
+extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
+    return guard([&] {
+        if (!plan || !mac_impl) fail(HE_EINVAL, "null argument");
+        *mac_impl = plan->use_tc ? 2 : 1;
     });
 }
 

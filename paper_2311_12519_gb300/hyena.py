@@ -46,7 +46,7 @@ class he_layout(ctypes.Structure):
 
 
 class he_tune(ctypes.Structure):
-    _fields_ = [("mac_groups", u32), ("reserved", u32 * 7)]
+    _fields_ = [("mac_groups", u32), ("mac_impl", u32), ("reserved", u32 * 6)]
 
 
 class he_stage_times(ctypes.Structure):
@@ -100,6 +100,8 @@ def load(build_if_stale: bool = True):
         "he_conv_forward_host": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp]),
         "he_plan_destroy": (None, [vp]),
         "he_conv_forward_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
+        "he_conv_status": (ctypes.c_int, [vp]),
+        "he_conv_info": (ctypes.c_int, [vp, P(ctypes.c_int)]),
         "he_ntt_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_ntt_inverse": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_rotate_workspace_bytes": (ctypes.c_int, [vp, ctypes.c_int, P(sz)]),
@@ -241,12 +243,22 @@ def he_decrypt_slots(p, sk, ct, N):
 
 
 # ---------------------------------------------------------------------- server
-def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0):
+def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0, mac_impl=0):
     w = np.ascontiguousarray(weights, dtype=np.int32)
-    t = he_tune(mac_groups)
+    t = he_tune(mac_groups, mac_impl)
     h = vp()
     _check(load().he_conv_plan(p, gk, ctypes.byref(d), _ptr(w), ctypes.byref(t), ctypes.byref(h)), "he_conv_plan")
     return h.value
+
+
+def he_conv_status(plan):
+    _check(load().he_conv_status(plan), "he_conv_status")
+
+
+def he_conv_info(plan):
+    v = ctypes.c_int()
+    _check(load().he_conv_info(plan, ctypes.byref(v)), "he_conv_info")
+    return v.value
 
 
 def he_conv_sizes(plan):

@@ -31,8 +31,8 @@ def from_dev(t, shape):
     return t.cpu().numpy().view(np.uint64).reshape(shape)
 
 
-def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0):
-    plan = H.he_conv_plan(p, gk, d, w, mac_groups=mac_groups)
+def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0, mac_impl=0):
+    plan = H.he_conv_plan(p, gk, d, w, mac_groups=mac_groups, mac_impl=mac_impl)
     n_in, n_out, ws = H.he_conv_sizes(plan)
     assert n_in == cts.size
     d_in = to_dev(cts)
@@ -43,6 +43,7 @@ def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0):
     torch.cuda.synchronize()
     assert (from_dev(d_in, cts.shape) == cts).all(), "input modified"
     out = from_dev(d_out, (n_out // (2 * L * N), 2, L, N))
+    H.he_conv_status(plan)
     H.he_plan_destroy(plan)
     return out
 
@@ -63,19 +64,19 @@ class Setup:
                 self._ksk[g] = bfv.galois_key(self.P, self.s, g, synth.SEED_KEYS)
         return self._ksk
 
-    def layer(self, spec, label=0, sample=None, mac_groups=0):
+    def layer(self, spec, label=0, sample=None, mac_groups=0, mac_impl=0, wmax=8):
         N, L = self.N, self.L
         d = H.conv_desc(**spec)
         ol = conv.Layout(N=N, **spec)
         act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), self.P.t, label=label)
         wt = synth.weights((spec["C_out"], 1 if spec["depthwise"] else spec["C_in"], spec["kh"], spec["kh"]),
-                           label=label)
+                           label=label, wmax=wmax)
         gs = H.he_layer_galois(self.p, d)
         gk = H.he_galois_keys(self.p, self.sk, gs, synth.SEED_KEYS)
         cts = H.he_encrypt_image(self.p, self.sk, d, act, synth.SEED_ENC, self.info)
         ref_in = conv.encrypt_image(self.P, ol, self.s, act, synth.SEED_ENC)
         assert (cts == ref_in).all()
-        out = gpu_layer(self.p, gk, d, wt, cts, L, N, mac_groups=mac_groups)
+        out = gpu_layer(self.p, gk, d, wt, cts, L, N, mac_groups=mac_groups, mac_impl=mac_impl)
         ref = conv.he_conv(self.P, ol, wt, ref_in, self.oracle_keys(gs), out_cts=sample)
         idx = range(len(out)) if sample is None else sample
         for c in idx:
@@ -221,3 +222,47 @@ def test_repeat_on_side_stream_and_host_path(small):
                            d_ws.data_ptr())
     assert (h_out.reshape(a.shape) == a).all()
     H.he_plan_destroy(plan)
+
+
+# ---------------------------------------------------------------- both MAC implementations
+@pytest.mark.parametrize("impl", [1, 2])
+@pytest.mark.parametrize("spec", [SMALL[0], SMALL[1], SMALL[4], SMALL[7], SMALL[11]])
+def test_mac_implementations(small, spec, impl):
+    small.layer(spec, mac_impl=impl)
+
+
+def test_tensor_core_mac_is_chosen_when_exact(small):
+    spec = dict(C_in=4, C_out=4, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
+    d = H.conv_desc(**spec)
+    gk = H.he_galois_keys(small.p, small.sk, H.he_layer_galois(small.p, d), synth.SEED_KEYS)
+    for wmax, expect in ((8, 2), (9, 1)):  # |s| = |v0 +- v1| <= 16 is the exactness bound
+        w = np.full((4, 4, 3, 3), wmax)
+        plan = H.he_conv_plan(small.p, gk, d, w)
+        assert H.he_conv_info(plan) == expect
+        H.he_plan_destroy(plan)
+    with pytest.raises(H.HyenaError):
+        H.he_conv_plan(small.p, gk, d, np.full((4, 4, 3, 3), 9), mac_impl=2)
+
+
+def test_tensor_core_mac_at_the_exactness_bound():
+    """K = 2048 terms, every scalar 16 and every chunk at -512: the fp32 sums reach 2^24 exactly.
+    A zero ciphertext makes every rotated residue 0 (all chunks 0 -> -512 after the offset)."""
+    S = Setup(1024, 2, 25)
+    C_in = 2 * (2048 // 18)  # 113 pairs -> K = 2034 <= 2048
+    spec = dict(C_in=C_in, C_out=4, H=2, W=2, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
+    d = H.conv_desc(**spec)
+    gk = H.he_galois_keys(S.p, S.sk, H.he_layer_galois(S.p, d), synth.SEED_KEYS)
+    lay = H.he_layout_for_layer(S.p, d)
+    zero = np.zeros((lay.n_ct_in, 2, 2, 1024), dtype=np.uint64)
+    w = np.full((4, C_in, 3, 3), 8)
+    out_tc = gpu_layer(S.p, gk, d, w, zero, 2, 1024, mac_impl=2)
+    assert (out_tc == 0).all()
+    # and on a real encryption, the tensor-core path equals the CUDA-core path word for word
+    act = synth.activations((1, C_in, 2, 2), S.P.t)
+    cts = H.he_encrypt_image(S.p, S.sk, d, act, synth.SEED_ENC, S.info)
+    w = np.where(synth.weights((4, C_in, 3, 3)) >= 0, 8, -8)
+    a = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=1)
+    b = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=2)
+    assert (a == b).all()
+    dec = H.he_decrypt_image(S.p, S.sk, d, b)
+    assert (dec == conv.conv_plain(act, w, 1, 1, False, S.P.t)).all()

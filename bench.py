@@ -264,7 +264,15 @@ def run_gpu(args, rank, world):
     top = max(stages, key=lambda k: stages[k][0])
     top_ms, top_launches = stages[top]
     per_launch_s = top_ms / 1000 / max(1, top_launches)
-    if top == "mac":
+    mac_tc = all(H.he_conv_info(pl) == 2 for pl in plans)
+    if top == "mac" and mac_tc:
+        # tensor-core contraction: 10 fp16 flops per modMAC would put it at a few % of the tensor roof;
+        # the binding roof is HBM (every rotated residue read once, every output written once)
+        achieved = stage_bytes["mac"] * args.steps / (top_ms / 1000) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "k_mac_tc", "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "tensor_tflops_equiv": 10 * conv_mm * args.steps / (top_ms / 1000) / 1e12}
+    elif top == "mac":
         # CUDA-core integer roof: 2 IMAD.WIDE per modMAC, 64 IMAD lanes per SM per clock issue
         # at half rate for the 64-bit wide form -> 32 wide products per SM per clock
         alu_peak = 152 * 2.07e9 * 32 / 2 / 1e12  # TmodMAC/s

@@ -223,6 +223,30 @@ void he_plan_destroy(he_plan* plan);
 int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in, uint64_t* d_out, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Batched execution of many layers                                    */
+/* ------------------------------------------------------------------ */
+/* Layers whose inputs are already encrypted are independent units of work:
+ * in private inference every layer input is freshly encrypted by the client
+ * (Sec. 2.2), so different layers and images can run together.  A batch runs
+ * each stage (input NTT, key switch, channel MAC, output NTT) of all its
+ * layers in one launch, so small layers fill the GPU; outputs are identical
+ * to he_conv_forward of every plan.  All plans must share one he_params and
+ * one device.  The batch keeps pointers to the plans, which must outlive it. */
+typedef struct he_batch he_batch;
+int he_batch_create(const he_plan* const* plans, int n, he_batch** out);
+/* Device workspace for one he_batch_forward (layers get disjoint regions). */
+int he_batch_workspace_bytes(const he_batch* b, size_t* bytes);
+/* d_in[i], d_out[i]: device buffers of plan i (sizes from he_conv_sizes). */
+int he_batch_forward(const he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_workspace,
+                     void* stream);
+/* The same as a CUDA graph: the first call with a given set of pointers and
+ * stream runs the batch once, captures it and instantiates the graph; later
+ * calls with the same pointers replay it.  Needs a non-default stream. */
+int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_workspace,
+                          void* stream);
+void he_batch_destroy(he_batch* b);
+
+/* ------------------------------------------------------------------ */
 /* Single steps, for tests (device pointers, stream-ordered)          */
 /* ------------------------------------------------------------------ */
 /* In-place negacyclic NTT of n_polys polynomials laid out [n_polys][N];

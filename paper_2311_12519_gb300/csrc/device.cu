@@ -11,6 +11,8 @@
 //                     with 64-bit split accumulators; one reduction per sum;
 //                     epilogue k*A0 + A1 * NTT(P_k) (the [k,-k] PMult)
 //   4. k_intt         inverse NTT to coefficient form
+// Every stage kernel takes a table of layers, so one launch per stage runs a
+// whole batch of layers (he_batch_*); a single layer is a table of one.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -32,6 +34,7 @@ struct LimbC {
 };
 struct KP {
     u32 N, logN, L, l, w;
+    u64 kmul;  // the k of the [k,-k] plaintext
     LimbC limb[HE_MAX_LIMBS];
     const u64* tw;
     const u64* tw_sh;
@@ -236,15 +239,63 @@ __device__ void ntt_inverse_block(u64* sm, u32 N, u32 logN, const u64* itw, cons
 
 __host__ __device__ constexpr size_t ntt_smem_bytes(u32 N) { return ((size_t)N + N / 32) * 8; }
 
-// Step 1: forward NTT of the inputs.  blockIdx.x = ciphertext c; blockIdx.y =
-// job: y < 2L -> polynomial y/L, limb y%L into R[c][rot_id]; otherwise digit
-// dd = (y-2L)/L of c1 lifted into limb (y-2L)%L, into D[c][dd].  Digits are
-// below 2^w <= 2^s < 2q, inside the forward transform's input range.
-__global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_inputs(const u64* __restrict__ in, u64* __restrict__ R, u64* __restrict__ D, KP kp,
-                             u32 n_rot, u32 rot_id) {
+// ------------------------------------------------------------------ batched launches
+// Every stage kernel runs over a table of layers passed by value: block b of a
+// launch belongs to the layer l with start[stage][l] <= b < start[stage][l+1]
+// (binary search; empty layers are skipped) and works on local block
+// b - start[stage][l].  A single layer is a table of one.
+struct LayerDev {
+    const u64* in;             // input ciphertexts [n_ct_in][2][L][N]
+    u64* R;                    // rotated copies [n_ct_in][n_rot][2][L][N], NTT form
+    u64* D;                    // digit NTTs [n_ct_in][L l][L][N]
+    u64* O;                    // NTT-form outputs [n_ct_out][2][L][N]
+    u64* out;                  // output ciphertexts [n_ct_out][2][L][N]
+    const u64* isrc;           // inverse-NTT source (O, or a rotated copy for he_rotate)
+    unsigned long long isrc_stride;  // words between the inverse-NTT source ciphertexts
+    const u64* ksk;            // Galois keys [n_gal][L l][2][L][N], NTT form
+    const RotDev* rots;        // rotations that need a key switch
+    const int16_t* scal;       // CUDA-core MAC scalars [out_groups][c_n][K]
+    const u64* pk;             // NTT(P_k) [L][N]
+    const __half* sc16;        // tensor-core MAC scalars [tc_rows][Kpad]
+    const int* bias;           // tensor-core MAC row offsets 512 sum(s)
+    int* err;                  // bounded-wait status
+    u32 n_ct_in, n_ct_out, n_rot, rot_id, n_ks, K, Kpad, in_groups, out_groups, row_units, tc_rows, tc_rows_per_cta;
+};
+
+enum { ST_NTT = 0, ST_KS = 1, ST_MAC = 2, ST_INTT = 3 };
+
+template <int MAXB>
+struct Batch {
+    u32 n;
+    u32 start[4][MAXB + 1];
+    LayerDev L[MAXB];
+};
+
+template <int MAXB>
+__device__ __forceinline__ u32 find_layer(const Batch<MAXB>& B, int stage, u32 blk) {
+    if (MAXB == 1) return 0;
+    u32 lo = 0, hi = B.n;  // last l with start[l] <= blk
+    while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (B.start[stage][mid] <= blk) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Step 1: forward NTT of the inputs.  Local block = (c, job): job < 2L ->
+// polynomial job/L, limb job%L into R[c][rot_id]; otherwise digit
+// dd = (job-2L)/L of c1 lifted into limb (job-2L)%L, into D[c][dd].  Digits
+// are below 2^w <= 2^s < 2q, inside the forward transform's input range.
+template <int MAXB>
+__global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_inputs(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ u64 sm[];
+    const u32 li = find_layer(B, ST_NTT, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L, l = kp.l;
-    const u32 c = blockIdx.x, y = blockIdx.y;
+    const u32 jobs = 2 * L + L * l * L;
+    const u32 local = blockIdx.x - B.start[ST_NTT][li];
+    const u32 c = local / jobs, y = local % jobs;
     const size_t ctw = 2ull * L * N;
     const u64* src;
     u64* dst;
@@ -252,13 +303,13 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_inputs(const u64* __res
     u64 mask = ~0ull;
     if (y < 2 * L) {
         limb = y % L;
-        src = in + c * ctw + (size_t)y * N;
-        dst = R + ((size_t)c * n_rot + rot_id) * ctw + (size_t)y * N;
+        src = Ly.in + c * ctw + (size_t)y * N;
+        dst = Ly.R + ((size_t)c * Ly.n_rot + Ly.rot_id) * ctw + (size_t)y * N;
     } else {
-        u32 z = y - 2 * L, dd = z / L;
+        const u32 z = y - 2 * L, dd = z / L;
         limb = z % L;
-        src = in + c * ctw + (size_t)(L + dd / l) * N;
-        dst = D + (((size_t)c * L * l + dd) * L + limb) * N;
+        src = Ly.in + c * ctw + (size_t)(L + dd / l) * N;
+        dst = Ly.D + (((size_t)c * L * l + dd) * L + limb) * N;
         shift = kp.w * (dd % l);
         mask = (kp.w >= 64) ? ~0ull : ((1ull << kp.w) - 1);
     }
@@ -283,52 +334,60 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_plain(u64* __restrict__
                           m.ninv_sh, [&](u32 i) { return poly[i]; }, [&](u32 i, u64 v) { poly[i] = v; });
 }
 
-// Step 4: inverse NTT of ciphertexts.  blockIdx.x = ciphertext, blockIdx.y = polynomial*L + limb.
-__global__ void __launch_bounds__(NTT_MAX_THREADS) k_intt(const u64* __restrict__ src, size_t src_ct_stride, u64* __restrict__ dst,
-                       size_t dst_ct_stride, KP kp) {
+// Step 4: inverse NTT of the outputs.  Local block = (ciphertext, polynomial*L + limb).
+template <int MAXB>
+__global__ void __launch_bounds__(NTT_MAX_THREADS) k_intt(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ u64 sm[];
-    const u32 N = kp.N, limb = blockIdx.y % kp.L;
-    const u64* s = src + blockIdx.x * src_ct_stride + (size_t)blockIdx.y * N;
-    u64* d = dst + blockIdx.x * dst_ct_stride + (size_t)blockIdx.y * N;
+    const u32 li = find_layer(B, ST_INTT, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
+    const u32 N = kp.N, L = kp.L;
+    const u32 local = blockIdx.x - B.start[ST_INTT][li];
+    const u32 c = local / (2 * L), y = local % (2 * L), limb = y % L;
+    const u64* s = Ly.isrc + c * Ly.isrc_stride + (size_t)y * N;
+    u64* d = Ly.out + c * (2ull * L * N) + (size_t)y * N;
     const LimbC m = kp.limb[limb];
     ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
                       m.ninv_sh, [&](u32 i) { return __ldg(s + i); }, [&](u32 i, u64 v) { d[i] = v; });
 }
 
-// Step 2: hoisted key switch.  Thread = NTT slot x of limb blockIdx.y;
-// blockIdx.z = rotation.  The NTT slot x holds the evaluation at psi^e with
-// e = 2 rev(x) + 1, so sigma_g reads slot rev((g e mod 2N - 1)/2).
-// The key values of (x, limb) stay in registers across all input ciphertexts.
-template <int LL>
-__global__ void k_keyswitch(const u64* __restrict__ D, u64* __restrict__ R, const u64* __restrict__ ksk,
-                            const RotDev* __restrict__ rots, u32 n_ct, u32 n_rot, u32 rot_id, KP kp) {
+// Step 2: hoisted key switch.  Thread = NTT slot x; local block = (rotation, limb, slot tile).
+// The NTT slot x holds the evaluation at psi^e with e = 2 rev(x) + 1, so
+// sigma_g reads slot rev((g e mod 2N - 1)/2).  The key values of (x, limb)
+// stay in registers across all input ciphertexts of the layer.
+constexpr int KS_THREADS = 256;
+template <int LL, int MAXB>
+__global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant__ Batch<MAXB> B, KP kp) {
+    const u32 li = find_layer(B, ST_KS, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L, logN = kp.logN;
-    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= N) return;
-    const u32 k = blockIdx.y;
-    const RotDev rd = rots[blockIdx.z];
+    const u32 xt_n = N / KS_THREADS;
+    const u32 local = blockIdx.x - B.start[ST_KS][li];
+    const u32 xt = local % xt_n, k = (local / xt_n) % L, r = local / (xt_n * L);
+    const u32 x = xt * KS_THREADS + threadIdx.x;
+    const RotDev rd = Ly.rots[r];
     const LimbC m = kp.limb[k];
     const u32 e = 2 * (__brev(x) >> (32 - logN)) + 1;
     const u32 e2 = (u32)(((u64)e * rd.galois) & (2ull * N - 1));
     const u32 src = __brev((e2 - 1) >> 1) >> (32 - logN);
     u64 k0[LL], k1[LL];
-    const u64* kb = ksk + (size_t)rd.key * LL * 2 * L * N;
+    const u64* kb = Ly.ksk + (size_t)rd.key * LL * 2 * L * N;
 #pragma unroll
     for (int dd = 0; dd < LL; dd++) {
         k0[dd] = kb[(((size_t)dd * 2 + 0) * L + k) * N + x];
         k1[dd] = kb[(((size_t)dd * 2 + 1) * L + k) * N + x];
     }
     const size_t ctw = 2ull * L * N;
-    for (u32 c = 0; c < n_ct; c++) {
-        const u64* Dc = D + (size_t)c * LL * L * N + (size_t)k * N + src;
+    const u32 n_rot = Ly.n_rot, rot_id = Ly.rot_id;
+    for (u32 c = 0; c < Ly.n_ct_in; c++) {
+        const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
         u128 a0 = 0, a1 = 0;
 #pragma unroll
         for (int dd = 0; dd < LL; dd++) {
-            u64 dv = Dc[(size_t)dd * L * N];
+            const u64 dv = Dc[(size_t)dd * L * N];
             a0 += (u128)dv * k0[dd];
             a1 += (u128)dv * k1[dd];
         }
-        u64* Rc = R + (size_t)c * n_rot * ctw;
+        u64* Rc = Ly.R + (size_t)c * n_rot * ctw;
         a0 += Rc[(size_t)rot_id * ctw + (size_t)k * N + src];
         Rc[(size_t)rd.rot * ctw + (size_t)k * N + x] = bred128(a0, m);
         Rc[(size_t)rd.rot * ctw + (size_t)(L + k) * N + x] = bred128(a1, m);
@@ -353,70 +412,71 @@ __device__ __forceinline__ void mad_wide(i64& acc, int a, int b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-template <int GT, bool PACKED, bool DW>
-__global__ void __launch_bounds__(MAC_THREADS) k_mac(const u64* __restrict__ R, u64* __restrict__ OUTN,
-                                                     const int16_t* __restrict__ scal, const u64* __restrict__ pk,
-                                                     KP kp, u32 in_groups, u32 out_groups, u32 n_rot, u32 K,
-                                                     u64 kmul) {
+// Local block = ((row unit, polynomial, limb), slot tile, group tile); the
+// group tile varies fastest so that blocks reading the same residues run together.
+template <int GT, bool PACKED, bool DW, int MAXB>
+__global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Batch<MAXB> B, KP kp) {
     constexpr int NR = PACKED ? 2 : 1;
     constexpr int NS = GT * NR;            // scalars used per term
     constexpr int NSP = (NS + 3) & ~3;     // padded to whole int4 loads
     __shared__ __align__(16) int ss[MAC_KC][NSP];
+    const u32 li = find_layer(B, ST_MAC, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L;
-    const u32 x = blockIdx.x * MAC_THREADS + threadIdx.x;
-    const u32 g0 = blockIdx.y * GT;
-    const u32 z = blockIdx.z, k = z % L, p = (z / L) & 1, ru = z / (2 * L);
+    const u32 gtiles = (Ly.out_groups + GT - 1) / GT, xt_n = N / MAC_THREADS;
+    const u32 local = blockIdx.x - B.start[ST_MAC][li];
+    const u32 gt = local % gtiles, xt = (local / gtiles) % xt_n, z = local / (gtiles * xt_n);
+    const u32 x = xt * MAC_THREADS + threadIdx.x;
+    const u32 g0 = gt * GT;
+    const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
     const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
+    const u32 K = Ly.K, n_rot = Ly.n_rot, in_groups = Ly.in_groups, out_groups = Ly.out_groups;
     i64 lo[NS], hi[NS];
 #pragma unroll
     for (int i = 0; i < NS; i++) lo[i] = hi[i] = 0;
 
     for (u32 kc0 = 0; kc0 < K; kc0 += MAC_KC) {
         const u32 kcn = min((u32)MAC_KC, K - kc0);
-        // scalars of this chunk, [term][group * NR + row] as int32
         for (u32 idx = threadIdx.x; idx < (u32)(MAC_KC * NSP); idx += MAC_THREADS) {
-            u32 kk = idx / NSP, c = idx % NSP, g = c / NR, r = c % NR;
+            const u32 kk = idx / NSP, c = idx % NSP, g = c / NR, r = c % NR;
             int v = 0;
-            if (kk < kcn && c < (u32)NS && g0 + g < out_groups) v = scal[((size_t)(g0 + g) * NR + r) * K + kc0 + kk];
+            if (kk < kcn && c < (u32)NS && g0 + g < out_groups) v = Ly.scal[((size_t)(g0 + g) * NR + r) * K + kc0 + kk];
             ss[kk][c] = v;
         }
         __syncthreads();
-        if (x < N) {
-            const u64* base = R + ((size_t)p * L + k) * N + x;
+        const u64* base = Ly.R + ((size_t)p * L + k) * N + x;
 #pragma unroll 2
-            for (u32 kk = 0; kk < kcn; kk++) {
-                const u32 kg = kc0 + kk;
-                const u32 ct = DW ? ru * in_groups + g0 : ru * in_groups + kg / n_rot;
-                const u32 rot = DW ? kg : kg % n_rot;
-                const u64 v = __ldg(base + ((size_t)ct * n_rot + rot) * ctw);
-                const int vl = (int)(v & 0x1FFFFFFull), vh = (int)(v >> 25);
-                int sv[NSP];
+        for (u32 kk = 0; kk < kcn; kk++) {
+            const u32 kg = kc0 + kk;
+            const u32 ct = DW ? ru * in_groups + g0 : ru * in_groups + kg / n_rot;
+            const u32 rot = DW ? kg : kg % n_rot;
+            const u64 v = __ldg(base + ((size_t)ct * n_rot + rot) * ctw);
+            const int vl = (int)(v & 0x1FFFFFFull), vh = (int)(v >> 25);
+            int sv[NSP];
 #pragma unroll
-                for (int i = 0; i < NSP; i += 4) {
-                    int4 q4 = *reinterpret_cast<const int4*>(&ss[kk][i]);
-                    sv[i] = q4.x, sv[i + 1] = q4.y, sv[i + 2] = q4.z, sv[i + 3] = q4.w;
-                }
+            for (int i = 0; i < NSP; i += 4) {
+                const int4 q4 = *reinterpret_cast<const int4*>(&ss[kk][i]);
+                sv[i] = q4.x, sv[i + 1] = q4.y, sv[i + 2] = q4.z, sv[i + 3] = q4.w;
+            }
 #pragma unroll
-                for (int i = 0; i < NS; i++) {
-                    mad_wide(lo[i], sv[i], vl);
-                    mad_wide(hi[i], sv[i], vh);
-                }
+            for (int i = 0; i < NS; i++) {
+                mad_wide(lo[i], sv[i], vl);
+                mad_wide(hi[i], sv[i], vh);
             }
         }
         __syncthreads();
     }
-    if (x >= N) return;
-    const u64 pkv = PACKED ? pk[(size_t)k * N + x] : 0;
+    const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
 #pragma unroll
     for (int g = 0; g < GT; g++) {
         if (g0 + g >= out_groups) break;
         u64 out = reduce_split(lo[g * NR], hi[g * NR], m);
         if (PACKED) {
-            u64 a1 = reduce_split(lo[g * NR + 1], hi[g * NR + 1], m);
-            out = addq(mulmod(kmul, out, m), mulmod(a1, pkv, m), m.q);
+            const u64 a1 = reduce_split(lo[g * NR + 1], hi[g * NR + 1], m);
+            out = addq(mulmod(kp.kmul, out, m), mulmod(a1, pkv, m), m.q);
         }
-        OUTN[((size_t)(ru * out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
+        Ly.O[((size_t)(ru * out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
     }
 }
 
@@ -483,19 +543,24 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
     return false;
 }
 
-template <bool PACKED>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_mac_tc(const u64* __restrict__ R, u64* __restrict__ OUTN, const __half* __restrict__ sc16,
-             const int* __restrict__ bias, const u64* __restrict__ pk, KP kp, u32 in_groups, u32 out_groups,
-             u32 n_rot, u32 K, u32 Kpad, u32 n_rows, u32 rows_per_cta, u64 kmul, int* __restrict__ err) {
+// Local block = ((row unit, polynomial, limb), slot tile, row tile).
+template <bool PACKED, int MAXB>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
+    const u32 li = find_layer(B, ST_MAC, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const u32 n0 = blockIdx.x * TC_MTILE;
-    const u32 row0 = blockIdx.y * rows_per_cta;
-    const u32 nrows = min(rows_per_cta, n_rows - row0);          // rows of this CTA (multiple of 16)
-    const u32 z = blockIdx.z, k = z % L, p = (z / L) & 1, ru = z / (2 * L);
+    const u32 rows_per_cta = Ly.tc_rows_per_cta, n_rows = Ly.tc_rows, Kpad = Ly.Kpad, K = Ly.K;
+    const u32 mtiles = (n_rows + rows_per_cta - 1) / rows_per_cta, nt_n = N / TC_MTILE;
+    const u32 local = blockIdx.x - B.start[ST_MAC][li];
+    const u32 mt = local % mtiles, nt = (local / mtiles) % nt_n, z = local / (mtiles * nt_n);
+    const u32 n0 = nt * TC_MTILE;
+    const u32 row0 = mt * rows_per_cta;
+    const u32 nrows = min(rows_per_cta, n_rows - row0);  // rows of this CTA (multiple of 16)
+    const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
+    const u32 n_rot = Ly.n_rot, in_groups = Ly.in_groups, out_groups = Ly.out_groups;
     const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
     u64* bars = reinterpret_cast<u64*>(tsm + 2 * TC_STAGE_BYTES);
@@ -520,14 +585,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const u32 n_tiles = Kpad / TC_KTILE;
     bool ok = true;
 
-    const u64* Rbase = R + ((size_t)p * L + k) * N + n0;
+    const u64* Rbase = Ly.R + ((size_t)p * L + k) * N + n0;
     for (u32 t = 0; t < n_tiles; t++) {
         const u32 st = t & 1;
         unsigned char* A = tsm + st * TC_STAGE_BYTES;
-        unsigned char* B = A + TC_A_BYTES;
+        unsigned char* Bs = A + TC_A_BYTES;
         if (t >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((t - 2) >> 1) & 1);  // stage free again
         const u32 kk0 = t * TC_KTILE;
-        // A: thread covers slot nl = tid % 128 and term octets o = tid/128, tid/128 + 2, ...
+        // A: thread covers slot nl = tid % 128 and term octets tid/128, tid/128 + 2, ...
         {
             const u32 nl = tid & (TC_MTILE - 1);
             for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
@@ -549,7 +614,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         // fp16 bits of 1024 + x are 0x6400 | x; subtracting 1536 gives x - 512 exactly
                         const u32 x0 = 0x6400u | (u32)((v[e] >> (10 * c)) & 0x3FF);
                         const u32 x1 = 0x6400u | (u32)((v[e + 1] >> (10 * c)) & 0x3FF);
-                        __half2 h = *reinterpret_cast<const __half2*>(&(const u32&)(x0 | (x1 << 16)));
+                        const u32 packed = x0 | (x1 << 16);
+                        __half2 h = *reinterpret_cast<const __half2*>(&packed);
                         h = __hsub2(h, __float2half2_rn(1536.0f));
                         w[e / 2] = *reinterpret_cast<u32*>(&h);
                     }
@@ -561,15 +627,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // B: scalar rows row0.. of this CTA, 64 terms, from the plan's fp16 table [n_rows][Kpad]
         for (u32 i = tid; i < nrows * (TC_KTILE / 8); i += TC_THREADS) {
             const u32 r = i / (TC_KTILE / 8), o = i % (TC_KTILE / 8);
-            const uint4 q4 = *reinterpret_cast<const uint4*>(sc16 + (size_t)(row0 + r) * Kpad + kk0 + o * 8);
-            *reinterpret_cast<uint4*>(B + kmajor_off(r, o * 8)) = q4;
+            const uint4 q4 = *reinterpret_cast<const uint4*>(Ly.sc16 + (size_t)(row0 + r) * Kpad + kk0 + o * 8);
+            *reinterpret_cast<uint4*>(Bs + kmajor_off(r, o * 8)) = q4;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         if (tid == 0 && ok) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const u32 a_base = smem_u32(A), b_base = smem_u32(B);
+            const u32 a_base = smem_u32(A), b_base = smem_u32(Bs);
 #pragma unroll
             for (int c = 0; c < TC_CHUNKS; c++) {
 #pragma unroll
@@ -590,15 +656,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     // wait for the last commit (it covers every earlier MMA of the issuing thread)
     if (n_tiles > 0 && ok) ok = mbar_wait(((n_tiles - 1) & 1) ? bar1 : bar0, ((n_tiles - 1) >> 1) & 1);
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok && tid == 0) atomicExch(Ly.err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
 
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (slots n0 + 32 (w%4) + lane); the two warp
-    // halves split the 16-column blocks of output rows
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (slot n0 + 32 (w%4) + lane); the two
+    // warp halves take alternate 16-column blocks of output rows
     if (ok) {
         const u32 sp = warp & 3, half = warp >> 2;
         const u32 nl = sp * 32 + lane, x = n0 + nl;
-        const u64 pkv = PACKED ? pk[(size_t)k * N + x] : 0;
+        const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
         for (u32 cb = half * 16; cb < nrows; cb += 32) {
             u32 d[TC_CHUNKS][16];
 #pragma unroll
@@ -615,7 +681,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             u64 red[16];
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const long long b = bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
+                const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
                 const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
                                      (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
                                      (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
@@ -630,8 +696,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const u32 g = row / NR;
                 if (g >= out_groups) continue;
                 u64 out = red[j];
-                if (PACKED) out = addq(mulmod(kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
-                OUTN[((size_t)(ru * out_groups + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
+                if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                Ly.O[((size_t)(ru * out_groups + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
             }
         }
     }
@@ -698,6 +764,7 @@ KP make_kp(const he_params* p) {
     KP kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.N = p->N, kp.logN = p->logN, kp.L = p->L, kp.l = p->l, kp.w = p->w;
+    kp.kmul = p->k;
     for (u32 k = 0; k < p->L; k++) {
         kp.limb[k].q = p->q[k];
         kp.limb[k].mu = p->mod[k].mu;
@@ -724,49 +791,6 @@ void launch_ntt_plain(const he_params* p, const KP& kp, u64* d, int n, int inver
     check_launch("k_ntt_plain");
 }
 
-template <int LL>
-void launch_ks_ll(dim3 grid, cudaStream_t s, const u64* D, u64* R, const u64* ksk, const RotDev* rots, u32 n_ct,
-                  u32 n_rot, u32 rot_id, const KP& kp) {
-    k_keyswitch<LL><<<grid, 256, 0, s>>>(D, R, ksk, rots, n_ct, n_rot, rot_id, kp);
-}
-
-void launch_keyswitch(const he_params* p, const KP& kp, const u64* D, u64* R, const u64* ksk, const RotDev* rots,
-                      u32 n_rots, u32 n_ct, u32 n_rot, u32 rot_id, cudaStream_t s) {
-    if (!n_rots || !n_ct) return;
-    dim3 grid((p->N + 255) / 256, p->L, n_rots);
-    const u32 LL = p->L * p->l;
-    switch (LL) {
-#define KS_CASE(v) \
-    case v: launch_ks_ll<v>(grid, s, D, R, ksk, rots, n_ct, n_rot, rot_id, kp); break;
-        KS_CASE(1) KS_CASE(2) KS_CASE(3) KS_CASE(4) KS_CASE(5) KS_CASE(6) KS_CASE(7) KS_CASE(8) KS_CASE(9)
-            KS_CASE(10) KS_CASE(12) KS_CASE(14) KS_CASE(15) KS_CASE(16)
-#undef KS_CASE
-        default:
-            fail(HE_EINVAL, "L * l must be at most 16 (and not 11 or 13)");
-    }
-    check_launch("k_keyswitch");
-}
-
-void launch_ntt_inputs(const he_params* p, const KP& kp, const u64* in, u64* R, u64* D, u32 n_ct, u32 n_rot,
-                       u32 rot_id, cudaStream_t s) {
-    if (!n_ct) return;
-    size_t smem = ntt_smem_bytes(p->N);
-    allow_smem(k_ntt_inputs, smem);
-    dim3 grid(n_ct, 2 * p->L + p->L * p->l * p->L);
-    k_ntt_inputs<<<grid, ntt_threads(p->N), smem, s>>>(in, R, D, kp, n_rot, rot_id);
-    check_launch("k_ntt_inputs");
-}
-
-void launch_intt(const he_params* p, const KP& kp, const u64* src, size_t src_stride, u64* dst, size_t dst_stride,
-                 u32 n_ct, cudaStream_t s) {
-    if (!n_ct) return;
-    size_t smem = ntt_smem_bytes(p->N);
-    allow_smem(k_intt, smem);
-    dim3 grid(n_ct, 2 * p->L);
-    k_intt<<<grid, ntt_threads(p->N), smem, s>>>(src, src_stride, dst, dst_stride, kp);
-    check_launch("k_intt");
-}
-
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Uploads Galois keys (coefficient form) and converts them to NTT form.
@@ -780,6 +804,169 @@ u64* upload_keys(const he_params* p, const KP& kp, const std::vector<const std::
         CUDA_OK(cudaMemcpyAsync(d + i * per, keys[i]->data(), per * 8, cudaMemcpyHostToDevice, s));
     launch_ntt_plain(p, kp, d, (int)(keys.size() * per / p->N), 0, s);
     return d;
+}
+
+// MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
+struct MacVariant {
+    bool tc = false, packed = false, dw = false;
+    u32 gt = 8;
+    bool operator==(const MacVariant& o) const {
+        return tc == o.tc && packed == o.packed && dw == o.dw && (tc || gt == o.gt);
+    }
+};
+
+struct StageLayer {
+    LayerDev dev;
+    MacVariant mv;
+};
+
+u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
+    const LayerDev& d = s.dev;
+    const u32 L = p->L, N = p->N;
+    switch (stage) {
+        case ST_NTT: return d.n_ct_in * (2 * L + L * p->l * L);
+        case ST_KS: return d.n_ks * L * (N / KS_THREADS);
+        case ST_MAC:
+            if (s.mv.tc) return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta);
+            return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + s.mv.gt - 1) / s.mv.gt);
+        default: return d.n_ct_out * 2 * L;
+    }
+}
+
+template <int LL, int MAXB>
+void ks_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+    k_keyswitch<LL, MAXB><<<blocks, KS_THREADS, 0, s>>>(B, kp);
+}
+
+template <int MAXB>
+void launch_keyswitch_b(const he_params* p, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+    switch (p->L * p->l) {
+#define KS_CASE(v) \
+    case v: ks_launch<v, MAXB>(blocks, B, kp, s); break;
+        KS_CASE(1) KS_CASE(2) KS_CASE(3) KS_CASE(4) KS_CASE(5) KS_CASE(6) KS_CASE(7) KS_CASE(8) KS_CASE(9)
+            KS_CASE(10) KS_CASE(12) KS_CASE(14) KS_CASE(15) KS_CASE(16)
+#undef KS_CASE
+        default:
+            fail(HE_EINVAL, "L * l must be at most 16 (and not 11 or 13)");
+    }
+}
+
+template <int GT, bool PACKED, bool DW, int MAXB>
+void mac_cuda_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+    k_mac<GT, PACKED, DW, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
+}
+
+template <int MAXB>
+void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+    if (mv.tc) {
+        if (mv.packed) {
+            allow_smem(k_mac_tc<true, MAXB>, TC_SMEM_BYTES);
+            k_mac_tc<true, MAXB><<<blocks, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp);
+        } else {
+            allow_smem(k_mac_tc<false, MAXB>, TC_SMEM_BYTES);
+            k_mac_tc<false, MAXB><<<blocks, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp);
+        }
+        return;
+    }
+    if (mv.dw) {
+        if (mv.packed) mac_cuda_launch<1, true, true, MAXB>(blocks, B, kp, s);
+        else mac_cuda_launch<1, false, true, MAXB>(blocks, B, kp, s);
+        return;
+    }
+    if (mv.packed) {
+        switch (mv.gt) {
+            case 1: mac_cuda_launch<1, true, false, MAXB>(blocks, B, kp, s); break;
+            case 2: mac_cuda_launch<2, true, false, MAXB>(blocks, B, kp, s); break;
+            case 4: mac_cuda_launch<4, true, false, MAXB>(blocks, B, kp, s); break;
+            default: mac_cuda_launch<8, true, false, MAXB>(blocks, B, kp, s); break;
+        }
+    } else {
+        switch (mv.gt) {
+            case 1: mac_cuda_launch<1, false, false, MAXB>(blocks, B, kp, s); break;
+            case 2: mac_cuda_launch<2, false, false, MAXB>(blocks, B, kp, s); break;
+            case 4: mac_cuda_launch<4, false, false, MAXB>(blocks, B, kp, s); break;
+            case 8: mac_cuda_launch<8, false, false, MAXB>(blocks, B, kp, s); break;
+            default: mac_cuda_launch<16, false, false, MAXB>(blocks, B, kp, s); break;
+        }
+    }
+}
+
+// Launches one stage over the given layers in tables of at most MAXB layers.
+template <int MAXB>
+void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector<const StageLayer*>& layers,
+                  cudaStream_t s) {
+    for (size_t c0 = 0; c0 < layers.size(); c0 += MAXB) {
+        const u32 n = (u32)std::min<size_t>(MAXB, layers.size() - c0);
+        Batch<MAXB> B;
+        std::memset(&B, 0, sizeof(B));
+        B.n = n;
+        u32 total = 0;
+        for (u32 i = 0; i < n; i++) {
+            B.L[i] = layers[c0 + i]->dev;
+            B.start[stage][i] = total;
+            total += stage_blocks(p, *layers[c0 + i], stage);
+        }
+        B.start[stage][n] = total;
+        if (!total) continue;
+        switch (stage) {
+            case ST_NTT: {
+                const size_t smem = ntt_smem_bytes(p->N);
+                allow_smem(k_ntt_inputs<MAXB>, smem);
+                k_ntt_inputs<MAXB><<<total, ntt_threads(p->N), smem, s>>>(B, kp);
+                check_launch("k_ntt_inputs");
+                break;
+            }
+            case ST_KS:
+                launch_keyswitch_b<MAXB>(p, total, B, kp, s);
+                check_launch("k_keyswitch");
+                break;
+            case ST_MAC:
+                launch_mac_b<MAXB>(layers[c0]->mv, total, B, kp, s);
+                check_launch("k_mac");
+                break;
+            default: {
+                const size_t smem = ntt_smem_bytes(p->N);
+                allow_smem(k_intt<MAXB>, smem);
+                k_intt<MAXB><<<total, ntt_threads(p->N), smem, s>>>(B, kp);
+                check_launch("k_intt");
+            }
+        }
+    }
+}
+
+// Runs the four stages over a list of layers.  Layers of one MAC variant share a launch.
+void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>& layers, cudaStream_t s, bool timed,
+                bool do_mac = true) {
+    std::vector<const StageLayer*> all;
+    for (auto& l : layers) all.push_back(&l);
+    const bool single = layers.size() == 1;
+    auto go = [&](int stage, const std::vector<const StageLayer*>& ls) {
+        if (single) launch_stage<1>(p, kp, stage, ls, s);
+        else launch_stage<32>(p, kp, stage, ls, s);
+    };
+    {
+        StageTimer t(HE_STAGE_NTT_IN, s, timed);
+        go(ST_NTT, all);
+    }
+    {
+        StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
+        go(ST_KS, all);
+    }
+    if (do_mac) {
+        StageTimer t(HE_STAGE_MAC, s, timed);
+        std::vector<bool> done(layers.size(), false);
+        for (size_t i = 0; i < layers.size(); i++) {
+            if (done[i]) continue;
+            std::vector<const StageLayer*> grp;
+            for (size_t j = i; j < layers.size(); j++)
+                if (!done[j] && layers[j].mv == layers[i].mv) grp.push_back(&layers[j]), done[j] = true;
+            go(ST_MAC, grp);
+        }
+    }
+    {
+        StageTimer t(HE_STAGE_NTT_OUT, s, timed);
+        go(ST_INTT, all);
+    }
 }
 
 }  // namespace
@@ -839,13 +1026,13 @@ struct he_plan {
     u32 mac_groups = 8;
     bool use_tc = false;
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0;
-    __half* d_sc16 = nullptr;
-    int* d_bias = nullptr;
-    int* d_err = nullptr;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
     int16_t* d_scal = nullptr;
     u64* d_pk = nullptr;
+    __half* d_sc16 = nullptr;
+    int* d_bias = nullptr;
+    int* d_err = nullptr;
     size_t off_R = 0, off_D = 0, off_O = 0, ws_bytes = 0;
     KP kp{};
     ~he_plan() {
@@ -860,6 +1047,22 @@ struct he_plan {
         cudaFree(d_bias);
         cudaFree(d_err);
         cudaSetDevice(cur);
+    }
+    // the stage-layer descriptor of one call
+    StageLayer stage_layer(const u64* in, u64* out, char* ws) const {
+        StageLayer s;
+        std::memset(&s.dev, 0, sizeof(s.dev));
+        LayerDev& L = s.dev;
+        L.in = in, L.out = out;
+        L.R = (u64*)(ws + off_R), L.D = (u64*)(ws + off_D), L.O = (u64*)(ws + off_O);
+        L.isrc = L.O;
+        L.isrc_stride = 2ull * p->L * p->N;
+        L.ksk = d_ksk, L.rots = d_rots, L.scal = d_scal, L.pk = d_pk, L.sc16 = d_sc16, L.bias = d_bias, L.err = d_err;
+        L.n_ct_in = lay.n_ct_in, L.n_ct_out = lay.n_ct_out, L.n_rot = n_rot, L.rot_id = rot_id, L.n_ks = n_ks;
+        L.K = K, L.Kpad = tc_kpad, L.in_groups = lay.in_groups, L.out_groups = lay.out_groups;
+        L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
+        s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups;
+        return s;
     }
 };
 
@@ -878,7 +1081,6 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
         P->dw = d->depthwise != 0;
         std::vector<RotEntry> rl = rotation_list(p, d, lay);
         P->n_rot = (u32)rl.size();
-        const u32 ndiag = (P->packed && !P->dw) ? 2 : 1;
         const u32 taps = d->kh * d->kh;
         // rotations that need a key switch, grouped by distinct Galois element
         std::vector<u32> gal;
@@ -911,7 +1113,7 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
         const u32 wcin = P->dw ? 1 : d->C_in;
         auto W = [&](u32 o, u32 i, u32 tap) -> i64 {
             if (o >= d->C_out || i >= d->C_in) return 0;
-            if (P->dw) return o == i ? weights[((size_t)o * 1 + 0) * taps + tap] : 0;
+            if (P->dw) return o == i ? weights[(size_t)o * taps + tap] : 0;
             return weights[((size_t)o * wcin + i) * taps + tap];
         };
         double worst0 = 0, worst1 = 0, worst_abs = 0;
@@ -936,9 +1138,16 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             }
             worst0 = std::max(worst0, s0q), worst1 = std::max(worst1, s1q), worst_abs = std::max(worst_abs, sab);
         }
-        (void)ndiag;
         double est = estimate_noise_log2(p, p->w, worst0, worst1, worst_abs, P->packed);
         if (est >= p->log2_delta - 1.0) fail(HE_ENOISE, "estimated noise exceeds Delta/2 for this layer");
+        // tensor-core contraction: exact while |s| <= 16 and K <= 2048 (fp32 sums below 2^24)
+        int max_abs_s = 0;
+        for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
+        const u32 impl = tune ? tune->mac_impl : 0;
+        const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && P->K <= (u32)TC_KMAX;
+        if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, K <= 2048 and a non-depthwise layer");
+        P->use_tc = tc_ok && impl != 1;
+        if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
         // device data
         CUDA_OK(cudaGetDevice(&P->device));
         P->kp = make_kp(p);
@@ -963,18 +1172,8 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             CUDA_OK(cudaMalloc(&P->d_pk, pk.size() * 8));
             CUDA_OK(cudaMemcpy(P->d_pk, pk.data(), pk.size() * 8, cudaMemcpyHostToDevice));
         }
-        CUDA_OK(cudaStreamSynchronize(s));
-        if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
-        if (P->dw) P->mac_groups = 1;
         CUDA_OK(cudaMalloc(&P->d_err, sizeof(int)));
         CUDA_OK(cudaMemset(P->d_err, 0, sizeof(int)));
-        // tensor-core contraction: exact while |s| <= 16 and K <= 2048 (fp32 sums below 2^24)
-        int max_abs_s = 0;
-        for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
-        const u32 impl = tune ? tune->mac_impl : 0;
-        const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && P->K <= (u32)TC_KMAX;
-        if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, K <= 2048 and a non-depthwise layer");
-        P->use_tc = tc_ok && impl != 1;
         if (P->use_tc) {
             const u32 rows = lay.out_groups * NR;
             P->tc_rows = (rows + 15) / 16 * 16;
@@ -997,12 +1196,14 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             CUDA_OK(cudaMalloc(&P->d_bias, bias.size() * sizeof(int)));
             CUDA_OK(cudaMemcpy(P->d_bias, bias.data(), bias.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
+        CUDA_OK(cudaStreamSynchronize(s));
         // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
         const size_t ctw = 2ull * p->L * p->N;
         P->off_R = 0;
         P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->n_rot * ctw * 8);
         P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
         P->ws_bytes = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
+        (void)taps;
         *out = P.release();
     });
 }
@@ -1017,79 +1218,20 @@ extern "C" int he_conv_sizes(const he_plan* plan, size_t* in_words, size_t* out_
     });
 }
 
-template <int GT, bool PACKED, bool DW>
-static void launch_mac_t(const he_plan* P, const u64* R, u64* O, cudaStream_t s) {
-    const he_params* p = P->p;
-    dim3 grid((p->N + MAC_THREADS - 1) / MAC_THREADS, (P->lay.out_groups + GT - 1) / GT, P->lay.row_units * 2 * p->L);
-    k_mac<GT, PACKED, DW><<<grid, MAC_THREADS, 0, s>>>(R, O, P->d_scal, P->d_pk, P->kp, P->lay.in_groups,
-                                                        P->lay.out_groups, P->n_rot, P->K, P->p->k);
+static void check_ptrs(const void* a, const void* b, const void* c) {
+    if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15) fail(HE_EINVAL, "device pointers must be 16-byte aligned");
 }
-
-template <bool PACKED>
-static void launch_mac_tc(const he_plan* P, const u64* R, u64* O, cudaStream_t s) {
-    const he_params* p = P->p;
-    allow_smem(k_mac_tc<PACKED>, TC_SMEM_BYTES);
-    dim3 grid(p->N / TC_MTILE, (P->tc_rows + P->tc_rows_per_cta - 1) / P->tc_rows_per_cta, P->lay.row_units * 2 * p->L);
-    k_mac_tc<PACKED><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(R, O, P->d_sc16, P->d_bias, P->d_pk, P->kp,
-                                                              P->lay.in_groups, P->lay.out_groups, P->n_rot, P->K,
-                                                              P->tc_kpad, P->tc_rows, P->tc_rows_per_cta, P->p->k,
-                                                              P->d_err);
-}
-
-static void launch_mac(const he_plan* P, const u64* R, u64* O, cudaStream_t s) {
-    if (P->use_tc) {
-        if (P->packed) launch_mac_tc<true>(P, R, O, s);
-        else launch_mac_tc<false>(P, R, O, s);
-    } else if (P->dw) {
-        if (P->packed) launch_mac_t<1, true, true>(P, R, O, s);
-        else launch_mac_t<1, false, true>(P, R, O, s);
-    } else if (P->packed) {
-        switch (P->mac_groups) {
-            case 1: launch_mac_t<1, true, false>(P, R, O, s); break;
-            case 2: launch_mac_t<2, true, false>(P, R, O, s); break;
-            case 4: launch_mac_t<4, true, false>(P, R, O, s); break;
-            default: launch_mac_t<8, true, false>(P, R, O, s); break;
-        }
-    } else {
-        switch (P->mac_groups) {
-            case 1: launch_mac_t<1, false, false>(P, R, O, s); break;
-            case 2: launch_mac_t<2, false, false>(P, R, O, s); break;
-            case 4: launch_mac_t<4, false, false>(P, R, O, s); break;
-            case 8: launch_mac_t<8, false, false>(P, R, O, s); break;
-            default: launch_mac_t<16, false, false>(P, R, O, s); break;
-        }
-    }
-    check_launch("k_mac");
+static void check_device(int device) {
+    int dev = -1;
+    CUDA_OK(cudaGetDevice(&dev));
+    if (dev != device) fail(HE_EINVAL, "plan was made on another device");
 }
 
 static void forward_impl(const he_plan* P, const u64* d_in, u64* d_out, void* ws, cudaStream_t s, bool timed = true) {
-    const he_params* p = P->p;
-    if (((uintptr_t)d_in | (uintptr_t)d_out | (uintptr_t)ws) & 15) fail(HE_EINVAL, "device pointers must be 16-byte aligned");
-    int dev = -1;
-    CUDA_OK(cudaGetDevice(&dev));
-    if (dev != P->device) fail(HE_EINVAL, "plan was made on another device");
-    char* base = (char*)ws;
-    u64* R = (u64*)(base + P->off_R);
-    u64* D = (u64*)(base + P->off_D);
-    u64* O = (u64*)(base + P->off_O);
-    const he_layout& lay = P->lay;
-    {
-        StageTimer t(HE_STAGE_NTT_IN, s, timed);
-        launch_ntt_inputs(p, P->kp, d_in, R, D, lay.n_ct_in, P->n_rot, P->rot_id, s);
-    }
-    {
-        StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
-        launch_keyswitch(p, P->kp, D, R, P->d_ksk, P->d_rots, P->n_ks, lay.n_ct_in, P->n_rot, P->rot_id, s);
-    }
-    {
-        StageTimer t(HE_STAGE_MAC, s, timed);
-        launch_mac(P, R, O, s);
-    }
-    {
-        StageTimer t(HE_STAGE_NTT_OUT, s, timed);
-        const size_t ctw = 2ull * p->L * p->N;
-        launch_intt(p, P->kp, O, ctw, d_out, ctw, lay.n_ct_out, s);
-    }
+    check_ptrs(d_in, d_out, ws);
+    check_device(P->device);
+    std::vector<StageLayer> ls{P->stage_layer(d_in, d_out, (char*)ws)};
+    run_layers(P->p, P->kp, ls, s, timed);
 }
 
 extern "C" int he_conv_forward(const he_plan* plan, const uint64_t* d_in, uint64_t* d_out, void* d_ws, void* stream) {
@@ -1129,6 +1271,106 @@ extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
 }
 
 extern "C" void he_plan_destroy(he_plan* plan) { delete plan; }
+
+// ================================================================== batches of layers
+struct he_batch {
+    std::vector<const he_plan*> plans;
+    const he_params* p = nullptr;
+    int device = 0;
+    std::vector<size_t> ws_off;
+    size_t ws_bytes = 0;
+    // captured graph and the pointers it was captured with
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> g_in, g_out;
+    const void* g_ws = nullptr;
+    cudaStream_t g_stream = nullptr;
+    ~he_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    std::vector<StageLayer> layers(const uint64_t* const* d_in, uint64_t* const* d_out, char* ws) const {
+        std::vector<StageLayer> ls;
+        for (size_t i = 0; i < plans.size(); i++) ls.push_back(plans[i]->stage_layer(d_in[i], d_out[i], ws + ws_off[i]));
+        return ls;
+    }
+};
+
+extern "C" int he_batch_create(const he_plan* const* plans, int n, he_batch** out) {
+    return guard([&] {
+        if (!plans || n <= 0 || !out) fail(HE_EINVAL, "bad argument");
+        auto B = std::make_unique<he_batch>();
+        B->p = plans[0]->p;
+        B->device = plans[0]->device;
+        size_t off = 0;
+        for (int i = 0; i < n; i++) {
+            if (!plans[i]) fail(HE_EINVAL, "null plan");
+            if (plans[i]->p != B->p) fail(HE_EINVAL, "all plans of a batch must share their parameters");
+            if (plans[i]->device != B->device) fail(HE_EINVAL, "all plans of a batch must be on one device");
+            B->plans.push_back(plans[i]);
+            B->ws_off.push_back(off);
+            off = align256(off + plans[i]->ws_bytes);
+        }
+        B->ws_bytes = off;
+        *out = B.release();
+    });
+}
+
+extern "C" int he_batch_workspace_bytes(const he_batch* b, size_t* bytes) {
+    return guard([&] {
+        if (!b || !bytes) fail(HE_EINVAL, "null argument");
+        *bytes = b->ws_bytes;
+    });
+}
+
+extern "C" int he_batch_forward(const he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_ws,
+                                void* stream) {
+    return guard([&] {
+        if (!b || !d_in || !d_out || !d_ws) fail(HE_EINVAL, "null argument");
+        check_device(b->device);
+        for (size_t i = 0; i < b->plans.size(); i++) check_ptrs(d_in[i], d_out[i], d_ws);
+        run_layers(b->p, b->plans[0]->kp, b->layers(d_in, d_out, (char*)d_ws), (cudaStream_t)stream, true);
+    });
+}
+
+extern "C" int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_ws,
+                                     void* stream) {
+    return guard([&] {
+        if (!b || !d_in || !d_out || !d_ws || !stream) fail(HE_EINVAL, "graph launches need pointers and a non-default stream");
+        check_device(b->device);
+        cudaStream_t s = (cudaStream_t)stream;
+        bool same = b->exec && b->g_ws == d_ws && b->g_stream == s;
+        for (size_t i = 0; same && i < b->plans.size(); i++) same = b->g_in[i] == d_in[i] && b->g_out[i] == d_out[i];
+        if (!same) {
+            for (size_t i = 0; i < b->plans.size(); i++) check_ptrs(d_in[i], d_out[i], d_ws);
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            std::vector<StageLayer> ls = b->layers(d_in, d_out, (char*)d_ws);
+            // one ordinary pass sets the kernels' attributes before capture
+            run_layers(b->p, b->plans[0]->kp, ls, s, false);
+            cudaGraph_t g = nullptr;
+            CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                run_layers(b->p, b->plans[0]->kp, ls, s, false);
+            } catch (...) {
+                cudaStreamEndCapture(s, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            CUDA_OK(cudaStreamEndCapture(s, &g));
+            cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) fail(HE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            b->g_in.assign(d_in, d_in + b->plans.size());
+            b->g_out.assign(d_out, d_out + b->plans.size());
+            b->g_ws = d_ws;
+            b->g_stream = s;
+        }
+        CUDA_OK(cudaGraphLaunch(b->exec, s));
+    });
+}
+
+extern "C" void he_batch_destroy(he_batch* b) { delete b; }
 
 // ================================================================== allocation-free forward
 // Scratch for he_conv_forward_noalloc.  A file-scope device array: the CUDA
@@ -1205,6 +1447,7 @@ extern "C" int he_rotate(const he_params* p, const he_galkeys* gk, uint32_t galo
         const std::vector<u64>* key = gk->find(galois);
         if (!key) fail(HE_EMISSINGKEY, "missing Galois key");
         if (p->L * p->l > 16) fail(HE_EINVAL, "L * l must be at most 16");
+        check_ptrs(d_in, d_out, d_ws);
         cudaStream_t s = (cudaStream_t)stream;
         KP kp = make_kp(p);
         u64* dkey = upload_keys(p, kp, {key}, s);
@@ -1214,12 +1457,16 @@ extern "C" int he_rotate(const he_params* p, const he_galkeys* gk, uint32_t galo
         CUDA_OK(cudaMemcpyAsync(drot, &rd, sizeof(RotDev), cudaMemcpyHostToDevice, s));
         size_t offD, total;
         rotate_offsets(p, n_ct, &offD, &total);
-        u64* R = (u64*)d_ws;
-        u64* D = (u64*)((char*)d_ws + offD);
-        launch_ntt_inputs(p, kp, d_in, R, D, (u32)n_ct, 2, 0, s);
-        launch_keyswitch(p, kp, D, R, dkey, drot, 1, (u32)n_ct, 2, 0, s);
         const size_t ctw = 2ull * p->L * p->N;
-        launch_intt(p, kp, R + ctw, 2 * ctw, d_out, ctw, (u32)n_ct, s);
+        StageLayer sl;
+        std::memset(&sl.dev, 0, sizeof(sl.dev));
+        LayerDev& L = sl.dev;
+        L.in = d_in, L.out = d_out;
+        L.R = (u64*)d_ws, L.D = (u64*)((char*)d_ws + offD);
+        L.isrc = L.R + ctw, L.isrc_stride = 2 * ctw;  // the rotated copy of every ciphertext
+        L.ksk = dkey, L.rots = drot;
+        L.n_ct_in = (u32)n_ct, L.n_ct_out = (u32)n_ct, L.n_rot = 2, L.rot_id = 0, L.n_ks = 1;
+        run_layers(p, kp, {sl}, s, false, /*do_mac=*/false);
         CUDA_OK(cudaStreamSynchronize(s));
         cudaFree(dkey);
         cudaFree(drot);

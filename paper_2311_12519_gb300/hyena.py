@@ -102,6 +102,11 @@ def load(build_if_stale: bool = True):
         "he_conv_forward_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
         "he_conv_status": (ctypes.c_int, [vp]),
         "he_conv_info": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "he_batch_create": (ctypes.c_int, [vp, ctypes.c_int, P(vp)]),
+        "he_batch_workspace_bytes": (ctypes.c_int, [vp, P(sz)]),
+        "he_batch_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "he_batch_graph_launch": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "he_batch_destroy": (None, [vp]),
         "he_ntt_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_ntt_inverse": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_rotate_workspace_bytes": (ctypes.c_int, [vp, ctypes.c_int, P(sz)]),
@@ -287,6 +292,39 @@ def he_conv_forward_noalloc(plan, d_in, d_out, stream=0):
     """he_conv_forward with the library's static device scratch instead of a
     caller workspace, for callers that cannot allocate device memory."""
     _check(load().he_conv_forward_noalloc(plan, _ptr(d_in), _ptr(d_out), stream or None), "he_conv_forward_noalloc")
+
+
+# ---------------------------------------------------------------------- batches
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[_ptr(x) for x in ptrs])
+    return arr
+
+
+def he_batch_create(plans):
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = vp()
+    _check(load().he_batch_create(arr, len(plans), ctypes.byref(h)), "he_batch_create")
+    return h.value
+
+
+def he_batch_workspace_bytes(b):
+    v = sz()
+    _check(load().he_batch_workspace_bytes(b, ctypes.byref(v)), "he_batch_workspace_bytes")
+    return v.value
+
+
+def he_batch_forward(b, d_ins, d_outs, d_ws, stream=0):
+    a, o = _ptr_array(d_ins), _ptr_array(d_outs)
+    _check(load().he_batch_forward(b, a, o, _ptr(d_ws), stream or None), "he_batch_forward")
+
+
+def he_batch_graph_launch(b, d_ins, d_outs, d_ws, stream):
+    a, o = _ptr_array(d_ins), _ptr_array(d_outs)
+    _check(load().he_batch_graph_launch(b, a, o, _ptr(d_ws), stream or None), "he_batch_graph_launch")
+
+
+def he_batch_destroy(b):
+    load().he_batch_destroy(b)
 
 
 # ---------------------------------------------------------------------- single steps

@@ -266,3 +266,90 @@ def test_tensor_core_mac_at_the_exactness_bound():
     assert (a == b).all()
     dec = H.he_decrypt_image(S.p, S.sk, d, b)
     assert (dec == conv.conv_plain(act, w, 1, 1, False, S.P.t)).all()
+
+
+# ---------------------------------------------------------------- batched execution
+def _plan_and_inputs(S, spec, label, mac_impl=0):
+    d = H.conv_desc(**spec)
+    act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), S.P.t, label=label)
+    wt = synth.weights((spec["C_out"], 1 if spec["depthwise"] else spec["C_in"], spec["kh"], spec["kh"]), label=label)
+    gk = H.he_galois_keys(S.p, S.sk, H.he_layer_galois(S.p, d), synth.SEED_KEYS)
+    plan = H.he_conv_plan(S.p, gk, d, wt, mac_impl=mac_impl)
+    cts = H.he_encrypt_image(S.p, S.sk, d, act, synth.SEED_ENC + label, S.info)
+    return plan, gk, cts
+
+
+def test_batch_equals_single_layers(small):
+    """One launch per stage over mixed layers (packed, unpacked, depthwise, 1x1, both MAC kinds)."""
+    specs = [SMALL[0], SMALL[1], SMALL[2], SMALL[3], SMALL[7], SMALL[11], SMALL[5]]
+    impls = [0, 1, 0, 0, 2, 1, 0]
+    items = [_plan_and_inputs(small, sp, i, impl) for i, (sp, impl) in enumerate(zip(specs, impls))]
+    plans = [it[0] for it in items]
+    refs, d_ins, d_outs = [], [], []
+    for plan, gk, cts in items:
+        n_in, n_out, ws = H.he_conv_sizes(plan)
+        d_in = to_dev(cts)
+        ref = torch.empty(n_out, dtype=torch.int64, device="cuda")
+        d_ws = torch.empty(ws // 8 + 1, dtype=torch.int64, device="cuda")
+        H.he_conv_forward(plan, d_in.data_ptr(), ref.data_ptr(), d_ws.data_ptr())
+        refs.append(ref)
+        d_ins.append(d_in)
+        d_outs.append(torch.full((n_out,), -1, dtype=torch.int64, device="cuda"))
+    b = H.he_batch_create(plans)
+    ws = torch.empty(H.he_batch_workspace_bytes(b) // 8 + 1, dtype=torch.int64, device="cuda")
+    H.he_batch_forward(b, [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr())
+    torch.cuda.synchronize()
+    for i in range(len(plans)):
+        assert torch.equal(d_outs[i], refs[i]), f"layer {i} differs in the batch"
+        d_outs[i].fill_(-1)
+    s = torch.cuda.Stream()
+    for _ in range(2):  # capture, then replay
+        H.he_batch_graph_launch(b, [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(),
+                                s.cuda_stream)
+        s.synchronize()
+        for i in range(len(plans)):
+            assert torch.equal(d_outs[i], refs[i]), f"layer {i} differs in the graph replay"
+            d_outs[i].fill_(-1)
+    H.he_batch_destroy(b)
+    for plan, gk, _ in items:
+        H.he_conv_status(plan)
+        H.he_plan_destroy(plan)
+        H.he_galkeys_destroy(gk)
+
+
+def test_batch_of_resnet20_stack_matches_oracle_samples(resnet):
+    """The whole 19-layer stack in one batch; sampled outputs against the oracle, all decrypted."""
+    shapes = synth.resnet20_convs()
+    specs = [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=3, stride=s.stride, depthwise=False, n_images=1,
+                  c_n=2) for s in shapes]
+    items = [_plan_and_inputs(resnet, sp, i) for i, sp in enumerate(specs)]
+    d_ins, d_outs = [], []
+    for plan, gk, cts in items:
+        n_in, n_out, ws = H.he_conv_sizes(plan)
+        d_ins.append(to_dev(cts))
+        d_outs.append(torch.full((n_out,), -1, dtype=torch.int64, device="cuda"))
+    b = H.he_batch_create([it[0] for it in items])
+    ws = torch.empty(H.he_batch_workspace_bytes(b) // 8 + 1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    H.he_batch_graph_launch(b, [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(),
+                            s.cuda_stream)
+    s.synchronize()
+    for i in (0, 8, 18):  # first layer, a stride-2 layer, the last 64-channel layer
+        plan, gk, cts = items[i]
+        sp = specs[i]
+        out = from_dev(d_outs[i], (-1, 2, 3, 8192))
+        ol = conv.Layout(N=8192, **sp)
+        act = synth.activations((1, sp["C_in"], sp["H"], sp["W"]), resnet.P.t, label=i)
+        wt = synth.weights((sp["C_out"], sp["C_in"], 3, 3), label=i)
+        ref_in = conv.encrypt_image(resnet.P, ol, resnet.s, act, synth.SEED_ENC + i)
+        assert (ref_in == cts).all()
+        ref = conv.he_conv(resnet.P, ol, wt, ref_in,
+                           resnet.oracle_keys(H.he_layer_galois(resnet.p, H.conv_desc(**sp))), out_cts=[0])
+        assert (out[0] == ref[0]).all()
+        dec = H.he_decrypt_image(resnet.p, resnet.sk, H.conv_desc(**sp), out)
+        assert (dec == conv.conv_plain(act, wt, sp["stride"], 1, False, resnet.P.t)).all()
+    H.he_batch_destroy(b)
+    for plan, gk, _ in items:
+        H.he_conv_status(plan)
+        H.he_plan_destroy(plan)
+        H.he_galkeys_destroy(gk)

@@ -259,7 +259,10 @@ struct LayerDev {
     const __half* sc16;        // tensor-core MAC scalars [tc_rows][Kpad]
     const int* bias;           // tensor-core MAC row offsets 512 sum(s)
     int* err;                  // bounded-wait status
+    const uint2* rotinfo;      // per rotation: (Galois element, key index); element 1 = identity
     u32 n_ct_in, n_ct_out, n_rot, rot_id, n_ks, K, Kpad, in_groups, out_groups, row_units, tc_rows, tc_rows_per_cta;
+    u32 tmem_cols;             // TMEM columns of a tensor-core MAC CTA (power of two >= 5 rows)
+    u32 r_slots, r_id;         // rotated copies stored per input ciphertext in R, and the identity's slot
 };
 
 enum { ST_NTT = 0, ST_KS = 1, ST_MAC = 2, ST_INTT = 3 };
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_inputs(const __grid_con
     if (y < 2 * L) {
         limb = y % L;
         src = Ly.in + c * ctw + (size_t)y * N;
-        dst = Ly.R + ((size_t)c * Ly.n_rot + Ly.rot_id) * ctw + (size_t)y * N;
+        dst = Ly.R + ((size_t)c * Ly.r_slots + Ly.r_id) * ctw + (size_t)y * N;
     } else {
         const u32 z = y - 2 * L, dd = z / L;
         limb = z % L;
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
         k1[dd] = kb[(((size_t)dd * 2 + 1) * L + k) * N + x];
     }
     const size_t ctw = 2ull * L * N;
-    const u32 n_rot = Ly.n_rot, rot_id = Ly.rot_id;
+    const u32 r_slots = Ly.r_slots, r_id = Ly.r_id;
     for (u32 c = 0; c < Ly.n_ct_in; c++) {
         const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
         u128 a0 = 0, a1 = 0;
@@ -387,8 +390,8 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             a0 += (u128)dv * k0[dd];
             a1 += (u128)dv * k1[dd];
         }
-        u64* Rc = Ly.R + (size_t)c * n_rot * ctw;
-        a0 += Rc[(size_t)rot_id * ctw + (size_t)k * N + src];
+        u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
+        a0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];
         Rc[(size_t)rd.rot * ctw + (size_t)k * N + x] = bred128(a0, m);
         Rc[(size_t)rd.rot * ctw + (size_t)(L + k) * N + x] = bred128(a1, m);
     }
@@ -481,7 +484,9 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
 }
 
 // ------------------------------------------------------------------ tensor-core MAC (tcgen05)
-// The same contraction on the 5th-generation tensor cores.  Per CTA tile:
+// The same contraction on the 5th-generation tensor cores, with the hoisted
+// key switch fused into its operand producer (so the rotated copies of the
+// inputs never go through HBM).  Per CTA tile:
 //   D_c[n][m] = sum_kk (x_c(n, kk) - 512) * s(m, kk),  c = 0..4,
 // n = 128 NTT slots (MMA M), m = output rows (g, r) (MMA N, <= 96),
 // kk = (input ciphertext, rotation) terms (MMA K), x_c = 10-bit chunk c of the
@@ -492,35 +497,35 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
 // (each chunk's sum plus 512 S stays below 2^25), reduces it once mod q_k,
 // and applies the [k,-k] PMult as in k_mac.
 // Shared-memory operands use the no-swizzle K-major canonical layout: 8x16-byte
-// core matrices, LBO = 128 B between core matrices along K, SBO = 1024 B
-// between core matrices along M/N (a 64-term K tile is 8 core matrices wide).
+// core matrices, LBO = 128 B between core matrices along K, SBO = 512 B
+// between core matrices along M/N (a 32-term K tile is 4 core matrices wide).
 constexpr int TC_THREADS = 256;
 constexpr int TC_MTILE = 128;     // NTT slots per CTA (MMA M)
-constexpr int TC_KTILE = 64;      // terms per pipeline stage
+constexpr int TC_KTILE = 32;      // terms per pipeline stage
 constexpr int TC_CHUNKS = 5;      // 10-bit chunks of a residue < 2^50
 constexpr int TC_NMAX = 96;       // output rows per CTA (MMA N <= 96 so 5 N <= 512 TMEM columns)
 constexpr int TC_KMAX = 2048;     // exactness bound on terms for |s| <= 16
 constexpr int TC_SMAX = 16;
-constexpr u32 TC_A_CHUNK_BYTES = TC_MTILE * TC_KTILE * 2;          // 16 KB
-constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 80 KB
-constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 12 KB
+constexpr u32 TC_A_CHUNK_BYTES = TC_MTILE * TC_KTILE * 2;          // 8 KB
+constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 40 KB
+constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 6 KB
+constexpr u32 TC_SBO = (TC_KTILE / 8) * 128;                       // bytes between 8-row core-matrix blocks
 constexpr u32 TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr u32 TC_SMEM_BYTES = 2 * TC_STAGE_BYTES + 64;             // + mbarriers and TMEM address
-constexpr u32 TC_TMEM_COLS = 512;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;                     // bounded mbarrier waits
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
 
 // byte offset of element (row, kk) inside a K-major no-swizzle tile with 64-term rows
 __device__ __forceinline__ u32 kmajor_off(u32 row, u32 kk) {
-    return (row >> 3) * 1024u + (kk >> 3) * 128u + (row & 7u) * 16u + (kk & 7u) * 2u;
+    return (row >> 3) * TC_SBO + (kk >> 3) * 128u + (row & 7u) * 16u + (kk & 7u) * 2u;
 }
 
 __device__ __forceinline__ u64 smem_desc(u32 saddr) {
     u64 d = 0;
     d |= (u64)((saddr & 0x3FFFFu) >> 4);          // start address
     d |= (u64)(128u >> 4) << 16;                   // leading byte offset (K direction)
-    d |= (u64)(1024u >> 4) << 32;                  // stride byte offset (M/N direction)
+    d |= (u64)(TC_SBO >> 4) << 32;                 // stride byte offset (M/N direction)
     d |= (u64)1 << 46;                             // fixed 0b001 at bits 46-48
     return d;                                      // base offset 0, no swizzle
 }
@@ -545,7 +550,7 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
 
 // Local block = ((row unit, polynomial, limb), slot tile, row tile).
 template <bool PACKED, int MAXB>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
     const u32 li = find_layer(B, ST_MAC, blockIdx.x);
@@ -561,6 +566,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     const u32 nrows = min(rows_per_cta, n_rows - row0);  // rows of this CTA (multiple of 16)
     const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
     const u32 n_rot = Ly.n_rot, in_groups = Ly.in_groups, out_groups = Ly.out_groups;
+    const u32 logN = kp.logN, LLd = L * kp.l;
     const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
     u64* bars = reinterpret_cast<u64*>(tsm + 2 * TC_STAGE_BYTES);
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TC_TMEM_COLS));
+                     "r"(Ly.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -585,16 +591,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     const u32 n_tiles = Kpad / TC_KTILE;
     bool ok = true;
 
-    const u64* Rbase = Ly.R + ((size_t)p * L + k) * N + n0;
     for (u32 t = 0; t < n_tiles; t++) {
         const u32 st = t & 1;
         unsigned char* A = tsm + st * TC_STAGE_BYTES;
         unsigned char* Bs = A + TC_A_BYTES;
         if (t >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((t - 2) >> 1) & 1);  // stage free again
         const u32 kk0 = t * TC_KTILE;
-        // A: thread covers slot nl = tid % 128 and term octets tid/128, tid/128 + 2, ...
+        // A: thread covers slot nl = tid % 128 and term octets tid/128, tid/128 + 2, ...  The
+        // rotated residue of term kk = (input ciphertext j, rotation r) is computed here from the
+        // digit NTTs (hoisted key switch): sum_dd D[dd][pi(x)] * key[dd][p][x] (+ NTT(c0)[pi(x)]
+        // for p = 0), one 128-bit lazy sum and one reduction; the identity rotation is read as is.
         {
             const u32 nl = tid & (TC_MTILE - 1);
+            const u32 x = n0 + nl;
+            const u32 xr = 2 * (__brev(x) >> (32 - logN)) + 1;  // exponent held by slot x
             for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
                 u64 v[8];
 #pragma unroll
@@ -602,8 +612,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                     const u32 kk = kk0 + o * 8 + e;
                     v[e] = 0;
                     if (kk < K) {
-                        const u32 ct = ru * in_groups + kk / n_rot, rot = kk % n_rot;
-                        v[e] = __ldg(Rbase + (size_t)(ct * n_rot + rot) * ctw + nl);
+                        const u32 j = kk / n_rot, rot = kk % n_rot, ct = ru * in_groups + j;
+                        const u64* Rid = Ly.R + ((size_t)ct * Ly.r_slots + Ly.r_id) * ctw;
+                        if (rot == Ly.rot_id) {
+                            v[e] = __ldg(Rid + ((size_t)p * L + k) * N + x);
+                        } else {
+                            const uint2 ri = Ly.rotinfo[rot];
+                            const u32 e2 = (u32)(((u64)xr * ri.x) & (2ull * N - 1));
+                            const u32 src = __brev((e2 - 1) >> 1) >> (32 - logN);
+                            const u64* Dc = Ly.D + ((size_t)ct * LLd * L + k) * N + src;
+                            const u64* kb = Ly.ksk + (((size_t)ri.y * LLd * 2 + p) * L + k) * N + x;
+                            u128 acc = p == 0 ? (u128)__ldg(Rid + (size_t)k * N + src) : (u128)0;
+                            for (u32 dd = 0; dd < LLd; dd++)
+                                acc += (u128)__ldg(Dc + (size_t)dd * L * N) * __ldg(kb + (size_t)dd * 2 * L * N);
+                            v[e] = bred128(acc, m);
+                        }
                     }
                 }
 #pragma unroll
@@ -705,7 +728,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Ly.tmem_cols));
     }
 }
 
@@ -949,8 +972,12 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
         go(ST_NTT, all);
     }
     {
-        StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
-        go(ST_KS, all);
+        // tensor-core layers rotate inside their MAC; the others need the key-switch stage
+        std::vector<const StageLayer*> ks;
+        for (auto& l : layers)
+            if (!l.mv.tc) ks.push_back(&l);
+        StageTimer t(HE_STAGE_KEYSWITCH, s, timed && !ks.empty());
+        if (!ks.empty()) go(ST_KS, ks);
     }
     if (do_mac) {
         StageTimer t(HE_STAGE_MAC, s, timed);
@@ -1033,6 +1060,8 @@ struct he_plan {
     __half* d_sc16 = nullptr;
     int* d_bias = nullptr;
     int* d_err = nullptr;
+    uint2* d_rotinfo = nullptr;
+    u32 tmem_cols = 0, r_slots = 0, r_id = 0;
     size_t off_R = 0, off_D = 0, off_O = 0, ws_bytes = 0;
     KP kp{};
     ~he_plan() {
@@ -1046,6 +1075,7 @@ struct he_plan {
         cudaFree(d_sc16);
         cudaFree(d_bias);
         cudaFree(d_err);
+        cudaFree(d_rotinfo);
         cudaSetDevice(cur);
     }
     // the stage-layer descriptor of one call
@@ -1061,6 +1091,7 @@ struct he_plan {
         L.n_ct_in = lay.n_ct_in, L.n_ct_out = lay.n_ct_out, L.n_rot = n_rot, L.rot_id = rot_id, L.n_ks = n_ks;
         L.K = K, L.Kpad = tc_kpad, L.in_groups = lay.in_groups, L.out_groups = lay.out_groups;
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
+        L.rotinfo = d_rotinfo, L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups;
         return s;
     }
@@ -1196,11 +1227,26 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             CUDA_OK(cudaMalloc(&P->d_bias, bias.size() * sizeof(int)));
             CUDA_OK(cudaMemcpy(P->d_bias, bias.data(), bias.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
+        // (Galois element, key index) of every rotation, for the fused key switch
+        {
+            std::vector<uint2> ri(P->n_rot, make_uint2(1u, 0u));
+            for (const RotDev& r : rots) ri[r.rot] = make_uint2(r.galois, r.key);
+            CUDA_OK(cudaMalloc(&P->d_rotinfo, ri.size() * sizeof(uint2)));
+            CUDA_OK(cudaMemcpy(P->d_rotinfo, ri.data(), ri.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+        }
+        if (P->use_tc) {
+            u32 cols = 32;
+            while (cols < (u32)TC_CHUNKS * P->tc_rows_per_cta) cols <<= 1;
+            P->tmem_cols = cols;
+        }
         CUDA_OK(cudaStreamSynchronize(s));
-        // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
+        // workspace: R [n_ct_in][r_slots][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N];
+        // the tensor-core path keeps only the identity copy in R (it rotates on the fly)
+        P->r_slots = P->use_tc ? 1 : P->n_rot;
+        P->r_id = P->use_tc ? 0 : P->rot_id;
         const size_t ctw = 2ull * p->L * p->N;
         P->off_R = 0;
-        P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->n_rot * ctw * 8);
+        P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);
         P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
         P->ws_bytes = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
         (void)taps;
@@ -1466,6 +1512,7 @@ extern "C" int he_rotate(const he_params* p, const he_galkeys* gk, uint32_t galo
         L.isrc = L.R + ctw, L.isrc_stride = 2 * ctw;  // the rotated copy of every ciphertext
         L.ksk = dkey, L.rots = drot;
         L.n_ct_in = (u32)n_ct, L.n_ct_out = (u32)n_ct, L.n_rot = 2, L.rot_id = 0, L.n_ks = 1;
+        L.r_slots = 2, L.r_id = 0;
         run_layers(p, kp, {sl}, s, false, /*do_mac=*/false);
         CUDA_OK(cudaStreamSynchronize(s));
         cudaFree(dkey);

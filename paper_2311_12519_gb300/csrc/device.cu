@@ -259,7 +259,6 @@ struct LayerDev {
     const __half* sc16;        // tensor-core MAC scalars [tc_rows][Kpad]
     const int* bias;           // tensor-core MAC row offsets 512 sum(s)
     int* err;                  // bounded-wait status
-    const uint2* rotinfo;      // per rotation: (Galois element, key index); element 1 = identity
     u32 n_ct_in, n_ct_out, n_rot, rot_id, n_ks, K, Kpad, in_groups, out_groups, row_units, tc_rows, tc_rows_per_cta;
     u32 tmem_cols;             // TMEM columns of a tensor-core MAC CTA (power of two >= 5 rows)
     u32 r_slots, r_id;         // rotated copies stored per input ciphertext in R, and the identity's slot
@@ -484,9 +483,10 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
 }
 
 // ------------------------------------------------------------------ tensor-core MAC (tcgen05)
-// The same contraction on the 5th-generation tensor cores, with the hoisted
-// key switch fused into its operand producer (so the rotated copies of the
-// inputs never go through HBM).  Per CTA tile:
+// The same contraction on the 5th-generation tensor cores.  Rows of rotated
+// residues stream into shared memory by bulk asynchronous copies (TC_RAW tiles
+// in flight), are split into fp16 chunks by all threads, and feed the MMA,
+// which one thread issues.  Per CTA tile:
 //   D_c[n][m] = sum_kk (x_c(n, kk) - 512) * s(m, kk),  c = 0..4,
 // n = 128 NTT slots (MMA M), m = output rows (g, r) (MMA N, <= 96),
 // kk = (input ciphertext, rotation) terms (MMA K), x_c = 10-bit chunk c of the
@@ -511,7 +511,11 @@ constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 40 KB
 constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 6 KB
 constexpr u32 TC_SBO = (TC_KTILE / 8) * 128;                       // bytes between 8-row core-matrix blocks
 constexpr u32 TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr u32 TC_SMEM_BYTES = 2 * TC_STAGE_BYTES + 64;             // + mbarriers and TMEM address
+constexpr int TC_RAW = 3;                                          // raw residue tiles in flight
+constexpr u32 TC_RAW_BYTES = TC_KTILE * TC_MTILE * 8;              // 32 KB: 32 rows of 128 residues
+constexpr u32 TC_RAW_OFF = 2 * TC_STAGE_BYTES;
+constexpr u32 TC_BAR_OFF = TC_RAW_OFF + TC_RAW * TC_RAW_BYTES;
+constexpr u32 TC_SMEM_BYTES = TC_BAR_OFF + 128;                    // + mbarriers and TMEM address
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;                     // bounded mbarrier waits
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -550,7 +554,7 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
 
 // Local block = ((row unit, polynomial, limb), slot tile, row tile).
 template <bool PACKED, int MAXB>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
     const u32 li = find_layer(B, ST_MAC, blockIdx.x);
@@ -566,16 +570,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mac_tc(const __grid_constant_
     const u32 nrows = min(rows_per_cta, n_rows - row0);  // rows of this CTA (multiple of 16)
     const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
     const u32 n_rot = Ly.n_rot, in_groups = Ly.in_groups, out_groups = Ly.out_groups;
-    const u32 logN = kp.logN, LLd = L * kp.l;
     const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
-    u64* bars = reinterpret_cast<u64*>(tsm + 2 * TC_STAGE_BYTES);
-    u32* tmem_slot = reinterpret_cast<u32*>(tsm + 2 * TC_STAGE_BYTES + 32);
+    u64* bars = reinterpret_cast<u64*>(tsm + TC_BAR_OFF);  // [0,1] MMA stages, [2..] raw slots
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + TC_BAR_OFF + 64);
     const u32 bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    auto rawbar = [&](u32 slot) { return smem_u32(&bars[2 + slot]); };
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
+        for (int i = 0; i < 2 + TC_RAW; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -591,43 +594,46 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mac_tc(const __grid_constant_
     const u32 n_tiles = Kpad / TC_KTILE;
     bool ok = true;
 
+    // rows kk of R for tile tt go to raw slot tt % TC_RAW: one 1 KB bulk copy per term
+    auto issue_tile = [&](u32 tt) {
+        const u32 slot = tt % TC_RAW, kb0 = tt * TC_KTILE;
+        const u32 nv = kb0 < K ? min((u32)TC_KTILE, K - kb0) : 0u;
+        const u32 bar = rawbar(slot);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nv * TC_MTILE * 8u)
+                     : "memory");
+        const u32 dst0 = smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES);
+        for (u32 r = 0; r < nv; r++) {
+            const u32 kk = kb0 + r, ct = ru * in_groups + kk / n_rot, rot = kk % n_rot;
+            const u64* src = Ly.R + ((size_t)ct * Ly.r_slots + rot) * ctw + ((size_t)p * L + k) * N + n0;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst0 + r * TC_MTILE * 8u),
+                "l"(src), "r"(TC_MTILE * 8u), "r"(bar)
+                : "memory");
+        }
+    };
+    if (tid == 0)
+        for (u32 tt = 0; tt + 1 < TC_RAW && tt < n_tiles; tt++) issue_tile(tt);
     for (u32 t = 0; t < n_tiles; t++) {
         const u32 st = t & 1;
         unsigned char* A = tsm + st * TC_STAGE_BYTES;
         unsigned char* Bs = A + TC_A_BYTES;
+        // the raw slot of tile t + TC_RAW - 1 was last read for tile t - 1, before its barrier
+        if (tid == 0 && t + TC_RAW - 1 < n_tiles) issue_tile(t + TC_RAW - 1);
         if (t >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((t - 2) >> 1) & 1);  // stage free again
         const u32 kk0 = t * TC_KTILE;
-        // A: thread covers slot nl = tid % 128 and term octets tid/128, tid/128 + 2, ...  The
-        // rotated residue of term kk = (input ciphertext j, rotation r) is computed here from the
-        // digit NTTs (hoisted key switch): sum_dd D[dd][pi(x)] * key[dd][p][x] (+ NTT(c0)[pi(x)]
-        // for p = 0), one 128-bit lazy sum and one reduction; the identity rotation is read as is.
+        // A: the rows of this tile arrived in raw[t % TC_RAW] by bulk copy; thread covers slot
+        // nl = tid % 128 and term octets tid/128, tid/128 + 2, ...
+        if (ok) ok = mbar_wait(rawbar(t % TC_RAW), (t / TC_RAW) & 1);
         {
             const u32 nl = tid & (TC_MTILE - 1);
-            const u32 x = n0 + nl;
-            const u32 xr = 2 * (__brev(x) >> (32 - logN)) + 1;  // exponent held by slot x
+            const u64* raw = reinterpret_cast<const u64*>(tsm + TC_RAW_OFF + (t % TC_RAW) * TC_RAW_BYTES);
             for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
                 u64 v[8];
 #pragma unroll
                 for (int e = 0; e < 8; e++) {
-                    const u32 kk = kk0 + o * 8 + e;
-                    v[e] = 0;
-                    if (kk < K) {
-                        const u32 j = kk / n_rot, rot = kk % n_rot, ct = ru * in_groups + j;
-                        const u64* Rid = Ly.R + ((size_t)ct * Ly.r_slots + Ly.r_id) * ctw;
-                        if (rot == Ly.rot_id) {
-                            v[e] = __ldg(Rid + ((size_t)p * L + k) * N + x);
-                        } else {
-                            const uint2 ri = Ly.rotinfo[rot];
-                            const u32 e2 = (u32)(((u64)xr * ri.x) & (2ull * N - 1));
-                            const u32 src = __brev((e2 - 1) >> 1) >> (32 - logN);
-                            const u64* Dc = Ly.D + ((size_t)ct * LLd * L + k) * N + src;
-                            const u64* kb = Ly.ksk + (((size_t)ri.y * LLd * 2 + p) * L + k) * N + x;
-                            u128 acc = p == 0 ? (u128)__ldg(Rid + (size_t)k * N + src) : (u128)0;
-                            for (u32 dd = 0; dd < LLd; dd++)
-                                acc += (u128)__ldg(Dc + (size_t)dd * L * N) * __ldg(kb + (size_t)dd * 2 * L * N);
-                            v[e] = bred128(acc, m);
-                        }
-                    }
+                    const u32 r = o * 8 + e;
+                    v[e] = (kk0 + r < K) ? raw[r * TC_MTILE + nl] : 0;
                 }
 #pragma unroll
                 for (int c = 0; c < TC_CHUNKS; c++) {
@@ -972,12 +978,8 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
         go(ST_NTT, all);
     }
     {
-        // tensor-core layers rotate inside their MAC; the others need the key-switch stage
-        std::vector<const StageLayer*> ks;
-        for (auto& l : layers)
-            if (!l.mv.tc) ks.push_back(&l);
-        StageTimer t(HE_STAGE_KEYSWITCH, s, timed && !ks.empty());
-        if (!ks.empty()) go(ST_KS, ks);
+        StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
+        go(ST_KS, all);
     }
     if (do_mac) {
         StageTimer t(HE_STAGE_MAC, s, timed);
@@ -1060,7 +1062,6 @@ struct he_plan {
     __half* d_sc16 = nullptr;
     int* d_bias = nullptr;
     int* d_err = nullptr;
-    uint2* d_rotinfo = nullptr;
     u32 tmem_cols = 0, r_slots = 0, r_id = 0;
     size_t off_R = 0, off_D = 0, off_O = 0, ws_bytes = 0;
     KP kp{};
@@ -1075,7 +1076,6 @@ struct he_plan {
         cudaFree(d_sc16);
         cudaFree(d_bias);
         cudaFree(d_err);
-        cudaFree(d_rotinfo);
         cudaSetDevice(cur);
     }
     // the stage-layer descriptor of one call
@@ -1091,7 +1091,7 @@ struct he_plan {
         L.n_ct_in = lay.n_ct_in, L.n_ct_out = lay.n_ct_out, L.n_rot = n_rot, L.rot_id = rot_id, L.n_ks = n_ks;
         L.K = K, L.Kpad = tc_kpad, L.in_groups = lay.in_groups, L.out_groups = lay.out_groups;
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
-        L.rotinfo = d_rotinfo, L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
+        L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups;
         return s;
     }
@@ -1227,23 +1227,15 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             CUDA_OK(cudaMalloc(&P->d_bias, bias.size() * sizeof(int)));
             CUDA_OK(cudaMemcpy(P->d_bias, bias.data(), bias.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
-        // (Galois element, key index) of every rotation, for the fused key switch
-        {
-            std::vector<uint2> ri(P->n_rot, make_uint2(1u, 0u));
-            for (const RotDev& r : rots) ri[r.rot] = make_uint2(r.galois, r.key);
-            CUDA_OK(cudaMalloc(&P->d_rotinfo, ri.size() * sizeof(uint2)));
-            CUDA_OK(cudaMemcpy(P->d_rotinfo, ri.data(), ri.size() * sizeof(uint2), cudaMemcpyHostToDevice));
-        }
         if (P->use_tc) {
             u32 cols = 32;
             while (cols < (u32)TC_CHUNKS * P->tc_rows_per_cta) cols <<= 1;
             P->tmem_cols = cols;
         }
         CUDA_OK(cudaStreamSynchronize(s));
-        // workspace: R [n_ct_in][r_slots][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N];
-        // the tensor-core path keeps only the identity copy in R (it rotates on the fly)
-        P->r_slots = P->use_tc ? 1 : P->n_rot;
-        P->r_id = P->use_tc ? 0 : P->rot_id;
+        // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
+        P->r_slots = P->n_rot;
+        P->r_id = P->rot_id;
         const size_t ctw = 2ull * p->L * p->N;
         P->off_R = 0;
         P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);

@@ -200,6 +200,17 @@ def run_gpu(args, rank, world):
         in_bytes += n_in * 8
         out_bytes += n_out * 8
     d_ws = torch.empty(ws_max // 8 + 1, dtype=torch.int64, device=dev)
+    if args.mode == "batch":
+        # profiler mode: per step one launch per stage (4 kernels), nothing else on the GPU
+        batch = H.he_batch_create(plans)
+        d_wsb = torch.empty(H.he_batch_workspace_bytes(batch) // 8 + 1, dtype=torch.int64, device=dev)
+        ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
+        torch.cuda.synchronize()
+        for _ in range(args.warmup + args.steps):
+            H.he_batch_forward(batch, ins_p, outs_p, d_wsb.data_ptr(), 0)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "batch", "steps": args.steps, "warmup": args.warmup, "layers": len(plans)}))
+        return
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     n_layers = len(plans)
     sp = stream.cuda_stream
@@ -356,6 +367,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hyena", choices=["hyena", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="full", choices=["full", "batch"],
+                    help="batch: only the batched forward, W + K times, no JSON (for profiler captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

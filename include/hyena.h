@@ -59,7 +59,7 @@ const char* he_last_error(void);
 typedef struct {
     uint32_t N;              /* ring degree, power of two in [1024, 16384] */
     uint32_t L;              /* RNS limbs q_1..q_L, 1 <= L <= HE_MAX_LIMBS */
-    uint32_t limb_bits;      /* q_i are the largest primes < 2^limb_bits, = 1 mod 2N (30..60; 0 -> 50) */
+    uint32_t limb_bits;      /* q_i are the largest primes < 2^limb_bits, = 1 mod 2N (30..54; 0 -> 50) */
     uint32_t t_bits;         /* if t == 0: t = largest prime < 2^t_bits, = 1 mod 2N (0 -> 20) */
     uint64_t t;              /* plaintext modulus p; must be prime and = 1 mod 2N; 0 -> from t_bits */
     uint32_t decomp_bits;    /* key-switching base 2^w; 0 -> largest w whose noise estimate fits */

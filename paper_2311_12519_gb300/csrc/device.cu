@@ -290,7 +290,7 @@ __device__ __forceinline__ u32 find_layer(const Batch<MAXB>& B, int stage, u32 b
 // dd = (job-2L)/L of c1 lifted into limb (job-2L)%L, into D[c][dd].  Digits
 // are below 2^w <= 2^s < 2q, inside the forward transform's input range.
 template <int MAXB>
-__global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_inputs(const __grid_constant__ Batch<MAXB> B, KP kp) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt_inputs(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ u64 sm[];
     const u32 li = find_layer(B, ST_NTT, blockIdx.x);
     const LayerDev& Ly = B.L[li];
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_plain(u64* __restrict__
 
 // Step 4: inverse NTT of the outputs.  Local block = (ciphertext, polynomial*L + limb).
 template <int MAXB>
-__global__ void __launch_bounds__(NTT_MAX_THREADS) k_intt(const __grid_constant__ Batch<MAXB> B, KP kp) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_intt(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ u64 sm[];
     const u32 li = find_layer(B, ST_INTT, blockIdx.x);
     const LayerDev& Ly = B.L[li];
@@ -350,6 +350,11 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_intt(const __grid_constant_
     const LimbC m = kp.limb[limb];
     ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
                       m.ninv_sh, [&](u32 i) { return __ldg(s + i); }, [&](u32 i, u64 v) { d[i] = v; });
+}
+
+// acc += a * b with one unsigned 32x32 -> 64-bit multiply-add
+__device__ __forceinline__ void mad_wide_u(u64& acc, u32 a, u32 b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
 // Step 2: hoisted key switch.  Thread = NTT slot x; local block = (rotation, limb, slot tile).
@@ -371,24 +376,38 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
     const u32 e = 2 * (__brev(x) >> (32 - logN)) + 1;
     const u32 e2 = (u32)(((u64)e * rd.galois) & (2ull * N - 1));
     const u32 src = __brev((e2 - 1) >> 1) >> (32 - logN);
-    u64 k0[LL], k1[LL];
+    // keys split at bit 25, held in registers for all input ciphertexts: a product of two
+    // residues below 2^s is (a1 2^25 + a0)(b1 2^25 + b0), four 32x32 -> 64-bit multiply-adds
+    // into three 64-bit partial sums.  With s <= 54 and at most 16 digit terms the high halves
+    // fit 32 bits and every partial sum stays below 2^64; the recombined sum is below 2^113.
+    u32 k0l[LL], k0h[LL], k1l[LL], k1h[LL];
     const u64* kb = Ly.ksk + (size_t)rd.key * LL * 2 * L * N;
 #pragma unroll
     for (int dd = 0; dd < LL; dd++) {
-        k0[dd] = kb[(((size_t)dd * 2 + 0) * L + k) * N + x];
-        k1[dd] = kb[(((size_t)dd * 2 + 1) * L + k) * N + x];
+        const u64 a = kb[(((size_t)dd * 2 + 0) * L + k) * N + x], b = kb[(((size_t)dd * 2 + 1) * L + k) * N + x];
+        k0l[dd] = (u32)(a & 0x1FFFFFFu), k0h[dd] = (u32)(a >> 25);
+        k1l[dd] = (u32)(b & 0x1FFFFFFu), k1h[dd] = (u32)(b >> 25);
     }
     const size_t ctw = 2ull * L * N;
     const u32 r_slots = Ly.r_slots, r_id = Ly.r_id;
     for (u32 c = 0; c < Ly.n_ct_in; c++) {
         const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
-        u128 a0 = 0, a1 = 0;
+        u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
 #pragma unroll
         for (int dd = 0; dd < LL; dd++) {
             const u64 dv = Dc[(size_t)dd * L * N];
-            a0 += (u128)dv * k0[dd];
-            a1 += (u128)dv * k1[dd];
+            const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+            mad_wide_u(lo0, dl, k0l[dd]);
+            mad_wide_u(mid0, dl, k0h[dd]);
+            mad_wide_u(mid0, dh, k0l[dd]);
+            mad_wide_u(hi0, dh, k0h[dd]);
+            mad_wide_u(lo1, dl, k1l[dd]);
+            mad_wide_u(mid1, dl, k1h[dd]);
+            mad_wide_u(mid1, dh, k1l[dd]);
+            mad_wide_u(hi1, dh, k1h[dd]);
         }
+        u128 a0 = ((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0;
+        u128 a1 = ((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1;
         u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
         a0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];
         Rc[(size_t)rd.rot * ctw + (size_t)k * N + x] = bred128(a0, m);
@@ -594,32 +613,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     const u32 n_tiles = Kpad / TC_KTILE;
     bool ok = true;
 
-    // rows kk of R for tile tt go to raw slot tt % TC_RAW: one 1 KB bulk copy per term
+    // rows kk of R for tile tt go to raw slot tt % TC_RAW: one 1 KB bulk copy per term, lane r of
+    // warp 0 copying row r (TC_KTILE == 32 rows per tile)
     auto issue_tile = [&](u32 tt) {
         const u32 slot = tt % TC_RAW, kb0 = tt * TC_KTILE;
         const u32 nv = kb0 < K ? min((u32)TC_KTILE, K - kb0) : 0u;
         const u32 bar = rawbar(slot);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nv * TC_MTILE * 8u)
-                     : "memory");
-        const u32 dst0 = smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES);
-        for (u32 r = 0; r < nv; r++) {
-            const u32 kk = kb0 + r, ct = ru * in_groups + kk / n_rot, rot = kk % n_rot;
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(nv * TC_MTILE * 8u)
+                         : "memory");
+        __syncwarp();
+        if (lane < nv) {
+            const u32 kk = kb0 + lane, ct = ru * in_groups + kk / n_rot, rot = kk % n_rot;
             const u64* src = Ly.R + ((size_t)ct * Ly.r_slots + rot) * ctw + ((size_t)p * L + k) * N + n0;
+            const u32 dst = smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES) + lane * TC_MTILE * 8u;
             asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    dst0 + r * TC_MTILE * 8u),
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                 "l"(src), "r"(TC_MTILE * 8u), "r"(bar)
                 : "memory");
         }
     };
-    if (tid == 0)
+    static_assert(TC_KTILE == 32, "one lane per row of a tile");
+    if (warp == 0)
         for (u32 tt = 0; tt + 1 < TC_RAW && tt < n_tiles; tt++) issue_tile(tt);
     for (u32 t = 0; t < n_tiles; t++) {
         const u32 st = t & 1;
         unsigned char* A = tsm + st * TC_STAGE_BYTES;
         unsigned char* Bs = A + TC_A_BYTES;
         // the raw slot of tile t + TC_RAW - 1 was last read for tile t - 1, before its barrier
-        if (tid == 0 && t + TC_RAW - 1 < n_tiles) issue_tile(t + TC_RAW - 1);
+        if (warp == 0 && t + TC_RAW - 1 < n_tiles) issue_tile(t + TC_RAW - 1);
         if (t >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((t - 2) >> 1) & 1);  // stage free again
         const u32 kk0 = t * TC_KTILE;
         // A: the rows of this tile arrived in raw[t % TC_RAW] by bulk copy; thread covers slot

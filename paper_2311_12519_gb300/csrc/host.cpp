@@ -409,7 +409,7 @@ extern "C" int he_params_create(const he_param_req* req, he_params** out) {
         if (N < 1024 || N > 16384 || (N & (N - 1))) fail(HE_EINVAL, "N must be a power of two in [1024, 16384]");
         if (req->L < 1 || req->L > HE_MAX_LIMBS) fail(HE_EINVAL, "L out of range");
         u32 lb = req->limb_bits ? req->limb_bits : 50;
-        if (lb < 30 || lb > 58) fail(HE_EINVAL, "limb_bits must be in [30, 58]");
+        if (lb < 30 || lb > 54) fail(HE_EINVAL, "limb_bits must be in [30, 54]");
         auto P = std::make_unique<he_params>();
         P->N = N;
         P->L = req->L;

@@ -571,25 +571,39 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
     return false;
 }
 
-// Local block = ((row unit, polynomial, limb), slot tile, row tile).
+// Persistent: each CTA walks work items blockIdx.x, blockIdx.x + gridDim.x, ... of every layer
+// of the table; an item is ((row unit, polynomial, limb), slot tile, row tile) of one layer.
+// The (item, K tile) pairs of a CTA form one stream with global index g: raw slot g % TC_RAW,
+// MMA stage g % 2.  Warp 0 issues the bulk copies two stream positions ahead, across item
+// boundaries, so the next item's rows load while the current item's epilogue runs.
+struct TcItem {
+    const LayerDev* ly;
+    u32 ru, p, k, n0, row0, nrows, n_tiles;
+};
+
+template <int MAXB>
+__device__ __forceinline__ bool tc_item(const Batch<MAXB>& B, u32 item, u32 N, u32 L, TcItem& it) {
+    if (item >= B.start[ST_MAC][B.n]) return false;
+    const u32 li = find_layer(B, ST_MAC, item);
+    const LayerDev& Ly = B.L[li];
+    const u32 rpc = Ly.tc_rows_per_cta, mtiles = (Ly.tc_rows + rpc - 1) / rpc, nt_n = N / TC_MTILE;
+    const u32 local = item - B.start[ST_MAC][li];
+    const u32 mt = local % mtiles, nt = (local / mtiles) % nt_n, z = local / (mtiles * nt_n);
+    it.ly = &Ly;
+    it.k = z % L, it.p = (z / L) & 1, it.ru = z / (2 * L);
+    it.n0 = nt * TC_MTILE;
+    it.row0 = mt * rpc;
+    it.nrows = min(rpc, Ly.tc_rows - it.row0);
+    it.n_tiles = Ly.Kpad / TC_KTILE;
+    return true;
+}
+
 template <bool PACKED, int MAXB>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp, u32 tmem_cols) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
-    const u32 li = find_layer(B, ST_MAC, blockIdx.x);
-    const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const u32 rows_per_cta = Ly.tc_rows_per_cta, n_rows = Ly.tc_rows, Kpad = Ly.Kpad, K = Ly.K;
-    const u32 mtiles = (n_rows + rows_per_cta - 1) / rows_per_cta, nt_n = N / TC_MTILE;
-    const u32 local = blockIdx.x - B.start[ST_MAC][li];
-    const u32 mt = local % mtiles, nt = (local / mtiles) % nt_n, z = local / (mtiles * nt_n);
-    const u32 n0 = nt * TC_MTILE;
-    const u32 row0 = mt * rows_per_cta;
-    const u32 nrows = min(rows_per_cta, n_rows - row0);  // rows of this CTA (multiple of 16)
-    const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
-    const u32 n_rot = Ly.n_rot, in_groups = Ly.in_groups, out_groups = Ly.out_groups;
-    const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
     u64* bars = reinterpret_cast<u64*>(tsm + TC_BAR_OFF);  // [0,1] MMA stages, [2..] raw slots
     u32* tmem_slot = reinterpret_cast<u32*>(tsm + TC_BAR_OFF + 64);
@@ -602,21 +616,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(Ly.tmem_cols));
+                     "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const u32 tmem = *tmem_slot;
-    const u32 idesc = tc_idesc(TC_MTILE, nrows);
-    const u32 n_tiles = Kpad / TC_KTILE;
     bool ok = true;
 
-    // rows kk of R for tile tt go to raw slot tt % TC_RAW: one 1 KB bulk copy per term, lane r of
-    // warp 0 copying row r (TC_KTILE == 32 rows per tile)
-    auto issue_tile = [&](u32 tt) {
-        const u32 slot = tt % TC_RAW, kb0 = tt * TC_KTILE;
+    // producer cursor (warp 0 only): stream position gp = (item ip, tile tp)
+    TcItem pit;
+    u32 ip = blockIdx.x, tp = 0, gp = 0;
+    bool p_live = tc_item(B, ip, N, L, pit);
+    auto produce_one = [&]() {  // issues the current producer position, then advances it
+        if (!p_live) return;
+        const LayerDev& Ly = *pit.ly;
+        const u32 slot = gp % TC_RAW, kb0 = tp * TC_KTILE, K = Ly.K;
         const u32 nv = kb0 < K ? min((u32)TC_KTILE, K - kb0) : 0u;
         const u32 bar = rawbar(slot);
         if (lane == 0)
@@ -625,139 +641,156 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                          : "memory");
         __syncwarp();
         if (lane < nv) {
-            const u32 kk = kb0 + lane, ct = ru * in_groups + kk / n_rot, rot = kk % n_rot;
-            const u64* src = Ly.R + ((size_t)ct * Ly.r_slots + rot) * ctw + ((size_t)p * L + k) * N + n0;
+            const u32 kk = kb0 + lane, ct = pit.ru * Ly.in_groups + kk / Ly.n_rot, rot = kk % Ly.n_rot;
+            const u64* src = Ly.R + ((size_t)ct * Ly.r_slots + rot) * ctw + ((size_t)pit.p * L + pit.k) * N + pit.n0;
             const u32 dst = smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES) + lane * TC_MTILE * 8u;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                 "l"(src), "r"(TC_MTILE * 8u), "r"(bar)
                 : "memory");
         }
+        gp++;
+        if (++tp == pit.n_tiles) {
+            tp = 0;
+            ip += gridDim.x;
+            p_live = tc_item(B, ip, N, L, pit);
+        }
     };
     static_assert(TC_KTILE == 32, "one lane per row of a tile");
     if (warp == 0)
-        for (u32 tt = 0; tt + 1 < TC_RAW && tt < n_tiles; tt++) issue_tile(tt);
-    for (u32 t = 0; t < n_tiles; t++) {
-        const u32 st = t & 1;
-        unsigned char* A = tsm + st * TC_STAGE_BYTES;
-        unsigned char* Bs = A + TC_A_BYTES;
-        // the raw slot of tile t + TC_RAW - 1 was last read for tile t - 1, before its barrier
-        if (warp == 0 && t + TC_RAW - 1 < n_tiles) issue_tile(t + TC_RAW - 1);
-        if (t >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((t - 2) >> 1) & 1);  // stage free again
-        const u32 kk0 = t * TC_KTILE;
-        // A: the rows of this tile arrived in raw[t % TC_RAW] by bulk copy; thread covers slot
-        // nl = tid % 128 and term octets tid/128, tid/128 + 2, ...
-        if (ok) ok = mbar_wait(rawbar(t % TC_RAW), (t / TC_RAW) & 1);
-        {
-            const u32 nl = tid & (TC_MTILE - 1);
-            const u64* raw = reinterpret_cast<const u64*>(tsm + TC_RAW_OFF + (t % TC_RAW) * TC_RAW_BYTES);
-            for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
-                u64 v[8];
+        for (int i = 0; i < TC_RAW - 1; i++) produce_one();
+
+    u32 g = 0;  // consumer stream position
+    TcItem it;
+    for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+        const LayerDev& Ly = *it.ly;
+        const u32 K = Ly.K, Kpad = Ly.Kpad, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
+        const u32 out_groups = Ly.out_groups;
+        const LimbC m = kp.limb[k];
+        const u32 idesc = tc_idesc(TC_MTILE, nrows);
+        for (u32 t = 0; t < it.n_tiles; t++, g++) {
+            const u32 st = g & 1;
+            unsigned char* A = tsm + st * TC_STAGE_BYTES;
+            unsigned char* Bs = A + TC_A_BYTES;
+            // keep the copies two positions ahead; raw slot (g + 2) % 3 was last read at g - 1
+            if (warp == 0 && __all_sync(0xffffffffu, ok)) produce_one();
+            if (g >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((g - 2) >> 1) & 1);  // MMA stage free again
+            const u32 kk0 = t * TC_KTILE;
+            if (ok) ok = mbar_wait(rawbar(g % TC_RAW), (g / TC_RAW) & 1);
+            {
+                const u32 nl = tid & (TC_MTILE - 1);
+                const u64* raw = reinterpret_cast<const u64*>(tsm + TC_RAW_OFF + (g % TC_RAW) * TC_RAW_BYTES);
+                for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
+                    u64 v[8];
 #pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    const u32 r = o * 8 + e;
-                    v[e] = (kk0 + r < K) ? raw[r * TC_MTILE + nl] : 0;
+                    for (int e = 0; e < 8; e++) {
+                        const u32 r = o * 8 + e;
+                        v[e] = (kk0 + r < K) ? raw[r * TC_MTILE + nl] : 0;
+                    }
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+                        u32 w[4];
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            // fp16 bits of 1024 + x are 0x6400 | x; subtracting 1536 gives x - 512 exactly
+                            const u32 x0 = 0x6400u | (u32)((v[e] >> (10 * c)) & 0x3FF);
+                            const u32 x1 = 0x6400u | (u32)((v[e + 1] >> (10 * c)) & 0x3FF);
+                            const u32 packed = x0 | (x1 << 16);
+                            __half2 h = *reinterpret_cast<const __half2*>(&packed);
+                            h = __hsub2(h, __float2half2_rn(1536.0f));
+                            w[e / 2] = *reinterpret_cast<u32*>(&h);
+                        }
+                        *reinterpret_cast<uint4*>(A + c * TC_A_CHUNK_BYTES + kmajor_off(nl, o * 8)) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
                 }
+            }
+            // B: scalar rows row0.. of this item, 32 terms, from the plan's fp16 table [rows][Kpad]
+            for (u32 i = tid; i < nrows * (TC_KTILE / 8); i += TC_THREADS) {
+                const u32 r = i / (TC_KTILE / 8), o = i % (TC_KTILE / 8);
+                const uint4 q4 = *reinterpret_cast<const uint4*>(Ly.sc16 + (size_t)(row0 + r) * Kpad + kk0 + o * 8);
+                *reinterpret_cast<uint4*>(Bs + kmajor_off(r, o * 8)) = q4;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            if (tid == 0 && ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const u32 a_base = smem_u32(A), b_base = smem_u32(Bs);
 #pragma unroll
                 for (int c = 0; c < TC_CHUNKS; c++) {
-                    u32 w[4];
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        // fp16 bits of 1024 + x are 0x6400 | x; subtracting 1536 gives x - 512 exactly
-                        const u32 x0 = 0x6400u | (u32)((v[e] >> (10 * c)) & 0x3FF);
-                        const u32 x1 = 0x6400u | (u32)((v[e + 1] >> (10 * c)) & 0x3FF);
-                        const u32 packed = x0 | (x1 << 16);
-                        __half2 h = *reinterpret_cast<const __half2*>(&packed);
-                        h = __hsub2(h, __float2half2_rn(1536.0f));
-                        w[e / 2] = *reinterpret_cast<u32*>(&h);
+                    for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                        const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
+                        const u64 bd = smem_desc(b_base + ks * 256);
+                        const u32 acc = (t > 0 || ks > 0) ? 1u : 0u;
+                        const u32 dt = tmem + (u32)(c * nrows);
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                     }
-                    *reinterpret_cast<uint4*>(A + c * TC_A_CHUNK_BYTES + kmajor_off(nl, o * 8)) =
-                        make_uint4(w[0], w[1], w[2], w[3]);
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    st ? bar1 : bar0));
             }
         }
-        // B: scalar rows row0.. of this CTA, 64 terms, from the plan's fp16 table [n_rows][Kpad]
-        for (u32 i = tid; i < nrows * (TC_KTILE / 8); i += TC_THREADS) {
-            const u32 r = i / (TC_KTILE / 8), o = i % (TC_KTILE / 8);
-            const uint4 q4 = *reinterpret_cast<const uint4*>(Ly.sc16 + (size_t)(row0 + r) * Kpad + kk0 + o * 8);
-            *reinterpret_cast<uint4*>(Bs + kmajor_off(r, o * 8)) = q4;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (tid == 0 && ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const u32 a_base = smem_u32(A), b_base = smem_u32(Bs);
+        // the last commit of this item covers all of its MMAs
+        const u32 gl = g - 1;
+        if (ok) ok = mbar_wait((gl & 1) ? bar1 : bar0, (gl >> 1) & 1);
+        if (!ok && tid == 0) atomicExch(Ly.err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (slot n0 + 32 (w%4) + lane); the two
+        // warp halves take alternate 16-column blocks of output rows
+        if (ok) {
+            const u32 sp = warp & 3, half = warp >> 2;
+            const u32 nl = sp * 32 + lane, x = it.n0 + nl;
+            const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+            for (u32 cb = half * 16; cb < nrows; cb += 32) {
+                u32 d[TC_CHUNKS][16];
 #pragma unroll
-            for (int c = 0; c < TC_CHUNKS; c++) {
-#pragma unroll
-                for (int ks = 0; ks < TC_KTILE / 16; ks++) {
-                    const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
-                    const u64 bd = smem_desc(b_base + ks * 256);
-                    const u32 acc = (t > 0 || ks > 0) ? 1u : 0u;
-                    const u32 dt = tmem + (u32)(c * nrows);
+                for (int c = 0; c < TC_CHUNKS; c++) {
+                    const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
                     asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]), "=r"(d[c][5]),
+                          "=r"(d[c][6]), "=r"(d[c][7]), "=r"(d[c][8]), "=r"(d[c][9]), "=r"(d[c][10]),
+                          "=r"(d[c][11]), "=r"(d[c][12]), "=r"(d[c][13]), "=r"(d[c][14]), "=r"(d[c][15])
+                        : "r"(ta));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                u64 red[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
+                    const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
+                                         (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
+                                         (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
+                    const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
+                                         (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
+                    const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+                    red[j] = bred128((u128)a, m);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j += NR) {
+                    const u32 row = row0 + cb + j;
+                    const u32 gg = row / NR;
+                    if (gg >= out_groups) continue;
+                    u64 out = red[j];
+                    if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                    Ly.O[((size_t)(it.ru * out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x] = out;
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                st ? bar1 : bar0));
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");  // TMEM reads done before the next item's MMAs
     }
-    // wait for the last commit (it covers every earlier MMA of the issuing thread)
-    if (n_tiles > 0 && ok) ok = mbar_wait(((n_tiles - 1) & 1) ? bar1 : bar0, ((n_tiles - 1) >> 1) & 1);
-    if (!ok && tid == 0) atomicExch(Ly.err, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (slot n0 + 32 (w%4) + lane); the two
-    // warp halves take alternate 16-column blocks of output rows
-    if (ok) {
-        const u32 sp = warp & 3, half = warp >> 2;
-        const u32 nl = sp * 32 + lane, x = n0 + nl;
-        const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
-        for (u32 cb = half * 16; cb < nrows; cb += 32) {
-            u32 d[TC_CHUNKS][16];
-#pragma unroll
-            for (int c = 0; c < TC_CHUNKS; c++) {
-                const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]), "=r"(d[c][5]),
-                      "=r"(d[c][6]), "=r"(d[c][7]), "=r"(d[c][8]), "=r"(d[c][9]), "=r"(d[c][10]), "=r"(d[c][11]),
-                      "=r"(d[c][12]), "=r"(d[c][13]), "=r"(d[c][14]), "=r"(d[c][15])
-                    : "r"(ta));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            u64 red[16];
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
-                const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
-                                     (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
-                                     (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
-                const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
-                                     (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
-                const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
-                red[j] = bred128((u128)a, m);
-            }
-#pragma unroll
-            for (int j = 0; j < 16; j += NR) {
-                const u32 row = row0 + cb + j;
-                const u32 g = row / NR;
-                if (g >= out_groups) continue;
-                u64 out = red[j];
-                if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
-                Ly.O[((size_t)(ru * out_groups + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    // after a timed-out wait, let copies that were issued but not consumed land (bounded) before exit
+    if (warp == 0)
+        for (u32 q = g; q < gp; q++) mbar_wait(rawbar(q % TC_RAW), (q / TC_RAW) & 1);
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Ly.tmem_cols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
     }
 }
 
@@ -829,6 +862,13 @@ KP make_kp(const he_params* p) {
 }
 
 u32 ntt_threads(u32 N) { return std::min<u32>(NTT_MAX_THREADS, N / NTT_E); }
+
+int sm_count() {
+    int dev = 0, n = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    CUDA_OK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(n, 1);
+}
 
 template <class K>
 void allow_smem(K kernel, size_t bytes) {
@@ -911,12 +951,16 @@ void mac_cuda_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_
 template <int MAXB>
 void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
     if (mv.tc) {
+        // persistent: one CTA per SM (the shared-memory footprint allows one), TMEM for the widest layer
+        u32 cols = 32;
+        for (u32 i = 0; i < B.n; i++) cols = std::max(cols, B.L[i].tmem_cols);
+        const u32 grid = std::min(blocks, (u32)sm_count());
         if (mv.packed) {
             allow_smem(k_mac_tc<true, MAXB>, TC_SMEM_BYTES);
-            k_mac_tc<true, MAXB><<<blocks, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp);
+            k_mac_tc<true, MAXB><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp, cols);
         } else {
             allow_smem(k_mac_tc<false, MAXB>, TC_SMEM_BYTES);
-            k_mac_tc<false, MAXB><<<blocks, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp);
+            k_mac_tc<false, MAXB><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp, cols);
         }
         return;
     }

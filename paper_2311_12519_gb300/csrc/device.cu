@@ -13,8 +13,10 @@
 //   4. k_intt         inverse NTT to coefficient form
 // Every stage kernel takes a table of layers, so one launch per stage runs a
 // whole batch of layers (he_batch_*); a single layer is a table of one.
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstring>
@@ -245,6 +247,7 @@ __host__ __device__ constexpr size_t ntt_smem_bytes(u32 N) { return ((size_t)N +
 // (binary search; empty layers are skipped) and works on local block
 // b - start[stage][l].  A single layer is a table of one.
 struct LayerDev {
+    CUtensorMap rmap;          // R as a 3-D tensor (slot, polynomial*L + limb, row = ct*n_rot + rot), tensor-core MAC
     const u64* in;             // input ciphertexts [n_ct_in][2][L][N]
     u64* R;                    // rotated copies [n_ct_in][n_rot][2][L][N], NTT form
     u64* D;                    // digit NTTs [n_ct_in][L l][L][N]
@@ -604,7 +607,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     constexpr int NR = PACKED ? 2 : 1;
     const u32 N = kp.N, L = kp.L;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const size_t ctw = 2ull * L * N;
     u64* bars = reinterpret_cast<u64*>(tsm + TC_BAR_OFF);  // [0,1] MMA stages, [2..] raw slots
     u32* tmem_slot = reinterpret_cast<u32*>(tsm + TC_BAR_OFF + 64);
     const u32 bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
@@ -632,21 +634,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     auto produce_one = [&]() {  // issues the current producer position, then advances it
         if (!p_live) return;
         const LayerDev& Ly = *pit.ly;
-        const u32 slot = gp % TC_RAW, kb0 = tp * TC_KTILE, K = Ly.K;
-        const u32 nv = kb0 < K ? min((u32)TC_KTILE, K - kb0) : 0u;
-        const u32 bar = rawbar(slot);
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                         "r"(nv * TC_MTILE * 8u)
+        const u32 slot = gp % TC_RAW;
+        if (lane == 0) {
+            // one tensor copy of 32 rows x 128 slots; rows past the layer's R are zero-filled (and any
+            // row past the layer's K is ignored by the converters), so the box always brings 32 KB
+            const u32 bar = rawbar(slot);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TC_RAW_BYTES)
                          : "memory");
-        __syncwarp();
-        if (lane < nv) {
-            const u32 kk = kb0 + lane, ct = pit.ru * Ly.in_groups + kk / Ly.n_rot, rot = kk % Ly.n_rot;
-            const u64* src = Ly.R + ((size_t)ct * Ly.r_slots + rot) * ctw + ((size_t)pit.p * L + pit.k) * N + pit.n0;
-            const u32 dst = smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES) + lane * TC_MTILE * 8u;
+            const int x = (int)pit.n0, y = (int)(pit.p * L + pit.k);
+            const int z = (int)(pit.ru * Ly.in_groups * Ly.n_rot + tp * TC_KTILE);
             asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                "l"(src), "r"(TC_MTILE * 8u), "r"(bar)
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+                    "r"(smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES)),
+                "l"(reinterpret_cast<u64>(&Ly.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
                 : "memory");
         }
         gp++;
@@ -656,7 +656,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
             p_live = tc_item(B, ip, N, L, pit);
         }
     };
-    static_assert(TC_KTILE == 32, "one lane per row of a tile");
     if (warp == 0)
         for (int i = 0; i < TC_RAW - 1; i++) produce_one();
 
@@ -862,6 +861,28 @@ KP make_kp(const he_params* p) {
 }
 
 u32 ntt_threads(u32 N) { return std::min<u32>(NTT_MAX_THREADS, N / NTT_E); }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+void encode_rmap(CUtensorMap* map, const u64* R, u32 N, u32 L, u32 rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    });
+    if (!fn) fail(HE_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[3] = {N, 2ull * L, rows};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * 8, 2ull * L * N * 8};
+    const cuuint32_t box[3] = {TC_MTILE, 1, TC_KTILE};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)R, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(HE_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -1159,6 +1180,7 @@ struct he_plan {
         L.K = K, L.Kpad = tc_kpad, L.in_groups = lay.in_groups, L.out_groups = lay.out_groups;
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
         L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
+        if (use_tc) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups;
         return s;
     }

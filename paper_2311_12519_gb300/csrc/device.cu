@@ -413,8 +413,10 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
         u128 a1 = ((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1;
         u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
         a0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];
-        Rc[(size_t)rd.rot * ctw + (size_t)k * N + x] = bred128(a0, m);
-        Rc[(size_t)rd.rot * ctw + (size_t)(L + k) * N + x] = bred128(a1, m);
+        // R streams out once and is read once by the MAC: evict-first keeps D and the keys in L2
+        __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), bred128(a0, m));
+        __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)(L + k) * N + x),
+               bred128(a1, m));
     }
 }
 
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
 // Shared-memory operands use the no-swizzle K-major canonical layout: 8x16-byte
 // core matrices, LBO = 128 B between core matrices along K, SBO = 512 B
 // between core matrices along M/N (a 32-term K tile is 4 core matrices wide).
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;
 constexpr int TC_MTILE = 128;     // NTT slots per CTA (MMA M)
 constexpr int TC_KTILE = 32;      // terms per pipeline stage
 constexpr int TC_CHUNKS = 5;      // 10-bit chunks of a residue < 2^50
@@ -739,28 +741,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
         if (ok) ok = mbar_wait((gl & 1) ? bar1 : bar0, (gl >> 1) & 1);
         if (!ok && tid == 0) atomicExch(Ly.err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (slot n0 + 32 (w%4) + lane); the two
-        // warp halves take alternate 16-column blocks of output rows
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (slot n0 + 32 (w%4) + lane); the four
+        // warp quarters take every fourth 8-column block of output rows
         if (ok) {
-            const u32 sp = warp & 3, half = warp >> 2;
+            const u32 sp = warp & 3, quarter = warp >> 2;
             const u32 nl = sp * 32 + lane, x = it.n0 + nl;
             const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
-            for (u32 cb = half * 16; cb < nrows; cb += 32) {
-                u32 d[TC_CHUNKS][16];
+            for (u32 cb = quarter * 8; cb < nrows; cb += 32) {
+                u32 d[TC_CHUNKS][8];
 #pragma unroll
                 for (int c = 0; c < TC_CHUNKS; c++) {
                     const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]), "=r"(d[c][5]),
-                          "=r"(d[c][6]), "=r"(d[c][7]), "=r"(d[c][8]), "=r"(d[c][9]), "=r"(d[c][10]),
-                          "=r"(d[c][11]), "=r"(d[c][12]), "=r"(d[c][13]), "=r"(d[c][14]), "=r"(d[c][15])
-                        : "r"(ta));
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
+                                   "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
+                                 : "r"(ta));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                u64 red[16];
+                u64 red[8];
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
+                for (int j = 0; j < 8; j++) {
                     const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
                     const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
                                          (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                     red[j] = bred128((u128)a, m);
                 }
 #pragma unroll
-                for (int j = 0; j < 16; j += NR) {
+                for (int j = 0; j < 8; j += NR) {
                     const u32 row = row0 + cb + j;
                     const u32 gg = row / NR;
                     if (gg >= out_groups) continue;

@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
     }
     const size_t ctw = 2ull * L * N;
     const u32 r_slots = Ly.r_slots, r_id = Ly.r_id;
+#pragma unroll 4
     for (u32 c = 0; c < Ly.n_ct_in; c++) {
         const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
         u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
@@ -535,7 +536,8 @@ constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 40 KB
 constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 6 KB
 constexpr u32 TC_SBO = (TC_KTILE / 8) * 128;                       // bytes between 8-row core-matrix blocks
 constexpr u32 TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_RAW = 3;                                          // raw residue tiles in flight
+constexpr int TC_RAW = 4;                                          // raw residue tiles (TC_RAW - 1 in flight)
+constexpr int TC_PF = 3;                                           // further tiles prefetched into L2
 constexpr u32 TC_RAW_BYTES = TC_KTILE * TC_MTILE * 8;              // 32 KB: 32 rows of 128 residues
 constexpr u32 TC_RAW_OFF = 2 * TC_STAGE_BYTES;
 constexpr u32 TC_BAR_OFF = TC_RAW_OFF + TC_RAW * TC_RAW_BYTES;
@@ -629,37 +631,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     const u32 tmem = *tmem_slot;
     bool ok = true;
 
-    // producer cursor (warp 0 only): stream position gp = (item ip, tile tp)
-    TcItem pit;
-    u32 ip = blockIdx.x, tp = 0, gp = 0;
-    bool p_live = tc_item(B, ip, N, L, pit);
-    auto produce_one = [&]() {  // issues the current producer position, then advances it
-        if (!p_live) return;
-        const LayerDev& Ly = *pit.ly;
-        const u32 slot = gp % TC_RAW;
-        if (lane == 0) {
+    // producer cursors (warp 0 only), walking the CTA's stream of (item, tile): the copy cursor
+    // brings tiles into shared memory, the prefetch cursor runs TC_PF tiles ahead of it into L2
+    struct Cursor {
+        TcItem it;
+        u32 ip, tp;
+        bool live;
+    };
+    auto cur_init = [&](Cursor& c) {
+        c.ip = blockIdx.x, c.tp = 0;
+        c.live = tc_item(B, c.ip, N, L, c.it);
+    };
+    auto cur_next = [&](Cursor& c) {
+        if (!c.live) return;
+        if (++c.tp == c.it.n_tiles) {
+            c.tp = 0;
+            c.ip += gridDim.x;
+            c.live = tc_item(B, c.ip, N, L, c.it);
+        }
+    };
+    auto coords = [&](const Cursor& c, int& x, int& y, int& z) {
+        x = (int)c.it.n0, y = (int)(c.it.p * L + c.it.k);
+        z = (int)(c.it.ru * c.it.ly->in_groups * c.it.ly->n_rot + c.tp * TC_KTILE);
+    };
+    Cursor cp, cf;
+    u32 gp = 0;
+    cur_init(cp);
+    cur_init(cf);
+    auto prefetch_one = [&]() {
+        if (cf.live && lane == 0) {
+            int x, y, z;
+            coords(cf, x, y, z);
+            asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(
+                             reinterpret_cast<u64>(&cf.it.ly->rmap)),
+                         "r"(x), "r"(y), "r"(z)
+                         : "memory");
+        }
+        cur_next(cf);
+    };
+    auto produce_one = [&]() {  // issues the copy cursor's tile, then advances both cursors
+        if (cp.live && lane == 0) {
             // one tensor copy of 32 rows x 128 slots; rows past the layer's R are zero-filled (and any
             // row past the layer's K is ignored by the converters), so the box always brings 32 KB
-            const u32 bar = rawbar(slot);
+            const u32 slot = gp % TC_RAW, bar = rawbar(slot);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TC_RAW_BYTES)
                          : "memory");
-            const int x = (int)pit.n0, y = (int)(pit.p * L + pit.k);
-            const int z = (int)(pit.ru * Ly.in_groups * Ly.n_rot + tp * TC_KTILE);
+            int x, y, z;
+            coords(cp, x, y, z);
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
                     "r"(smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES)),
-                "l"(reinterpret_cast<u64>(&Ly.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
+                "l"(reinterpret_cast<u64>(&cp.it.ly->rmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
                 : "memory");
         }
-        gp++;
-        if (++tp == pit.n_tiles) {
-            tp = 0;
-            ip += gridDim.x;
-            p_live = tc_item(B, ip, N, L, pit);
-        }
+        if (cp.live) gp++;
+        cur_next(cp);
+        prefetch_one();
     };
-    if (warp == 0)
+    if (warp == 0) {
+        for (int i = 0; i < TC_RAW - 1 + TC_PF; i++) prefetch_one();
         for (int i = 0; i < TC_RAW - 1; i++) produce_one();
+    }
 
     u32 g = 0;  // consumer stream position
     TcItem it;
@@ -673,7 +705,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
             const u32 st = g & 1;
             unsigned char* A = tsm + st * TC_STAGE_BYTES;
             unsigned char* Bs = A + TC_A_BYTES;
-            // keep the copies two positions ahead; raw slot (g + 2) % 3 was last read at g - 1
+            // keep the copies TC_RAW - 1 positions ahead; raw slot (g + TC_RAW - 1) % TC_RAW was last read at g - 1
             if (warp == 0 && __all_sync(0xffffffffu, ok)) produce_one();
             if (g >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((g - 2) >> 1) & 1);  // MMA stage free again
             const u32 kk0 = t * TC_KTILE;

@@ -259,7 +259,7 @@ struct LayerDev {
     const RotDev* rots;        // rotations that need a key switch
     const int16_t* scal;       // CUDA-core MAC scalars [out_groups][c_n][K]
     const u64* pk;             // NTT(P_k) [L][N]
-    const __half* sc16;        // tensor-core MAC scalars [tc_rows][Kpad]
+    const __half* sc16;        // tensor-core MAC scalars, one shared-memory tile image per (row tile, K tile)
     const int* bias;           // tensor-core MAC row offsets 512 sum(s)
     int* err;                  // bounded-wait status
     u32 n_ct_in, n_ct_out, n_rot, rot_id, n_ks, K, Kpad, in_groups, out_groups, row_units, tc_rows, tc_rows_per_cta;
@@ -535,12 +535,13 @@ constexpr u32 TC_A_CHUNK_BYTES = TC_MTILE * TC_KTILE * 2;          // 8 KB
 constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 40 KB
 constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 6 KB
 constexpr u32 TC_SBO = (TC_KTILE / 8) * 128;                       // bytes between 8-row core-matrix blocks
-constexpr u32 TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_RAW = 4;                                          // raw residue tiles (TC_RAW - 1 in flight)
-constexpr int TC_PF = 3;                                           // further tiles prefetched into L2
+constexpr u32 TC_STAGE_BYTES = TC_A_BYTES;                         // converted residues, 2 stages
+constexpr int TC_RAW = 3;                                          // raw residue tiles (TC_RAW - 1 in flight)
+constexpr int TC_BSLOTS = 4;                                       // scalar tiles: slot g % 4
 constexpr u32 TC_RAW_BYTES = TC_KTILE * TC_MTILE * 8;              // 32 KB: 32 rows of 128 residues
 constexpr u32 TC_RAW_OFF = 2 * TC_STAGE_BYTES;
-constexpr u32 TC_BAR_OFF = TC_RAW_OFF + TC_RAW * TC_RAW_BYTES;
+constexpr u32 TC_BS_OFF = TC_RAW_OFF + TC_RAW * TC_RAW_BYTES;
+constexpr u32 TC_BAR_OFF = TC_BS_OFF + TC_BSLOTS * TC_B_BYTES;
 constexpr u32 TC_SMEM_BYTES = TC_BAR_OFF + 128;                    // + mbarriers and TMEM address
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;                     // bounded mbarrier waits
 
@@ -654,60 +655,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
         x = (int)c.it.n0, y = (int)(c.it.p * L + c.it.k);
         z = (int)(c.it.ru * c.it.ly->in_groups * c.it.ly->n_rot + c.tp * TC_KTILE);
     };
-    Cursor cp, cf;
+    Cursor cp;
     u32 gp = 0;
     cur_init(cp);
-    cur_init(cf);
-    auto prefetch_one = [&]() {
-        if (cf.live && lane == 0) {
-            int x, y, z;
-            coords(cf, x, y, z);
-            asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(
-                             reinterpret_cast<u64>(&cf.it.ly->rmap)),
-                         "r"(x), "r"(y), "r"(z)
-                         : "memory");
-        }
-        cur_next(cf);
-    };
-    auto produce_one = [&]() {  // issues the copy cursor's tile, then advances both cursors
+    auto produce_one = [&]() {  // issues the copy cursor's tile, then advances it
         if (cp.live && lane == 0) {
-            // one tensor copy of 32 rows x 128 slots; rows past the layer's R are zero-filled (and any
-            // row past the layer's K is ignored by the converters), so the box always brings 32 KB
-            const u32 slot = gp % TC_RAW, bar = rawbar(slot);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TC_RAW_BYTES)
+            // one tensor copy of 32 rows x 128 slots (rows past the layer's R are zero-filled and rows
+            // past its K are ignored by the converters) plus the scalar tile image, on one barrier
+            const LayerDev& Lc = *cp.it.ly;
+            const u32 slot = gp % TC_RAW, bar = rawbar(slot), bbytes = Lc.tc_rows_per_cta * TC_KTILE * 2;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TC_RAW_BYTES + bbytes)
                          : "memory");
             int x, y, z;
             coords(cp, x, y, z);
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
                     "r"(smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES)),
-                "l"(reinterpret_cast<u64>(&cp.it.ly->rmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
+                "l"(reinterpret_cast<u64>(&Lc.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
                 : "memory");
+            const u32 mt = cp.it.row0 / Lc.tc_rows_per_cta, ktiles = Lc.Kpad / TC_KTILE;
+            const __half* bsrc = Lc.sc16 + ((size_t)mt * ktiles + cp.tp) * (Lc.tc_rows_per_cta * TC_KTILE);
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             smem_u32(tsm + TC_BS_OFF + (gp % TC_BSLOTS) * TC_B_BYTES)),
+                         "l"(bsrc), "r"(bbytes), "r"(bar)
+                         : "memory");
         }
         if (cp.live) gp++;
         cur_next(cp);
-        prefetch_one();
     };
-    if (warp == 0) {
-        for (int i = 0; i < TC_RAW - 1 + TC_PF; i++) prefetch_one();
+    if (warp == 0)
         for (int i = 0; i < TC_RAW - 1; i++) produce_one();
-    }
 
     u32 g = 0;  // consumer stream position
     TcItem it;
     for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
         const LayerDev& Ly = *it.ly;
-        const u32 K = Ly.K, Kpad = Ly.Kpad, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
+        const u32 K = Ly.K, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
         const u32 out_groups = Ly.out_groups;
         const LimbC m = kp.limb[k];
         const u32 idesc = tc_idesc(TC_MTILE, nrows);
         for (u32 t = 0; t < it.n_tiles; t++, g++) {
             const u32 st = g & 1;
             unsigned char* A = tsm + st * TC_STAGE_BYTES;
-            unsigned char* Bs = A + TC_A_BYTES;
-            // keep the copies TC_RAW - 1 positions ahead; raw slot (g + TC_RAW - 1) % TC_RAW was last read at g - 1
+            unsigned char* Bs = tsm + TC_BS_OFF + (g % TC_BSLOTS) * TC_B_BYTES;
+            if (g >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((g - 2) >> 1) & 1);  // MMA g-2 done
+            // keep the copies two positions ahead: raw slot (g + 2) % 3 was last read at g - 1, and
+            // scalar slot (g + 2) % 4 = (g - 2) % 4 was last read by MMA g - 2, which has completed
             if (warp == 0 && __all_sync(0xffffffffu, ok)) produce_one();
-            if (g >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((g - 2) >> 1) & 1);  // MMA stage free again
             const u32 kk0 = t * TC_KTILE;
             if (ok) ok = mbar_wait(rawbar(g % TC_RAW), (g / TC_RAW) & 1);
             {
@@ -737,12 +731,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                             make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
-            }
-            // B: scalar rows row0.. of this item, 32 terms, from the plan's fp16 table [rows][Kpad]
-            for (u32 i = tid; i < nrows * (TC_KTILE / 8); i += TC_THREADS) {
-                const u32 r = i / (TC_KTILE / 8), o = i % (TC_KTILE / 8);
-                const uint4 q4 = *reinterpret_cast<const uint4*>(Ly.sc16 + (size_t)(row0 + r) * Kpad + kk0 + o * 8);
-                *reinterpret_cast<uint4*>(Bs + kmajor_off(r, o * 8)) = q4;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1331,14 +1319,22 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             P->tc_rows = (rows + 15) / 16 * 16;
             P->tc_rows_per_cta = std::min<u32>(TC_NMAX, P->tc_rows);
             P->tc_kpad = (P->K + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
-            std::vector<__half> h16((size_t)P->tc_rows * P->tc_kpad, __float2half(0.0f));
+            // scalar tiles stored as the exact shared-memory image the MMA reads (K-major, no
+            // swizzle), one block of rows_per_cta x 32 terms per (row tile, K tile)
+            const u32 rpc = P->tc_rows_per_cta, ktiles = P->tc_kpad / TC_KTILE;
+            const u32 mtiles = (P->tc_rows + rpc - 1) / rpc;
+            std::vector<__half> h16((size_t)mtiles * ktiles * rpc * TC_KTILE, __float2half(0.0f));
             std::vector<int> bias(P->tc_rows, 0);
             for (u32 g = 0; g < lay.out_groups; g++)
                 for (u32 r = 0; r < NR; r++) {
+                    const u32 row = g * NR + r, mt = row / rpc, rl = row % rpc;
                     long long S = 0;
                     for (u32 kk = 0; kk < P->K; kk++) {
                         int v = sc[((size_t)g * NR + r) * P->K + kk];
-                        h16[(size_t)(g * NR + r) * P->tc_kpad + kk] = __float2half((float)v);
+                        const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
+                        const size_t byte = ((size_t)mt * ktiles + kt) * rpc * TC_KTILE * 2 +
+                                            (rl >> 3) * TC_SBO + (kl >> 3) * 128 + (rl & 7) * 16 + (kl & 7) * 2;
+                        h16[byte / 2] = __float2half((float)v);
                         S += v;
                     }
                     bias[g * NR + r] = (int)(512 * S);

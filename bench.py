@@ -33,6 +33,11 @@ N_RING, L_LIMBS, LIMB_BITS = 8192, 3, 50
 WORKLOAD = "resnet20-3x3-stack, 32x32, 1 image/GPU, N=8192, L=3x50-bit, t=1032193, c_n=2"
 METRIC = "HE-conv layers/s (ResNet-20 stack, bit-exact)"
 L2_BYTES = 129 * 2**20
+# DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the device source with this sha256 prefix;
+# reported as roofline traffic only while device.cu is unchanged
+PROFILED_TRAFFIC = {"source": "03c81fc60a59f009", "k_keyswitch": 2.712e9, "k_mac_tc": 2.359e9, "k_ntt_inputs": 0.380e9,
+                    "k_intt": 0.223e9}
 
 
 def layer_descs():
@@ -186,7 +191,8 @@ def run_gpu(args, rank, world):
         ctb = 2 * L * N * 8
         # algorithmic bytes of each stage (one read of every input, one write of every output)
         stage_bytes["ntt_in"] += lay.n_ct_in * ctb + lay.n_ct_in * (2 * L + L * l * L) * N * 8
-        stage_bytes["keyswitch"] += (lay.n_ct_in * lay.n_galois * (L * l * L * N * 8 + L * N * 8 + ctb)
+        # minimum: rotated copies written once, digit NTTs, NTT(c0) and keys read once
+        stage_bytes["keyswitch"] += (lay.n_ct_in * lay.n_galois * ctb + lay.n_ct_in * (L * l * L + L) * N * 8
                                      + lay.n_galois * L * l * 2 * L * N * 8)
         stage_bytes["mac"] += lay.n_ct_in * n_rot * ctb + lay.n_ct_out * ctb
         stage_bytes["ntt_out"] += 2 * lay.n_ct_out * ctb
@@ -328,6 +334,13 @@ def run_gpu(args, rank, world):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": top, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roof["ms_per_launch"] = per_launch_s * 1000
+    import hashlib
+    src = hashlib.sha256(open(os.path.join(ROOT, "paper_2311_12519_gb300", "csrc", "device.cu"), "rb").read())
+    kname = {"mac": "k_mac_tc" if mac_tc else "k_mac", "keyswitch": "k_keyswitch", "ntt_in": "k_ntt_inputs",
+             "ntt_out": "k_intt"}[top]
+    if src.hexdigest().startswith(PROFILED_TRAFFIC["source"]) and kname in PROFILED_TRAFFIC:
+        roof["traffic"] = PROFILED_TRAFFIC[kname]
+    roof["kernel"] = kname
     roof["stage_share"] = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages_b.values())), 4)
                            for k, v in stages_b.items()}
     cpu = None

@@ -537,12 +537,11 @@ constexpr u32 TC_B_BYTES = TC_NMAX * TC_KTILE * 2;                 // 6 KB
 constexpr u32 TC_SBO = (TC_KTILE / 8) * 128;                       // bytes between 8-row core-matrix blocks
 constexpr u32 TC_STAGE_BYTES = TC_A_BYTES;                         // converted residues, 2 stages
 constexpr int TC_RAW = 3;                                          // raw residue tiles (TC_RAW - 1 in flight)
-constexpr int TC_BSLOTS = 4;                                       // scalar tiles: slot g % 4
 constexpr u32 TC_RAW_BYTES = TC_KTILE * TC_MTILE * 8;              // 32 KB: 32 rows of 128 residues
 constexpr u32 TC_RAW_OFF = 2 * TC_STAGE_BYTES;
 constexpr u32 TC_BS_OFF = TC_RAW_OFF + TC_RAW * TC_RAW_BYTES;
-constexpr u32 TC_BAR_OFF = TC_BS_OFF + TC_BSLOTS * TC_B_BYTES;
-constexpr u32 TC_SMEM_BYTES = TC_BAR_OFF + 128;                    // + mbarriers and TMEM address
+constexpr u32 TC_BAR_OFF = TC_BS_OFF + TC_RAW * TC_B_BYTES;         // scalar tile of slot s at TC_BS_OFF + s B
+constexpr u32 TC_SMEM_BYTES = TC_BAR_OFF + 128;                    // + 12 mbarriers, TMEM address, abort flag
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;                     // bounded mbarrier waits
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -566,18 +565,6 @@ __host__ __device__ constexpr u32 tc_idesc(u32 M, u32 N) {
     return (1u << 4) | (0u << 7) | (0u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
-    for (long long i = 0; i < TC_SPIN_LIMIT; i++) {
-        u32 ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
 
 // Persistent: each CTA walks work items blockIdx.x, blockIdx.x + gridDim.x, ... of every layer
 // of the table; an item is ((row unit, polynomial, limb), slot tile, row tile) of one layer.
@@ -606,19 +593,34 @@ __device__ __forceinline__ bool tc_item(const Batch<MAXB>& B, u32 item, u32 N, u
     return true;
 }
 
+// Warp roles: warp 0 issues the copies, warp 1 (lane 0) issues the MMAs, warps 2..15 convert
+// residues to fp16 chunks, warps 4..15 also run the epilogue.  Barriers (all bounded waits):
+//   raw_full[s]   copies of stream position g landed in slot s = g % TC_RAW   (1 arrive + tx)
+//   raw_empty[s]  slot s read by every converter warp and by the MMAs          (TC_CONV + 1)
+//   a_full[st]    converted stage st = g % 2 written by every converter warp   (TC_CONV)
+//   a_empty[st]   MMAs of stage st done                                          (1, commit)
+//   acc_full      last MMA of a work item done                                   (1, commit)
+//   acc_empty     accumulators read by every epilogue warp                       (TC_EPI)
+constexpr int TC_CONV = TC_THREADS / 32 - 2;  // converter warps 2..15
+constexpr int TC_EPI = TC_THREADS / 32 - 4;   // epilogue warps 4..15
+static_assert(TC_THREADS == 512, "warp roles assume 16 warps");
+
 template <bool PACKED, int MAXB>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp, u32 tmem_cols) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
     const u32 N = kp.N, L = kp.L;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    u64* bars = reinterpret_cast<u64*>(tsm + TC_BAR_OFF);  // [0,1] MMA stages, [2..] raw slots
-    u32* tmem_slot = reinterpret_cast<u32*>(tsm + TC_BAR_OFF + 64);
-    const u32 bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
-    auto rawbar = [&](u32 slot) { return smem_u32(&bars[2 + slot]); };
+    u64* bars = reinterpret_cast<u64*>(tsm + TC_BAR_OFF);
+    // barrier indices: raw_full 0..2, raw_empty 3..5, a_full 6..7, a_empty 8..9, acc_full 10, acc_empty 11
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + TC_BAR_OFF + 12 * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + TC_BAR_OFF + 12 * 8 + 4);
 
     if (tid == 0) {
-        for (int i = 0; i < 2 + TC_RAW; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
+        const u32 counts[12] = {1, 1, 1, TC_CONV + 1, TC_CONV + 1, TC_CONV + 1, TC_CONV, TC_CONV, 1, 1, 1, TC_EPI};
+        for (int i = 0; i < 12; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(counts[i]));
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -630,84 +632,116 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const u32 tmem = *tmem_slot;
-    bool ok = true;
+    int* err = B.L[0].err;
 
-    // producer cursors (warp 0 only), walking the CTA's stream of (item, tile): the copy cursor
-    // brings tiles into shared memory, the prefetch cursor runs TC_PF tiles ahead of it into L2
-    struct Cursor {
-        TcItem it;
-        u32 ip, tp;
-        bool live;
-    };
-    auto cur_init = [&](Cursor& c) {
-        c.ip = blockIdx.x, c.tp = 0;
-        c.live = tc_item(B, c.ip, N, L, c.it);
-    };
-    auto cur_next = [&](Cursor& c) {
-        if (!c.live) return;
-        if (++c.tp == c.it.n_tiles) {
-            c.tp = 0;
-            c.ip += gridDim.x;
-            c.live = tc_item(B, c.ip, N, L, c.it);
-        }
-    };
-    auto coords = [&](const Cursor& c, int& x, int& y, int& z) {
-        x = (int)c.it.n0, y = (int)(c.it.p * L + c.it.k);
-        z = (int)(c.it.ru * c.it.ly->in_groups * c.it.ly->n_rot + c.tp * TC_KTILE);
-    };
-    Cursor cp;
-    u32 gp = 0;
-    cur_init(cp);
-    auto produce_one = [&]() {  // issues the copy cursor's tile, then advances it
-        if (cp.live && lane == 0) {
-            // one tensor copy of 32 rows x 128 slots (rows past the layer's R are zero-filled and rows
-            // past its K are ignored by the converters) plus the scalar tile image, on one barrier
-            const LayerDev& Lc = *cp.it.ly;
-            const u32 slot = gp % TC_RAW, bar = rawbar(slot), bbytes = Lc.tc_rows_per_cta * TC_KTILE * 2;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TC_RAW_BYTES + bbytes)
-                         : "memory");
-            int x, y, z;
-            coords(cp, x, y, z);
+    // bounded wait that gives up at once when another role has given up
+    auto wait = [&](int i, u32 parity) -> bool {
+        for (long long it = 0; it < TC_SPIN_LIMIT; it++) {
+            if (*abort_flag) return false;
+            u32 ok;
             asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-                    "r"(smem_u32(tsm + TC_RAW_OFF + slot * TC_RAW_BYTES)),
-                "l"(reinterpret_cast<u64>(&Lc.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(bar(i)), "r"(parity)
                 : "memory");
-            const u32 mt = cp.it.row0 / Lc.tc_rows_per_cta, ktiles = Lc.Kpad / TC_KTILE;
-            const __half* bsrc = Lc.sc16 + ((size_t)mt * ktiles + cp.tp) * (Lc.tc_rows_per_cta * TC_KTILE);
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             smem_u32(tsm + TC_BS_OFF + (gp % TC_BSLOTS) * TC_B_BYTES)),
-                         "l"(bsrc), "r"(bbytes), "r"(bar)
-                         : "memory");
+            if (ok) return true;
         }
-        if (cp.live) gp++;
-        cur_next(cp);
+        *abort_flag = 1;
+        atomicExch(err, 1);
+        return false;
     };
-    if (warp == 0)
-        for (int i = 0; i < TC_RAW - 1; i++) produce_one();
+    auto arrive = [&](int i) { asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(i)) : "memory"); };
 
-    u32 g = 0;  // consumer stream position
-    TcItem it;
-    for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
-        const LayerDev& Ly = *it.ly;
-        const u32 K = Ly.K, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
-        const u32 out_groups = Ly.out_groups;
-        const LimbC m = kp.limb[k];
-        const u32 idesc = tc_idesc(TC_MTILE, nrows);
-        for (u32 t = 0; t < it.n_tiles; t++, g++) {
-            const u32 st = g & 1;
-            unsigned char* A = tsm + st * TC_STAGE_BYTES;
-            unsigned char* Bs = tsm + TC_BS_OFF + (g % TC_BSLOTS) * TC_B_BYTES;
-            if (g >= 2 && ok) ok = mbar_wait(st ? bar1 : bar0, ((g - 2) >> 1) & 1);  // MMA g-2 done
-            // keep the copies two positions ahead: raw slot (g + 2) % 3 was last read at g - 1, and
-            // scalar slot (g + 2) % 4 = (g - 2) % 4 was last read by MMA g - 2, which has completed
-            if (warp == 0 && __all_sync(0xffffffffu, ok)) produce_one();
-            const u32 kk0 = t * TC_KTILE;
-            if (ok) ok = mbar_wait(rawbar(g % TC_RAW), (g / TC_RAW) & 1);
-            {
-                const u32 nl = tid & (TC_MTILE - 1);
-                const u64* raw = reinterpret_cast<const u64*>(tsm + TC_RAW_OFF + (g % TC_RAW) * TC_RAW_BYTES);
-                for (u32 o = tid >> 7; o < TC_KTILE / 8; o += TC_THREADS / TC_MTILE) {
+    if (warp == 0) {
+        // ---------------------------------------------------------------- copies
+        u32 g = 0;
+        TcItem it;
+        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 bbytes = Ly.tc_rows_per_cta * TC_KTILE * 2, ktiles = Ly.Kpad / TC_KTILE;
+            const u32 mt = it.row0 / Ly.tc_rows_per_cta;
+            for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                const u32 s = g % TC_RAW;
+                const bool fr = g < TC_RAW || wait(3 + s, ((g / TC_RAW) - 1) & 1);
+                if (!__all_sync(0xffffffffu, fr)) break;
+                if (lane == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)),
+                                 "r"(TC_RAW_BYTES + bbytes)
+                                 : "memory");
+                    const int x = (int)it.n0, y = (int)(it.p * L + it.k);
+                    const int z = (int)(it.ru * Ly.in_groups * Ly.n_rot + t * TC_KTILE);
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+                            "r"(smem_u32(tsm + TC_RAW_OFF + s * TC_RAW_BYTES)),
+                        "l"(reinterpret_cast<u64>(&Ly.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar(s))
+                        : "memory");
+                    const __half* bsrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (Ly.tc_rows_per_cta * TC_KTILE);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(tsm + TC_BS_OFF + s * TC_B_BYTES)),
+                        "l"(bsrc), "r"(bbytes), "r"(bar(s))
+                        : "memory");
+                }
+                __syncwarp();
+            }
+            if (*abort_flag) break;
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMAs (lane 0)
+        if (lane == 0) {
+            u32 g = 0, n_items = 0;
+            TcItem it;
+            for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x, n_items++) {
+                if (n_items > 0 && !wait(11, (n_items - 1) & 1)) break;  // accumulators read out
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const u32 idesc = tc_idesc(TC_MTILE, it.nrows);
+                bool okk = true;
+                for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                    const u32 st = g & 1, s = g % TC_RAW;
+                    if (!wait(6 + st, (g >> 1) & 1)) { okk = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const u32 a_base = smem_u32(tsm + st * TC_STAGE_BYTES), b_base = smem_u32(tsm + TC_BS_OFF + s * TC_B_BYTES);
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+#pragma unroll
+                        for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                            const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
+                            const u64 bd = smem_desc(b_base + ks * 256);
+                            const u32 acc = (t > 0 || ks > 0) ? 1u : 0u;
+                            const u32 dt = tmem + (u32)(c * it.nrows);
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(8 + st)));
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(3 + s)));
+                }
+                if (!okk) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(10)));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- converters (+ epilogue)
+        u32 g = 0, n_items = 0;
+        TcItem it;
+        const u32 cw = warp - 2;  // converter index 0..13
+        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x, n_items++) {
+            const LayerDev& Ly = *it.ly;
+            const u32 K = Ly.K;
+            bool okk = true;
+            for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                const u32 st = g & 1, s = g % TC_RAW, kk0 = t * TC_KTILE;
+                bool w = wait(s, (g / TC_RAW) & 1);                    // raw data landed
+                w = w && (g < 2 || wait(8 + st, ((g >> 1) - 1) & 1));  // stage free
+                if (!__all_sync(0xffffffffu, w)) { okk = false; break; }
+                const u64* raw = reinterpret_cast<const u64*>(tsm + TC_RAW_OFF + s * TC_RAW_BYTES);
+                unsigned char* A = tsm + st * TC_STAGE_BYTES;
+                // 512 (slot, octet) pieces per tile over 14 warps: piece i = slot (i % 128), octet (i / 128)
+                for (u32 i = cw * 32 + lane; i < TC_MTILE * (TC_KTILE / 8); i += TC_CONV * 32) {
+                    const u32 nl = i & (TC_MTILE - 1), o = i >> 7;
                     u64 v[8];
 #pragma unroll
                     for (int e = 0; e < 8; e++) {
@@ -731,81 +765,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                             make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    arrive(6 + st);  // stage written
+                    arrive(3 + s);   // raw slot read
+                }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            if (tid == 0 && ok) {
+            if (!okk) break;
+            if (warp >= 4) {
+                // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane; the three warps of a
+                // sub-partition take every third 8-column block of output rows
+                if (!__all_sync(0xffffffffu, wait(10, n_items & 1))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const u32 a_base = smem_u32(A), b_base = smem_u32(Bs);
+                const u32 sp = warp & 3, third = (warp - 4) >> 2;
+                const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
+                const LimbC m = kp.limb[k];
+                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+                for (u32 cb = third * 8; cb < nrows; cb += 24) {
+                    u32 d[TC_CHUNKS][8];
 #pragma unroll
-                for (int c = 0; c < TC_CHUNKS; c++) {
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+                        const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
+                                       "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
+                                     : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    u64 red[8];
 #pragma unroll
-                    for (int ks = 0; ks < TC_KTILE / 16; ks++) {
-                        const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
-                        const u64 bd = smem_desc(b_base + ks * 256);
-                        const u32 acc = (t > 0 || ks > 0) ? 1u : 0u;
-                        const u32 dt = tmem + (u32)(c * nrows);
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    for (int j = 0; j < 8; j++) {
+                        const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
+                        const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
+                        const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
+                        const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+                        red[j] = bred128((u128)a, m);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; j += NR) {
+                        const u32 row = row0 + cb + j;
+                        const u32 gg = row / NR;
+                        if (gg >= Ly.out_groups) continue;
+                        u64 out = red[j];
+                        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                        Ly.O[((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x] = out;
                     }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    st ? bar1 : bar0));
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) arrive(11);  // accumulators free
             }
         }
-        // the last commit of this item covers all of its MMAs
-        const u32 gl = g - 1;
-        if (ok) ok = mbar_wait((gl & 1) ? bar1 : bar0, (gl >> 1) & 1);
-        if (!ok && tid == 0) atomicExch(Ly.err, 1);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane (slot n0 + 32 (w%4) + lane); the four
-        // warp quarters take every fourth 8-column block of output rows
-        if (ok) {
-            const u32 sp = warp & 3, quarter = warp >> 2;
-            const u32 nl = sp * 32 + lane, x = it.n0 + nl;
-            const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
-            for (u32 cb = quarter * 8; cb < nrows; cb += 32) {
-                u32 d[TC_CHUNKS][8];
-#pragma unroll
-                for (int c = 0; c < TC_CHUNKS; c++) {
-                    const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                 : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
-                                   "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
-                                 : "r"(ta));
-                }
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                u64 red[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
-                    const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
-                                         (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
-                                         (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
-                    const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
-                                         (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
-                    const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
-                    red[j] = bred128((u128)a, m);
-                }
-#pragma unroll
-                for (int j = 0; j < 8; j += NR) {
-                    const u32 row = row0 + cb + j;
-                    const u32 gg = row / NR;
-                    if (gg >= out_groups) continue;
-                    u64 out = red[j];
-                    if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
-                    Ly.O[((size_t)(it.ru * out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x] = out;
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");  // TMEM reads done before the next item's MMAs
     }
-    // after a timed-out wait, let copies that were issued but not consumed land (bounded) before exit
-    if (warp == 0)
-        for (u32 q = g; q < gp; q++) mbar_wait(rawbar(q % TC_RAW), (q / TC_RAW) & 1);
+    // drain: every copy that was issued is waited for by the converters in the normal path; after an
+    // abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    if (*abort_flag && tid == 0)
+        for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");

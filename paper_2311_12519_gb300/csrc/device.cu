@@ -298,31 +298,40 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt_inputs(const __grid_
     const u32 li = find_layer(B, ST_NTT, blockIdx.x);
     const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L, l = kp.l;
-    const u32 jobs = 2 * L + L * l * L;
+    // with one digit per limb (l = 1) the digit of c1 in its own limb is c1 itself, so the
+    // NTT of c1 is not a job of its own: the digit job (dd = k, limb k) also writes it to R
+    const u32 c1_jobs = l == 1 ? 0 : L;
+    const u32 jobs = L + c1_jobs + L * l * L;
     const u32 local = blockIdx.x - B.start[ST_NTT][li];
     const u32 c = local / jobs, y = local % jobs;
     const size_t ctw = 2ull * L * N;
+    u64* const Rid = Ly.R + ((size_t)c * Ly.r_slots + Ly.r_id) * ctw;
     const u64* src;
     u64* dst;
+    u64* dst2 = nullptr;
     u32 limb, shift = 0;
     u64 mask = ~0ull;
-    if (y < 2 * L) {
+    if (y < L + c1_jobs) {
         limb = y % L;
         src = Ly.in + c * ctw + (size_t)y * N;
-        dst = Ly.R + ((size_t)c * Ly.r_slots + Ly.r_id) * ctw + (size_t)y * N;
+        dst = Rid + (size_t)y * N;
     } else {
-        const u32 z = y - 2 * L, dd = z / L;
+        const u32 z = y - L - c1_jobs, dd = z / L;
         limb = z % L;
         src = Ly.in + c * ctw + (size_t)(L + dd / l) * N;
         dst = Ly.D + (((size_t)c * L * l + dd) * L + limb) * N;
         shift = kp.w * (dd % l);
         mask = (kp.w >= 64) ? ~0ull : ((1ull << kp.w) - 1);
+        if (l == 1 && dd == limb) dst2 = Rid + (size_t)(L + limb) * N;
     }
     const LimbC m = kp.limb[limb];
     ntt_forward_block(
         sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q,
         [&](u32 i) { return shift >= 64 ? 0ull : (__ldg(src + i) >> shift) & mask; },
-        [&](u32 i, u64 v) { dst[i] = v; });
+        [&](u32 i, u64 v) {
+            dst[i] = v;
+            if (dst2) dst2[i] = v;
+        });
 }
 
 // Plain batched NTT: polynomial blockIdx.x of [n][N], limb = index % L.
@@ -353,6 +362,21 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_intt(const __grid_consta
     const LimbC m = kp.limb[limb];
     ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
                       m.ninv_sh, [&](u32 i) { return __ldg(s + i); }, [&](u32 i, u64 v) { d[i] = v; });
+}
+
+// Barrett reduction of x = hi 2^50 + mid 2^25 + lo for a 50-bit limb (s - 1 = 49), without 128-bit
+// arithmetic: lo < 2^58, mid < 2^56, hi < 2^55 (at most 16 digit terms), so x < 2^106 < 2^(s+63) and
+//   floor(x / 2^49) = 2 hi + floor(mid / 2^24) + floor(((mid mod 2^24) 2^25 + lo) / 2^49)
+// with the last numerator below 2^59.  The quotient estimate mulhi(q1, mu) is the same as bred's.
+__device__ __forceinline__ u64 bred_split50(u64 lo, u64 mid, u64 hi, const LimbC& m) {
+    const u64 t = ((mid & 0xFFFFFFull) << 25) + lo;
+    const u64 q1 = (hi << 1) + (mid >> 24) + (t >> 49);
+    const u64 xlo = lo + (mid << 25) + (hi << 50);  // x mod 2^64
+    const u64 q3 = __umul64hi(q1, m.mu);
+    u64 r = xlo - q3 * m.q;
+    r = r >= m.q ? r - m.q : r;
+    r = r >= m.q ? r - m.q : r;
+    return r;
 }
 
 // acc += a * b with one unsigned 32x32 -> 64-bit multiply-add
@@ -410,14 +434,19 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             mad_wide_u(mid1, dh, k1l[dd]);
             mad_wide_u(hi1, dh, k1h[dd]);
         }
-        u128 a0 = ((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0;
-        u128 a1 = ((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1;
         u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
-        a0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];
+        lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];  // + sigma(c0); lo stays below 2^57
+        u64 r0, r1;
+        if (m.sm1 == 49) {
+            r0 = bred_split50(lo0, mid0, hi0, m);
+            r1 = bred_split50(lo1, mid1, hi1, m);
+        } else {
+            r0 = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
+            r1 = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
+        }
         // R streams out once and is read once by the MAC: evict-first keeps D and the keys in L2
-        __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), bred128(a0, m));
-        __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)(L + k) * N + x),
-               bred128(a1, m));
+        __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), r0);
+        __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)(L + k) * N + x), r1);
     }
 }
 
@@ -977,7 +1006,7 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
     const LayerDev& d = s.dev;
     const u32 L = p->L, N = p->N;
     switch (stage) {
-        case ST_NTT: return d.n_ct_in * (2 * L + L * p->l * L);
+        case ST_NTT: return d.n_ct_in * (L + (p->l == 1 ? 0 : L) + L * p->l * L);
         case ST_KS: return d.n_ks * L * (N / KS_THREADS);
         case ST_MAC:
             if (s.mv.tc) return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta);

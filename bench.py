@@ -373,6 +373,118 @@ def run_gpu(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ablation
+ABLATION = [
+    # (name, counterpart in the paper's latency study, decomp_bits, c_n, mac_impl)
+    ("eager, w=25", "Fig. latency (c): no latency optimisation", 25, 2, 3),
+    ("eager, w=50", "Fig. latency (d): parameter selection only", 50, 2, 3),
+    ("lazy CUDA-core, w=50", "Fig. latency (e): all optimisations", 50, 2, 1),
+    ("lazy tensor-core, w=50", "(e) with the contraction on tcgen05 (the default form)", 50, 2, 2),
+    ("lazy tensor-core, w=50, c_n=1", "padded convolution without output-channel packing (Sec. 2.4)", 50, 1, 2),
+]
+
+
+def conv_mod_t(act, wt, stride, t):
+    """Plain 2-D convolution (zero padding 1, 3x3 taps) reduced mod t, for checking decryptions."""
+    n, ci, h, w = act.shape
+    x = np.pad(act.astype(np.int64), ((0, 0), (0, 0), (1, 1), (1, 1)))
+    ho, wo = (h - 1) // stride + 1, (w - 1) // stride + 1
+    out = np.zeros((n, wt.shape[0], ho, wo), dtype=np.int64)
+    for dy in range(3):
+        for dx in range(3):
+            win = x[:, :, dy:dy + h:stride, dx:dx + w:stride][:, :, :ho, :wo]
+            out += np.einsum("nchw,oc->nohw", win, wt[:, :, dy, dx].astype(np.int64))
+    return out % t
+
+
+def run_ablation(args):
+    """Each row of ABLATION on the whole 19-layer stack in the batched graph form: ms per step,
+    per-stage times, and the decryptions of every layer checked against the plain convolution;
+    the MAC variants at the same w must also agree word for word."""
+    import torch
+
+    from paper_2311_12519_gb300 import hyena as H
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    specs = layer_descs()
+    words = {}
+    for name, paper, w, c_n, impl in ABLATION:
+        p = H.he_params_create(N_RING, L_LIMBS, limb_bits=LIMB_BITS, decomp_bits=w, est_mac_terms=64 * 9)
+        info = H.he_params_info(p)
+        sk = H.he_keygen(p, synth.SEED_KEYS)
+        descs = [H.conv_desc(**dict(s, c_n=c_n)) for s in specs]
+        gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
+        gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
+        plans, d_ins, d_outs, acts, wts = [], [], [], [], []
+        for i, (s, d) in enumerate(zip(specs, descs)):
+            act = synth.activations((1, s["C_in"], s["H"], s["W"]), info.t, label=i)
+            wt = synth.weights((s["C_out"], s["C_in"], s["kh"], s["kh"]), label=i)
+            cts = H.he_encrypt_image(p, sk, d, act, synth.SEED_ENC, info)
+            plan = H.he_conv_plan(p, gk, d, wt, mac_impl=impl)
+            plans.append(plan)
+            acts.append(act)
+            wts.append(wt)
+            d_ins.append(torch.from_numpy(cts.reshape(-1).view(np.int64)).to(dev))
+            d_outs.append(torch.empty(H.he_conv_sizes(plan)[1], dtype=torch.int64, device=dev))
+        batch = H.he_batch_create(plans)
+        d_ws = torch.empty(H.he_batch_workspace_bytes(batch) // 8 + 1, dtype=torch.int64, device=dev)
+        ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                H.he_batch_graph_launch(batch, ins_p, outs_p, d_ws.data_ptr(), sp)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            with ClockSampler(0) as clk:
+                for e0, e1 in ev:
+                    flush.zero_()
+                    e0.record(stream)
+                    H.he_batch_graph_launch(batch, ins_p, outs_p, d_ws.data_ptr(), sp)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+            ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / args.steps
+            H.he_profile_enable(True)
+            H.he_profile_collect()
+            for _ in range(args.steps):
+                flush.zero_()
+                H.he_batch_forward(batch, ins_p, outs_p, d_ws.data_ptr(), sp)
+            torch.cuda.synchronize()
+            H.he_profile_enable(False)
+            stages = H.he_profile_collect()
+        decrypt_ok = True
+        outs = []
+        for d, s, act, wt, o in zip(descs, specs, acts, wts, d_outs):
+            out = o.cpu().numpy().view(np.uint64)
+            outs.append(out)
+            dec = H.he_decrypt_image(p, sk, d, out.reshape(-1, 2, info.L, info.N))
+            decrypt_ok &= bool(((dec - conv_mod_t(act, wt, s["stride"], info.t)) % info.t == 0).all())
+        key = (w, c_n)
+        same_words = None
+        if key in words:
+            same_words = all(np.array_equal(a, b) for a, b in zip(words[key], outs))
+        else:
+            words[key] = outs
+        print(json.dumps({
+            "ablation": name, "paper": paper, "decomp_bits": info.w, "c_n": c_n,
+            "mac_impl": H.he_conv_info(plans[0]), "ms_per_step": ms, "layers_per_s": len(plans) * 1000 / ms,
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "est_noise_log2": info.est_noise_log2, "log2_delta": info.log2_delta,
+            "decrypts_to_plain_conv": decrypt_ok, "words_equal_to_first_mac_form": same_words,
+            "clocks": clk.summary(), "workload": WORKLOAD.replace("c_n=2", f"c_n={c_n}")}), flush=True)
+        H.he_batch_destroy(batch)
+        for plan in plans:
+            H.he_plan_destroy(plan)
+        H.he_galkeys_destroy(gk)
+        H.he_seckey_destroy(sk)
+        H.he_params_destroy(p)
+        del d_ins, d_outs, d_ws
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,13 +492,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hyena", choices=["hyena", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="full", choices=["full", "batch"],
-                    help="batch: only the batched forward, W + K times, no JSON (for profiler captures)")
+    ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation"],
+                    help="batch: only the batched forward, W + K times, no JSON (for profiler captures); "
+                         "ablation: one JSON line per variant of the latency study (reduction, w, c_n, MAC unit)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.mode == "ablation":
+        if rank == 0:
+            run_ablation(args)
         return
     if world > 1:
         import torch

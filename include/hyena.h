@@ -165,7 +165,8 @@ int he_decrypt_slots(const he_params* p, const he_seckey* sk, const uint64_t* ct
 /* ------------------------------------------------------------------ */
 typedef struct {
     uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block (0 -> default) */
-    uint32_t mac_impl;       /* 0 auto, 1 CUDA-core MAC, 2 tensor-core MAC (HE_EINVAL if not exact) */
+    uint32_t mac_impl;       /* 0 auto, 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL if not exact),
+                                3 CUDA-core eager MAC (reduced after every term; for ablations) */
     uint32_t reserved[6];
 } he_tune;
 
@@ -193,7 +194,7 @@ int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_
 /* Synchronises the device and returns HE_ETIMEOUT if a bounded wait inside
  * an earlier forward of this plan gave up (the outputs are then invalid). */
 int he_conv_status(const he_plan* plan);
-/* *mac_impl = 1 (CUDA-core MAC) or 2 (tensor-core MAC) for this plan.  The
+/* *mac_impl = 1 (CUDA-core MAC), 2 (tensor-core MAC) or 3 (eager) for this plan.  The
  * tensor-core form (fp16 10-bit chunks, fp32 sums) is chosen automatically
  * when it is exact: no depthwise, |s| <= 16 and at most 2048 terms. */
 int he_conv_info(const he_plan* plan, int* mac_impl);

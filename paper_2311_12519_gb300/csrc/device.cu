@@ -536,6 +536,52 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
     }
 }
 
+// Eager form, for the ablation of Sec. 3.2.2 only: every CMult is reduced and every HAdd is a
+// modular add, as a conventional implementation would do (the outputs are identical).
+template <bool PACKED, int MAXB>
+__global__ void __launch_bounds__(MAC_THREADS) k_mac_eager(const __grid_constant__ Batch<MAXB> B, KP kp) {
+    constexpr int GT = 4, NR = PACKED ? 2 : 1;
+    const u32 li = find_layer(B, ST_MAC, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
+    const u32 N = kp.N, L = kp.L;
+    const u32 gtiles = (Ly.out_groups + GT - 1) / GT, xt_n = N / MAC_THREADS;
+    const u32 local = blockIdx.x - B.start[ST_MAC][li];
+    const u32 gt = local % gtiles, xt = (local / gtiles) % xt_n, z = local / (gtiles * xt_n);
+    const u32 x = xt * MAC_THREADS + threadIdx.x, g0 = gt * GT;
+    const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
+    const LimbC m = kp.limb[k];
+    const size_t ctw = 2ull * L * N;
+    u64 acc[GT][NR];
+#pragma unroll
+    for (int g = 0; g < GT; g++)
+#pragma unroll
+        for (int r = 0; r < NR; r++) acc[g][r] = 0;
+    const u64* base = Ly.R + ((size_t)p * L + k) * N + x;
+    for (u32 kk = 0; kk < Ly.K; kk++) {
+        const u32 ct = ru * Ly.in_groups + kk / Ly.n_rot, rot = kk % Ly.n_rot;
+        const u64 v = __ldg(base + ((size_t)ct * Ly.n_rot + rot) * ctw);
+#pragma unroll
+        for (int g = 0; g < GT; g++) {
+            if (g0 + g >= Ly.out_groups) break;
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                const int sv = Ly.scal[((size_t)(g0 + g) * NR + r) * Ly.K + kk];
+                const u64 prod = mulmod((u64)(sv < 0 ? -sv : sv), v, m);  // CMult, reduced
+                acc[g][r] = sv < 0 ? (acc[g][r] >= prod ? acc[g][r] - prod : acc[g][r] + m.q - prod)
+                                   : addq(acc[g][r], prod, m.q);             // HAdd, reduced
+            }
+        }
+    }
+    const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+#pragma unroll
+    for (int g = 0; g < GT; g++) {
+        if (g0 + g >= Ly.out_groups) break;
+        u64 out = acc[g][0];
+        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(acc[g][1], pkv, m), m.q);
+        Ly.O[((size_t)(ru * Ly.out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
+    }
+}
+
 // ------------------------------------------------------------------ tensor-core MAC (tcgen05)
 // The same contraction on the 5th-generation tensor cores.  Rows of rotated
 // residues stream into shared memory by bulk asynchronous copies (TC_RAW tiles
@@ -990,10 +1036,10 @@ u64* upload_keys(const he_params* p, const KP& kp, const std::vector<const std::
 
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
-    bool tc = false, packed = false, dw = false;
+    bool tc = false, packed = false, dw = false, eager = false;
     u32 gt = 8;
     bool operator==(const MacVariant& o) const {
-        return tc == o.tc && packed == o.packed && dw == o.dw && (tc || gt == o.gt);
+        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && (tc || eager || gt == o.gt);
     }
 };
 
@@ -1009,6 +1055,7 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
         case ST_NTT: return d.n_ct_in * (L + (p->l == 1 ? 0 : L) + L * p->l * L);
         case ST_KS: return d.n_ks * L * (N / KS_THREADS);
         case ST_MAC:
+            if (s.mv.eager) return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + 3) / 4);
             if (s.mv.tc) return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta);
             return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + s.mv.gt - 1) / s.mv.gt);
         default: return d.n_ct_out * 2 * L;
@@ -1040,6 +1087,11 @@ void mac_cuda_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_
 
 template <int MAXB>
 void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+    if (mv.eager) {
+        if (mv.packed) k_mac_eager<true, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
+        else k_mac_eager<false, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
+        return;
+    }
     if (mv.tc) {
         // persistent: one CTA per SM (the shared-memory footprint allows one), TMEM for the widest layer
         u32 cols = 32;
@@ -1210,7 +1262,7 @@ struct he_plan {
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
     bool packed = false, dw = false;
     u32 mac_groups = 8;
-    bool use_tc = false;
+    bool use_tc = false, eager = false;
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
@@ -1250,7 +1302,7 @@ struct he_plan {
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
         L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
         if (use_tc) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
-        s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups;
+        s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
         return s;
     }
 };
@@ -1335,7 +1387,10 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
         const u32 impl = tune ? tune->mac_impl : 0;
         const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && P->K <= (u32)TC_KMAX;
         if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, K <= 2048 and a non-depthwise layer");
-        P->use_tc = tc_ok && impl != 1;
+        if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
+        if (impl > 3) fail(HE_EINVAL, "mac_impl must be 0..3");
+        P->eager = impl == 3;
+        P->use_tc = tc_ok && impl != 1 && impl != 3;
         if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
         // device data
         CUDA_OK(cudaGetDevice(&P->device));
@@ -1470,7 +1525,7 @@ extern "C" int he_conv_status(const he_plan* plan) {
 extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
     return guard([&] {
         if (!plan || !mac_impl) fail(HE_EINVAL, "null argument");
-        *mac_impl = plan->use_tc ? 2 : 1;
+        *mac_impl = plan->use_tc ? 2 : (plan->eager ? 3 : 1);
     });
 }
 

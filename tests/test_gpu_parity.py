@@ -225,10 +225,21 @@ def test_repeat_on_side_stream_and_host_path(small):
 
 
 # ---------------------------------------------------------------- both MAC implementations
-@pytest.mark.parametrize("impl", [1, 2])
+@pytest.mark.parametrize("impl", [1, 2, 3])
 @pytest.mark.parametrize("spec", [SMALL[0], SMALL[1], SMALL[4], SMALL[7], SMALL[11]])
 def test_mac_implementations(small, spec, impl):
+    """1 lazy CUDA-core, 2 tensor-core, 3 eager (reduced after every CMult and HAdd, Sec. 3.2.2's
+    conventional form): all three give the oracle's words."""
     small.layer(spec, mac_impl=impl)
+
+
+def test_eager_mac_rejects_depthwise(small):
+    d = H.conv_desc(**SMALL[2])
+    gk = H.he_galois_keys(small.p, small.sk, H.he_layer_galois(small.p, d), synth.SEED_KEYS)
+    with pytest.raises(H.HyenaError) as e:
+        H.he_conv_plan(small.p, gk, d, synth.weights((4, 1, 3, 3)), mac_impl=3)
+    assert e.value.code == H.HE_EINVAL
+    H.he_galkeys_destroy(gk)
 
 
 def test_tensor_core_mac_is_chosen_when_exact(small):
@@ -280,9 +291,9 @@ def _plan_and_inputs(S, spec, label, mac_impl=0):
 
 
 def test_batch_equals_single_layers(small):
-    """One launch per stage over mixed layers (packed, unpacked, depthwise, 1x1, both MAC kinds)."""
-    specs = [SMALL[0], SMALL[1], SMALL[2], SMALL[3], SMALL[7], SMALL[11], SMALL[5]]
-    impls = [0, 1, 0, 0, 2, 1, 0]
+    """One launch per stage over mixed layers (packed, unpacked, depthwise, 1x1, all three MAC kinds)."""
+    specs = [SMALL[0], SMALL[1], SMALL[2], SMALL[3], SMALL[7], SMALL[11], SMALL[5], SMALL[4], SMALL[8]]
+    impls = [0, 1, 0, 0, 2, 1, 0, 3, 3]
     items = [_plan_and_inputs(small, sp, i, impl) for i, (sp, impl) in enumerate(zip(specs, impls))]
     plans = [it[0] for it in items]
     refs, d_ins, d_outs = [], [], []

@@ -2,11 +2,15 @@
 
 Workload: the 19 3x3 convolutions of a ResNet-20 on 32x32 inputs, one image
 per GPU, N = 8192, L = 3 RNS limbs of 50 bits, t = 1032193, Hyena packing
-(c_n = 2), plain per-layer kernels.  A step runs all 19 layers once through
-he_conv_forward on fresh synthetic ciphertexts resident in HBM.  value =
-layers/s over all ranks; modMAC/s is reported beside it.  e2e repeats the
-step through he_conv_forward_host with pinned host buffers (copies inside
-the timed region).  --impl reference times the CPU oracle instead.
+(c_n = 2).  A step runs all 19 layers once on fresh synthetic ciphertexts
+resident in HBM.  value = layers/s over all ranks of the batched form (one
+launch per stage for all layers, replayed as a CUDA graph); the plain
+per-layer form (he_conv_forward per layer) is reported beside it, with
+modMAC/s.  e2e repeats the step through he_conv_forward_host with pinned
+host buffers (copies inside the timed region).  --workload vgg16|mobilenet
+measures the VGG-16 (8 images, N = 16384) or MobileNetV1 (32 images) stack
+the same way; --mode ablation prints one line per variant of the latency
+study; --impl reference times the CPU oracle instead.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under
 torch.distributed.run (one process per GPU, no collective on the data path).
@@ -31,6 +35,14 @@ import synth  # noqa: E402
 
 N_RING, L_LIMBS, LIMB_BITS = 8192, 3, 50
 WORKLOAD = "resnet20-3x3-stack, 32x32, 1 image/GPU, N=8192, L=3x50-bit, t=1032193, c_n=2"
+# other stacks (not the headline): name -> (shapes, N, L, images per GPU, batch workspace limit, description)
+WORKLOADS = {
+    "resnet20": (synth.resnet20_convs, N_RING, L_LIMBS, 1, None, WORKLOAD),
+    "vgg16": (synth.vgg16_convs, 16384, 4, 8, 64 << 30,
+              "vgg16-3x3-stack, 224x224, 8 images/GPU, N=16384, L=4x50-bit, t=786433, c_n=2"),
+    "mobilenet": (synth.mobilenet_v1_convs, 8192, 4, 32, 64 << 30,
+                  "mobilenetv1-dw+pw-stack, 224x224, 32 images/GPU, N=8192, L=4x50-bit, t=1032193, c_n=2"),
+}
 METRIC = "HE-conv layers/s (ResNet-20 stack, bit-exact)"
 L2_BYTES = 129 * 2**20
 # DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
@@ -40,9 +52,10 @@ PROFILED_TRAFFIC = {"source": "03c81fc60a59f009", "k_keyswitch": 2.712e9, "k_mac
                     "k_intt": 0.223e9}
 
 
-def layer_descs():
+def layer_descs(workload="resnet20"):
+    shapes, _, _, images, _, _ = WORKLOADS[workload]
     return [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
-                 n_images=1, c_n=2) for s in synth.resnet20_convs()]
+                 n_images=images, c_n=2) for s in shapes()]
 
 
 def modmacs(spec, lay, n_rot, L, l, N):
@@ -165,11 +178,13 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    p = H.he_params_create(N_RING, L_LIMBS, limb_bits=LIMB_BITS, decomp_bits=0, est_mac_terms=64 * 9)
+    _, n_ring, n_limbs, images, ws_limit, workload = WORKLOADS[args.workload]
+    specs = layer_descs(args.workload)
+    k_max = max(s["kh"] ** 2 * (1 if s["depthwise"] else s["C_in"]) for s in specs)
+    p = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=0, est_mac_terms=k_max)
     info = H.he_params_info(p)
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
-    specs = layer_descs()
     descs = [H.conv_desc(**s) for s in specs]
     gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
     gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
@@ -178,13 +193,13 @@ def run_gpu(args, rank, world):
     stage_bytes = {"ntt_in": 0, "keyswitch": 0, "mac": 0, "ntt_out": 0}
     for i, (s, d) in enumerate(zip(specs, descs)):
         ri = rank_inputs(rank)
-        act = synth.activations((1, s["C_in"], s["H"], s["W"]), info.t, label=i + ri["act_label"])
-        wt = synth.weights((s["C_out"], s["C_in"], s["kh"], s["kh"]), label=i)
+        act = synth.activations((images, s["C_in"], s["H"], s["W"]), info.t, label=i + ri["act_label"])
+        wt = synth.weights((s["C_out"], 1 if s["depthwise"] else s["C_in"], s["kh"], s["kh"]), label=i)
         cts = H.he_encrypt_image(p, sk, d, act, ri["enc_seed"], info)
         plan = H.he_conv_plan(p, gk, d, wt)
         n_in, n_out, ws = H.he_conv_sizes(plan)
         lay = H.he_layout_for_layer(p, d)
-        n_rot = s["kh"] ** 2 * 2
+        n_rot = s["kh"] ** 2 * (1 if s["depthwise"] else 2)
         cm, km = modmacs(s, lay, n_rot, L, l, N)
         conv_mm += cm
         ks_mm += km
@@ -205,11 +220,12 @@ def run_gpu(args, rank, world):
         ws_max = max(ws_max, ws)
         in_bytes += n_in * 8
         out_bytes += n_out * 8
-    d_ws = torch.empty(ws_max // 8 + 1, dtype=torch.int64, device=dev)
+    # the batch runs in waves under the workspace limit; the plain per-layer form shares its workspace
+    batch = H.he_batch_create(plans) if ws_limit is None else H.he_batch_create_limited(plans, ws_limit)
+    d_ws = torch.empty(max(ws_max, H.he_batch_workspace_bytes(batch)) // 8 + 1, dtype=torch.int64, device=dev)
+    d_wsb = d_ws
     if args.mode == "batch":
-        # profiler mode: per step one launch per stage (4 kernels), nothing else on the GPU
-        batch = H.he_batch_create(plans)
-        d_wsb = torch.empty(H.he_batch_workspace_bytes(batch) // 8 + 1, dtype=torch.int64, device=dev)
+        # profiler mode: per step one launch per stage and wave, nothing else on the GPU
         ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
         torch.cuda.synchronize()
         for _ in range(args.warmup + args.steps):
@@ -256,8 +272,6 @@ def run_gpu(args, rank, world):
         stages = H.he_profile_collect()
         ms_plain = sum(e0.elapsed_time(e1) for e0, e1 in ev)
         # batched form: one launch per stage for all layers, replayed as a CUDA graph
-        batch = H.he_batch_create(plans)
-        d_wsb = torch.empty(H.he_batch_workspace_bytes(batch) // 8 + 1, dtype=torch.int64, device=dev)
         ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
 
         def step_batch():
@@ -344,14 +358,16 @@ def run_gpu(args, rank, world):
     roof["stage_share"] = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages_b.values())), 4)
                            for k, v in stages_b.items()}
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "resnet20":
         times, desc = oracle_sample(reps=1)
         cpu = {"value": 1.0 / times[0], "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": desc}
     line = {
-        "metric": METRIC, "value": layers_per_s, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "resnet20" else METRIC.replace("ResNet-20", args.workload),
+        "value": layers_per_s, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "layers_per_step": n_layers, "images_per_gpu": 1,
+        "config": {"workload": workload, "layers_per_step": n_layers, "images_per_gpu": images,
+                   "batch_waves": H.he_batch_waves(batch),
                    "l2": "flushed before each timed step (256 MiB write)", "decomp_bits": info.w,
                    "parallelism": f"replicas x{world} (independent images, no collective)"},
         "modmac_per_s": (conv_mm + ks_mm) * world * args.steps / (ms / 1000),
@@ -363,7 +379,8 @@ def run_gpu(args, rank, world):
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clk_b.summary(),
-        "form": "batched: one launch per stage for all 19 layers, replayed as a CUDA graph",
+        "form": f"batched: one launch per stage for all {n_layers} layers of each of {H.he_batch_waves(batch)} "
+                "workspace wave(s), replayed as a CUDA graph",
         "plain_per_layer": {"value": layers_per_second(world, n_layers, args.steps, ms_plain / 1000),
                             "unit": "layers/s", "ms_per_step": ms_plain / args.steps,
                             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
@@ -492,6 +509,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hyena", choices=["hyena", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="resnet20", choices=sorted(WORKLOADS),
+                    help="the headline ResNet-20 stack, or the VGG-16 (8 images) or MobileNetV1 (32 images) stack")
     ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation"],
                     help="batch: only the batched forward, W + K times, no JSON (for profiler captures); "
                          "ablation: one JSON line per variant of the latency study (reduction, w, c_n, MAC unit)")

@@ -235,7 +235,18 @@ int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in, uint64_t*
  * one device.  The batch keeps pointers to the plans, which must outlive it. */
 typedef struct he_batch he_batch;
 int he_batch_create(const he_plan* const* plans, int n, he_batch** out);
-/* Device workspace for one he_batch_forward (layers get disjoint regions). */
+/* The same, with the layers split into waves whose workspaces together fit
+ * max_workspace_bytes (first fit, largest workspace first).  Waves run one
+ * after another and reuse one workspace region, so a stack larger than the
+ * device (VGG-16 on 8 images needs over 100 GB of rotated copies) runs in
+ * one call; each wave still launches each stage once for all its layers.  A
+ * layer whose own workspace exceeds the limit gets a wave of its own, and the
+ * workspace is then that layer's.  he_batch_create is this with no limit. */
+int he_batch_create_limited(const he_plan* const* plans, int n, size_t max_workspace_bytes, he_batch** out);
+/* *n_waves = the number of waves the batch runs in. */
+int he_batch_waves(const he_batch* b, int* n_waves);
+/* Device workspace for one he_batch_forward: the largest wave's (layers of a
+ * wave get disjoint regions). */
 int he_batch_workspace_bytes(const he_batch* b, size_t* bytes);
 /* d_in[i], d_out[i]: device buffers of plan i (sizes from he_conv_sizes). */
 int he_batch_forward(const he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_workspace,

@@ -44,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     host_o = os.path.join(OUT_DIR, "host.o")
     dev_o = os.path.join(OUT_DIR, "device.o")
     cmds = [
-        ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-c", os.path.join(CSRC, "host.cpp"), "-o", host_o] + inc,
+        ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-c", os.path.join(CSRC, "host.cpp"), "-o", host_o] + inc,
         [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v" if verbose else "-O3",
          "-c", os.path.join(CSRC, "device.cu"), "-o", dev_o] + inc,
     ]
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if pr.returncode != 0:
             raise RuntimeError(f"build failed: {' '.join(c)}\n{out}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, host_o, dev_o], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, host_o, dev_o], check=True)
     os.replace(tmp, LIB)
     return LIB
 

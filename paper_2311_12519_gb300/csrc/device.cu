@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <memory>
 
@@ -1536,6 +1537,8 @@ struct he_batch {
     std::vector<const he_plan*> plans;
     const he_params* p = nullptr;
     int device = 0;
+    // layers run in waves that reuse one workspace region; ws_off is a layer's offset inside it
+    std::vector<std::vector<u32>> waves;
     std::vector<size_t> ws_off;
     size_t ws_bytes = 0;
     // captured graph and the pointers it was captured with
@@ -1546,30 +1549,61 @@ struct he_batch {
     ~he_batch() {
         if (exec) cudaGraphExecDestroy(exec);
     }
-    std::vector<StageLayer> layers(const uint64_t* const* d_in, uint64_t* const* d_out, char* ws) const {
+    std::vector<StageLayer> layers(const std::vector<u32>& wave, const uint64_t* const* d_in, uint64_t* const* d_out,
+                                   char* ws) const {
         std::vector<StageLayer> ls;
-        for (size_t i = 0; i < plans.size(); i++) ls.push_back(plans[i]->stage_layer(d_in[i], d_out[i], ws + ws_off[i]));
+        for (u32 i : wave) ls.push_back(plans[i]->stage_layer(d_in[i], d_out[i], ws + ws_off[i]));
         return ls;
+    }
+    void run(const uint64_t* const* d_in, uint64_t* const* d_out, char* ws, cudaStream_t s, bool timed) const {
+        for (const auto& w : waves) run_layers(p, plans[0]->kp, layers(w, d_in, d_out, ws), s, timed);
     }
 };
 
-extern "C" int he_batch_create(const he_plan* const* plans, int n, he_batch** out) {
+extern "C" int he_batch_create_limited(const he_plan* const* plans, int n, size_t max_workspace_bytes,
+                                       he_batch** out) {
     return guard([&] {
         if (!plans || n <= 0 || !out) fail(HE_EINVAL, "bad argument");
         auto B = std::make_unique<he_batch>();
         B->p = plans[0]->p;
         B->device = plans[0]->device;
-        size_t off = 0;
         for (int i = 0; i < n; i++) {
             if (!plans[i]) fail(HE_EINVAL, "null plan");
             if (plans[i]->p != B->p) fail(HE_EINVAL, "all plans of a batch must share their parameters");
             if (plans[i]->device != B->device) fail(HE_EINVAL, "all plans of a batch must be on one device");
             B->plans.push_back(plans[i]);
-            B->ws_off.push_back(off);
-            off = align256(off + plans[i]->ws_bytes);
         }
-        B->ws_bytes = off;
+        // first fit, largest workspace first; a layer larger than the limit gets a wave of its own
+        std::vector<u32> order(n);
+        for (int i = 0; i < n; i++) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](u32 a, u32 b) { return plans[a]->ws_bytes > plans[b]->ws_bytes; });
+        std::vector<size_t> used;
+        B->ws_off.assign(n, 0);
+        for (u32 i : order) {
+            const size_t need = align256(plans[i]->ws_bytes);
+            size_t w = 0;
+            while (w < used.size() && used[w] + need > max_workspace_bytes) w++;
+            if (w == used.size()) used.push_back(0), B->waves.emplace_back();
+            B->ws_off[i] = used[w];
+            used[w] += need;
+            B->waves[w].push_back(i);
+        }
+        // layers of a wave in their given order
+        for (auto& w : B->waves) std::sort(w.begin(), w.end());
+        for (size_t u : used) B->ws_bytes = std::max(B->ws_bytes, u);
         *out = B.release();
+    });
+}
+
+extern "C" int he_batch_create(const he_plan* const* plans, int n, he_batch** out) {
+    return he_batch_create_limited(plans, n, SIZE_MAX, out);
+}
+
+extern "C" int he_batch_waves(const he_batch* b, int* n_waves) {
+    return guard([&] {
+        if (!b || !n_waves) fail(HE_EINVAL, "null argument");
+        *n_waves = (int)b->waves.size();
     });
 }
 
@@ -1586,7 +1620,7 @@ extern "C" int he_batch_forward(const he_batch* b, const uint64_t* const* d_in, 
         if (!b || !d_in || !d_out || !d_ws) fail(HE_EINVAL, "null argument");
         check_device(b->device);
         for (size_t i = 0; i < b->plans.size(); i++) check_ptrs(d_in[i], d_out[i], d_ws);
-        run_layers(b->p, b->plans[0]->kp, b->layers(d_in, d_out, (char*)d_ws), (cudaStream_t)stream, true);
+        b->run(d_in, d_out, (char*)d_ws, (cudaStream_t)stream, true);
     });
 }
 
@@ -1604,13 +1638,12 @@ extern "C" int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, u
                 cudaGraphExecDestroy(b->exec);
                 b->exec = nullptr;
             }
-            std::vector<StageLayer> ls = b->layers(d_in, d_out, (char*)d_ws);
             // one ordinary pass sets the kernels' attributes before capture
-            run_layers(b->p, b->plans[0]->kp, ls, s, false);
+            b->run(d_in, d_out, (char*)d_ws, s, false);
             cudaGraph_t g = nullptr;
             CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             try {
-                run_layers(b->p, b->plans[0]->kp, ls, s, false);
+                b->run(d_in, d_out, (char*)d_ws, s, false);
             } catch (...) {
                 cudaStreamEndCapture(s, &g);
                 if (g) cudaGraphDestroy(g);

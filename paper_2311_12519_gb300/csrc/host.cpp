@@ -3,10 +3,14 @@
 // layer (Sec. 2.4, Sec. 3.1) and the noise estimate that picks the key
 // switching base.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 
 #include "internal.h"
 
@@ -319,14 +323,41 @@ static void sample_gauss(const he_params* p, u64 key, i64* out) {
 
 // ------------------------------------------------------------------ ring helpers
 // c = a * b mod (X^N + 1, q_k) with b given by signed small coefficients
-static void mul_small(const he_params* p, u32 k, const u64* a, const i64* b, u64* c) {
+// c = a * s in limb k, with the secret's NTT from key generation
+static void mul_secret(const he_params* p, const he_seckey* sk, u32 k, const u64* a, u64* c) {
     const HostNtt& T = p->ntt[k];
-    std::vector<u64> A(a, a + p->N), Bv(p->N);
-    for (u32 n = 0; n < p->N; n++) Bv[n] = p->mod[k].from_signed(b[n]);
+    const u64* S = sk->s_ntt.data() + (size_t)k * p->N;
+    std::vector<u64> A(a, a + p->N);
     T.forward(A.data());
-    T.forward(Bv.data());
-    for (u32 n = 0; n < p->N; n++) c[n] = p->mod[k].mul(A[n], Bv[n]);
+    for (u32 n = 0; n < p->N; n++) c[n] = p->mod[k].mul(A[n], S[n]);
     T.inverse(c);
+}
+// Runs fn(i) for every i in [0, n) on up to 64 host threads; independent items only.  The
+// first exception a worker throws is rethrown here after all workers have stopped.
+template <class F>
+static void parallel_for(u32 n, F fn) {
+    const u32 T = std::min<u32>({n, 64u, std::max(1u, std::thread::hardware_concurrency())});
+    if (T <= 1) {
+        for (u32 i = 0; i < n; i++) fn(i);
+        return;
+    }
+    std::atomic<u32> next{0};
+    std::exception_ptr err;
+    std::mutex mu;
+    auto work = [&] {
+        try {
+            for (u32 i = next++; i < n; i = next++) fn(i);
+        } catch (...) {
+            std::lock_guard<std::mutex> g(mu);
+            if (!err) err = std::current_exception();
+            next = n;
+        }
+    };
+    std::vector<std::thread> th;
+    for (u32 t = 1; t < T; t++) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+    if (err) std::rethrow_exception(err);
 }
 // sigma_g on signed coefficients: X^i -> X^(i g mod 2N), negated past N
 static void automorph_signed(u32 N, u32 g, const i64* a, i64* out) {
@@ -517,6 +548,12 @@ extern "C" int he_keygen(const he_params* p, uint64_t seed, he_seckey** out) {
         sk->s.resize(p->N);
         u64 key = SplitMix::stream(seed, TAG_SECRET, 0, 0);
         for (u32 n = 0; n < p->N; n++) sk->s[n] = (i64)(SplitMix::at(key, n) % 3) - 1;
+        sk->s_ntt.resize((size_t)p->L * p->N);
+        for (u32 k = 0; k < p->L; k++) {
+            u64* S = sk->s_ntt.data() + (size_t)k * p->N;
+            for (u32 n = 0; n < p->N; n++) S[n] = p->mod[k].from_signed(sk->s[n]);
+            p->ntt[k].forward(S);
+        }
         *out = sk.release();
     });
 }
@@ -536,12 +573,17 @@ extern "C" int he_galois_keys(const he_params* p, const he_seckey* sk, const uin
         const u32 N = p->N, L = p->L, l = p->l;
         auto gk = std::make_unique<he_galkeys>();
         gk->p = p;
-        std::vector<i64> sg(N), e(N);
-        std::vector<u64> a((size_t)L * N), as(N);
         for (int gi = 0; gi < n; gi++) {
             u32 g = galois[gi];
             if ((g & 1) == 0 || g >= 2 * N || g == 1) fail(HE_EINVAL, "Galois element must be odd, in [3, 2N)");
-            if (gk->find(g)) continue;
+            if (std::find(gk->galois.begin(), gk->galois.end(), g) == gk->galois.end()) gk->galois.push_back(g);
+        }
+        gk->keys.resize(gk->galois.size());
+        // every (element, digit) key is drawn from its own counter stream, so elements are independent
+        parallel_for((u32)gk->galois.size(), [&](u32 gi) {
+            const u32 g = gk->galois[gi];
+            std::vector<i64> sg(N), e(N);
+            std::vector<u64> a((size_t)L * N), as(N);
             automorph_signed(N, g, sk->s.data(), sg.data());
             std::vector<u64> key((size_t)L * l * 2 * L * N);
             for (u32 i = 0; i < L; i++)
@@ -551,7 +593,7 @@ extern "C" int he_galois_keys(const he_params* p, const he_seckey* sk, const uin
                     sample_gauss(p, SplitMix::stream(seed, TAG_KSK_E, g, dd), e.data());
                     for (u32 k = 0; k < L; k++) {
                         const Modulus& m = p->mod[k];
-                        mul_small(p, k, a.data() + (size_t)k * N, sk->s.data(), as.data());
+                        mul_secret(p, sk, k, a.data() + (size_t)k * N, as.data());
                         u64 gadget = (k == i) ? m.pow(2, (u64)p->w * j) : 0;
                         u64* b_out = key.data() + (((size_t)dd * 2 + 0) * L + k) * N;
                         u64* a_out = key.data() + (((size_t)dd * 2 + 1) * L + k) * N;
@@ -563,9 +605,8 @@ extern "C" int he_galois_keys(const he_params* p, const he_seckey* sk, const uin
                         }
                     }
                 }
-            gk->galois.push_back(g);
-            gk->keys.push_back(std::move(key));
-        }
+            gk->keys[gi] = std::move(key);
+        });
         *out = gk.release();
     });
 }
@@ -598,7 +639,7 @@ static void encrypt_poly(const he_params* p, const he_seckey* sk, const std::vec
     sample_gauss(p, SplitMix::stream(seed, TAG_ENC_E, index, 0), e.data());
     for (u32 k = 0; k < L; k++) {
         const Modulus& md = p->mod[k];
-        mul_small(p, k, a.data() + (size_t)k * N, sk->s.data(), as.data());
+        mul_secret(p, sk, k, a.data() + (size_t)k * N, as.data());
         u64* c0 = ct + (size_t)k * N;
         u64* c1 = ct + (size_t)(L + k) * N;
         for (u32 x = 0; x < N; x++) {
@@ -614,7 +655,7 @@ static void decrypt_poly(const he_params* p, const he_seckey* sk, const u64* ct,
     const u32 N = p->N, L = p->L;
     std::vector<u64> ph((size_t)L * N), cs(N);
     for (u32 k = 0; k < L; k++) {
-        mul_small(p, k, ct + (size_t)(L + k) * N, sk->s.data(), cs.data());
+        mul_secret(p, sk, k, ct + (size_t)(L + k) * N, cs.data());
         for (u32 x = 0; x < N; x++) ph[(size_t)k * N + x] = p->mod[k].add(ct[(size_t)k * N + x], cs[x]);
     }
     m.assign(N, 0);
@@ -801,12 +842,12 @@ extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const h
                 }
             }
         }
-        std::vector<u64> m;
         const size_t ctw = 2ULL * p->L * N;
-        for (u32 c = 0; c < lay.n_ct_in; c++) {
+        parallel_for(lay.n_ct_in, [&](u32 c) {  // ciphertext c draws from its own counter streams
+            std::vector<u64> m;
             encode_slots(p, slots.data() + (size_t)c * N, m);
             encrypt_poly(p, sk, m, seed, c, ct_out + c * ctw);
-        }
+        });
     });
 }
 
@@ -820,11 +861,11 @@ extern "C" int he_decrypt_image(const he_params* p, const he_seckey* sk, const h
         const u32 per_ct = lay.blocks_per_row * (d->c_n == 1 ? 2 : 1);
         const size_t ctw = 2ULL * p->L * N;
         std::vector<int64_t> slots((size_t)lay.n_ct_out * N);
-        std::vector<u64> m;
-        for (u32 c = 0; c < lay.n_ct_out; c++) {
+        parallel_for(lay.n_ct_out, [&](u32 c) {
+            std::vector<u64> m;
             decrypt_poly(p, sk, ct + c * ctw, m);
             decode_slots(p, m, slots.data() + (size_t)c * N);
-        }
+        });
         u64 inv = unscale ? p->mod_t.inv(lay.scale % p->t) : 1;
         std::memset(out, 0, sizeof(int64_t) * (size_t)d->n_images * d->C_out * lay.Ho * lay.Wo);
         for (u32 unit = 0; unit < lay.units; unit++) {

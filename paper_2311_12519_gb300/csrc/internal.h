@@ -148,6 +148,7 @@ struct he_params {
 struct he_seckey {
     const he_params* p = nullptr;
     std::vector<hy::i64> s;
+    std::vector<hy::u64> s_ntt;  // [L][N]: s in each limb, host NTT form, for the products a*s
 };
 
 struct he_galkeys {

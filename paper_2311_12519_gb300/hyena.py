@@ -103,6 +103,8 @@ def load(build_if_stale: bool = True):
         "he_conv_status": (ctypes.c_int, [vp]),
         "he_conv_info": (ctypes.c_int, [vp, P(ctypes.c_int)]),
         "he_batch_create": (ctypes.c_int, [vp, ctypes.c_int, P(vp)]),
+        "he_batch_create_limited": (ctypes.c_int, [vp, ctypes.c_int, sz, P(vp)]),
+        "he_batch_waves": (ctypes.c_int, [vp, P(ctypes.c_int)]),
         "he_batch_workspace_bytes": (ctypes.c_int, [vp, P(sz)]),
         "he_batch_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "he_batch_graph_launch": (ctypes.c_int, [vp, vp, vp, vp, vp]),
@@ -305,6 +307,20 @@ def he_batch_create(plans):
     h = vp()
     _check(load().he_batch_create(arr, len(plans), ctypes.byref(h)), "he_batch_create")
     return h.value
+
+
+def he_batch_create_limited(plans, max_workspace_bytes):
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = vp()
+    _check(load().he_batch_create_limited(arr, len(plans), max_workspace_bytes, ctypes.byref(h)),
+           "he_batch_create_limited")
+    return h.value
+
+
+def he_batch_waves(b):
+    v = ctypes.c_int()
+    _check(load().he_batch_waves(b, ctypes.byref(v)), "he_batch_waves")
+    return v.value
 
 
 def he_batch_workspace_bytes(b):

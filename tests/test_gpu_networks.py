@@ -1,0 +1,115 @@
+"""Full-size network stacks on the GPU, batched in waves under a workspace limit.
+
+  * VGG-16: the 13 3x3 convolutions on 8 images of 224x224, N = 16384, L = 4
+    (6128 input and 8704 output ciphertexts, over 100 GB of rotated copies in
+    all, so the batch runs in waves that share one workspace region).
+  * MobileNetV1: the 27 convolutions (3x3 depthwise and 1x1 pointwise) on 32
+    images of 224x224, N = 8192, L = 4, mixed layer sizes in one batch.
+
+For every layer the batched output equals he_conv_forward of that layer word
+for word (the bar is bit-exactness).  In sampled layers, sampled output
+ciphertexts are recomputed by the oracle from the same input ciphertexts, and
+every output of those layers is decrypted against the plain convolution.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import bfv, conv  # noqa: E402
+from oracle import params as prm  # noqa: E402
+from paper_2311_12519_gb300 import hyena as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+WAVE_LIMIT = 40 << 30  # bytes of workspace per wave
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
+    p = H.he_params_create(N, L, decomp_bits=50)
+    info = H.he_params_info(p)
+    sk = H.he_keygen(p, synth.SEED_KEYS)
+    specs = [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
+                  n_images=n_images, c_n=2) for s in shapes]
+    descs = [H.conv_desc(**sp) for sp in specs]
+    gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
+    gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
+    plans, d_ins, d_outs, host_in, acts, wts = [], [], [], [], [], []
+    for i, (sp, d) in enumerate(zip(specs, descs)):
+        act = synth.activations((n_images, sp["C_in"], sp["H"], sp["W"]), info.t, label=i)
+        wt = synth.weights((sp["C_out"], 1 if sp["depthwise"] else sp["C_in"], sp["kh"], sp["kh"]), label=i)
+        cts = H.he_encrypt_image(p, sk, d, act, synth.SEED_ENC + i, info)
+        plans.append(H.he_conv_plan(p, gk, d, wt))
+        n_in, n_out, _ = H.he_conv_sizes(plans[-1])
+        assert n_in == cts.size
+        d_ins.append(torch.from_numpy(cts.reshape(-1).view(np.int64)).cuda())
+        d_outs.append(torch.full((n_out,), -1, dtype=torch.int64, device="cuda"))
+        keep = i in oracle_samples or i in decrypt_layers
+        host_in.append(cts if i in oracle_samples else None)
+        acts.append(act if keep else None)
+        wts.append(wt if keep else None)
+    b = H.he_batch_create_limited(plans, WAVE_LIMIT)
+    assert H.he_batch_waves(b) >= 2, "the stack should need more than one wave at this limit"
+    ws_bytes = H.he_batch_workspace_bytes(b)
+    assert ws_bytes <= WAVE_LIMIT or ws_bytes == max(H.he_conv_sizes(pl)[2] for pl in plans)
+    ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    H.he_batch_graph_launch(b, [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(),
+                            s.cuda_stream)
+    s.synchronize()
+    for plan in plans:
+        H.he_conv_status(plan)
+    # batched = plain per-layer, every layer, word for word (the workspace is free again)
+    tmp = torch.empty(max(t.numel() for t in d_outs), dtype=torch.int64, device="cuda")
+    for i, plan in enumerate(plans):
+        n_out = d_outs[i].numel()
+        tmp[:n_out].fill_(-1)
+        H.he_conv_forward(plan, d_ins[i].data_ptr(), tmp.data_ptr(), ws.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(tmp[:n_out], d_outs[i]), f"layer {i}: batched output differs from he_conv_forward"
+    del tmp, ws
+    # sampled output ciphertexts against the oracle, from the same input ciphertexts
+    P = prm.make_params(N=N, L=L, w=50)
+    s_or = bfv.keygen(P, synth.SEED_KEYS)
+    ksk = {}
+    for i, cts in sorted(oracle_samples.items()):
+        sp = specs[i]
+        ol = conv.Layout(N=N, **sp)
+        gs = H.he_layer_galois(p, descs[i])
+        for g in gs:
+            if g not in ksk:
+                ksk[g] = bfv.galois_key(P, s_or, g, synth.SEED_KEYS)
+        out = d_outs[i].cpu().numpy().view(np.uint64).reshape(-1, 2, L, N)
+        ref = conv.he_conv(P, ol, wts[i], host_in[i], ksk, out_cts=cts)
+        for c in cts:
+            assert (out[c] == ref[c]).all(), f"layer {i}, ciphertext {c} differs from the oracle"
+    for i in decrypt_layers:
+        sp = specs[i]
+        out = d_outs[i].cpu().numpy().view(np.uint64).reshape(-1, 2, L, N)
+        dec = H.he_decrypt_image(p, sk, descs[i], out)
+        plain = conv.conv_plain(acts[i], wts[i], sp["stride"], (sp["kh"] - 1) // 2, sp["depthwise"], info.t)
+        assert (dec == plain).all(), f"layer {i}: decryption differs from the plain convolution"
+    H.he_batch_destroy(b)
+    for plan in plans:
+        H.he_plan_destroy(plan)
+    H.he_galkeys_destroy(gk)
+    H.he_seckey_destroy(sk)
+    H.he_params_destroy(p)
+
+
+def test_vgg16_stack_8_images_batched_in_waves():
+    shapes = synth.vgg16_convs()
+    _run_stack(16384, 4, shapes, 8, oracle_samples={0: [0, 1791], 6: [5], 12: [0]}, decrypt_layers=[0, 12])
+
+
+def test_mobilenet_v1_stack_32_images_batched_in_waves():
+    shapes = synth.mobilenet_v1_convs()
+    _run_stack(8192, 4, shapes, 32, oracle_samples={0: [3], 3: [0, 77], 26: [0]}, decrypt_layers=[0, 3, 26])

@@ -195,8 +195,9 @@ int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_
  * an earlier forward of this plan gave up (the outputs are then invalid). */
 int he_conv_status(const he_plan* plan);
 /* *mac_impl = 1 (CUDA-core MAC), 2 (tensor-core MAC) or 3 (eager) for this plan.  The
- * tensor-core form (fp16 10-bit chunks, fp32 sums) is chosen automatically
- * when it is exact: no depthwise, |s| <= 16 and at most 2048 terms. */
+ * tensor-core form (fp16 10-bit chunks, fp32 sums of at most 2048 terms per
+ * accumulation) is chosen automatically when it is exact: no depthwise and
+ * |s| <= 16. */
 int he_conv_info(const he_plan* plan, int* mac_impl);
 void he_plan_destroy(he_plan* plan);
 

@@ -418,7 +418,40 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
     }
     const size_t ctw = 2ull * L * N;
     const u32 r_slots = Ly.r_slots, r_id = Ly.r_id;
+    if (m.sm1 == 49) {
+        // 50-bit limbs: halves below 2^25, so the Karatsuba middle term (a0 + a1)(b0 + b1) - a0 b0 - a1 b1
+        // needs one multiply-add per product instead of two; its factors stay below 2^26 and the sums of
+        // at most 16 digit terms below 2^57.  The two subtractions are taken once per sum.
+        u32 k0s[LL], k1s[LL];
+#pragma unroll
+        for (int dd = 0; dd < LL; dd++) k0s[dd] = k0l[dd] + k0h[dd], k1s[dd] = k1l[dd] + k1h[dd];
 #pragma unroll 4
+        for (u32 c = 0; c < Ly.n_ct_in; c++) {
+            const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
+            u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
+#pragma unroll
+            for (int dd = 0; dd < LL; dd++) {
+                const u64 dv = Dc[(size_t)dd * L * N];
+                const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
+                mad_wide_u(lo0, dl, k0l[dd]);
+                mad_wide_u(hi0, dh, k0h[dd]);
+                mad_wide_u(mid0, ds, k0s[dd]);
+                mad_wide_u(lo1, dl, k1l[dd]);
+                mad_wide_u(hi1, dh, k1h[dd]);
+                mad_wide_u(mid1, ds, k1s[dd]);
+            }
+            mid0 -= lo0 + hi0;
+            mid1 -= lo1 + hi1;
+            u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
+            lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];  // + sigma(c0); lo stays below 2^57
+            const u64 r0 = bred_split50(lo0, mid0, hi0, m), r1 = bred_split50(lo1, mid1, hi1, m);
+            // R streams out once and is read once by the MAC: evict-first keeps D and the keys in L2
+            __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), r0);
+            __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)(L + k) * N + x), r1);
+        }
+        return;
+    }
+#pragma unroll 2
     for (u32 c = 0; c < Ly.n_ct_in; c++) {
         const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
         u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
@@ -436,16 +469,9 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             mad_wide_u(hi1, dh, k1h[dd]);
         }
         u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
-        lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];  // + sigma(c0); lo stays below 2^57
-        u64 r0, r1;
-        if (m.sm1 == 49) {
-            r0 = bred_split50(lo0, mid0, hi0, m);
-            r1 = bred_split50(lo1, mid1, hi1, m);
-        } else {
-            r0 = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
-            r1 = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
-        }
-        // R streams out once and is read once by the MAC: evict-first keeps D and the keys in L2
+        lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];
+        const u64 r0 = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
+        const u64 r1 = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
         __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), r0);
         __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)(L + k) * N + x), r1);
     }
@@ -537,11 +563,13 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
     }
 }
 
-// Eager form, for the ablation of Sec. 3.2.2 only: every CMult is reduced and every HAdd is a
-// modular add, as a conventional implementation would do (the outputs are identical).
+// Eager form, for the ablation of Sec. 3.2.2 only: the same tiling and scalar staging as
+// k_mac (GT = 4 groups), but every CMult is reduced (Barrett on the full product) and
+// every HAdd is a modular add, as a conventional implementation does.  Same outputs.
 template <bool PACKED, int MAXB>
 __global__ void __launch_bounds__(MAC_THREADS) k_mac_eager(const __grid_constant__ Batch<MAXB> B, KP kp) {
-    constexpr int GT = 4, NR = PACKED ? 2 : 1;
+    constexpr int GT = 4, NR = PACKED ? 2 : 1, NS = GT * NR, NSP = (NS + 3) & ~3;
+    __shared__ __align__(16) int ss[MAC_KC][NSP];
     const u32 li = find_layer(B, ST_MAC, blockIdx.x);
     const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L;
@@ -552,34 +580,47 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac_eager(const __grid_constant
     const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
     const LimbC m = kp.limb[k];
     const size_t ctw = 2ull * L * N;
-    u64 acc[GT][NR];
+    const u32 K = Ly.K, n_rot = Ly.n_rot, in_groups = Ly.in_groups, out_groups = Ly.out_groups;
+    u64 acc[NS];
 #pragma unroll
-    for (int g = 0; g < GT; g++)
+    for (int i = 0; i < NS; i++) acc[i] = 0;
+    for (u32 kc0 = 0; kc0 < K; kc0 += MAC_KC) {
+        const u32 kcn = min((u32)MAC_KC, K - kc0);
+        for (u32 idx = threadIdx.x; idx < (u32)(MAC_KC * NSP); idx += MAC_THREADS) {
+            const u32 kk = idx / NSP, c = idx % NSP, g = c / NR, r = c % NR;
+            int v = 0;
+            if (kk < kcn && c < (u32)NS && g0 + g < out_groups) v = Ly.scal[((size_t)(g0 + g) * NR + r) * K + kc0 + kk];
+            ss[kk][c] = v;
+        }
+        __syncthreads();
+        const u64* base = Ly.R + ((size_t)p * L + k) * N + x;
+#pragma unroll 2
+        for (u32 kk = 0; kk < kcn; kk++) {
+            const u32 kg = kc0 + kk;
+            const u32 ct = ru * in_groups + kg / n_rot, rot = kg % n_rot;
+            const u64 v = __ldg(base + ((size_t)ct * n_rot + rot) * ctw);
+            int sv[NSP];
 #pragma unroll
-        for (int r = 0; r < NR; r++) acc[g][r] = 0;
-    const u64* base = Ly.R + ((size_t)p * L + k) * N + x;
-    for (u32 kk = 0; kk < Ly.K; kk++) {
-        const u32 ct = ru * Ly.in_groups + kk / Ly.n_rot, rot = kk % Ly.n_rot;
-        const u64 v = __ldg(base + ((size_t)ct * Ly.n_rot + rot) * ctw);
+            for (int i = 0; i < NSP; i += 4) {
+                const int4 q4 = *reinterpret_cast<const int4*>(&ss[kk][i]);
+                sv[i] = q4.x, sv[i + 1] = q4.y, sv[i + 2] = q4.z, sv[i + 3] = q4.w;
+            }
 #pragma unroll
-        for (int g = 0; g < GT; g++) {
-            if (g0 + g >= Ly.out_groups) break;
-#pragma unroll
-            for (int r = 0; r < NR; r++) {
-                const int sv = Ly.scal[((size_t)(g0 + g) * NR + r) * Ly.K + kk];
-                const u64 prod = mulmod((u64)(sv < 0 ? -sv : sv), v, m);  // CMult, reduced
-                acc[g][r] = sv < 0 ? (acc[g][r] >= prod ? acc[g][r] - prod : acc[g][r] + m.q - prod)
-                                   : addq(acc[g][r], prod, m.q);             // HAdd, reduced
+            for (int i = 0; i < NS; i++) {
+                const u64 prod = mulmod((u64)(sv[i] < 0 ? -sv[i] : sv[i]), v, m);  // CMult, reduced
+                acc[i] = sv[i] < 0 ? (acc[i] >= prod ? acc[i] - prod : acc[i] + m.q - prod)
+                                   : addq(acc[i], prod, m.q);                     // HAdd, reduced
             }
         }
+        __syncthreads();
     }
     const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
 #pragma unroll
     for (int g = 0; g < GT; g++) {
-        if (g0 + g >= Ly.out_groups) break;
-        u64 out = acc[g][0];
-        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(acc[g][1], pkv, m), m.q);
-        Ly.O[((size_t)(ru * Ly.out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
+        if (g0 + g >= out_groups) break;
+        u64 out = acc[g * NR];
+        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(acc[g * NR + 1], pkv, m), m.q);
+        Ly.O[((size_t)(ru * out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
     }
 }
 
@@ -593,10 +634,13 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac_eager(const __grid_constant
 // kk = (input ciphertext, rotation) terms (MMA K), x_c = 10-bit chunk c of the
 // residue.  Operands are fp16 (exact integers), accumulators fp32 in TMEM:
 // |s| <= 16 and |x_c - 512| <= 512 keep every partial sum below 2^24 for
-// K <= 2048 terms, so the fp32 sums are exact integers.  The epilogue forms
-//   A = sum_c 2^(10c) (D_c + 512 S),  S = sum_kk s,
-// (each chunk's sum plus 512 S stays below 2^25), reduces it once mod q_k,
-// and applies the [k,-k] PMult as in k_mac.
+// 2048 terms, so the fp32 sums are exact integers.  Longer contractions run
+// as segments of at most 2048 terms, each accumulated afresh in TMEM.  The
+// epilogue of a segment forms
+//   A = sum_c 2^(10c) (D_c + 512 S),  S = sum of the segment's s,
+// (each chunk's sum plus 512 S stays below 2^25), reduces it once mod q_k and
+// applies the [k,-k] PMult as in k_mac; since that map is linear, segment
+// results add mod q_k into the output, which the same thread wrote before.
 // Shared-memory operands use the no-swizzle K-major canonical layout: 8x16-byte
 // core matrices, LBO = 128 B between core matrices along K, SBO = 512 B
 // between core matrices along M/N (a 32-term K tile is 4 core matrices wide).
@@ -605,7 +649,8 @@ constexpr int TC_MTILE = 128;     // NTT slots per CTA (MMA M)
 constexpr int TC_KTILE = 32;      // terms per pipeline stage
 constexpr int TC_CHUNKS = 5;      // 10-bit chunks of a residue < 2^50
 constexpr int TC_NMAX = 96;       // output rows per CTA (MMA N <= 96 so 5 N <= 512 TMEM columns)
-constexpr int TC_KMAX = 2048;     // exactness bound on terms for |s| <= 16
+constexpr int TC_KMAX = 2048;     // exactness bound on the terms of one fp32 accumulation for |s| <= 16
+constexpr u32 TC_SEG_TILES = TC_KMAX / TC_KTILE;  // K tiles per accumulation segment
 constexpr int TC_SMAX = 16;
 constexpr u32 TC_A_CHUNK_BYTES = TC_MTILE * TC_KTILE * 2;          // 8 KB
 constexpr u32 TC_A_BYTES = TC_CHUNKS * TC_A_CHUNK_BYTES;           // 40 KB
@@ -765,15 +810,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMAs (lane 0)
         if (lane == 0) {
-            u32 g = 0, n_items = 0;
+            u32 g = 0, unit = 0;  // unit = (item, segment): one accumulation in TMEM
             TcItem it;
-            for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x, n_items++) {
-                if (n_items > 0 && !wait(11, (n_items - 1) & 1)) break;  // accumulators read out
-                asm volatile("tcgen05.fence::after_thread_sync;");
+            for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
                 const u32 idesc = tc_idesc(TC_MTILE, it.nrows);
                 bool okk = true;
                 for (u32 t = 0; t < it.n_tiles; t++, g++) {
-                    const u32 st = g & 1, s = g % TC_RAW;
+                    const u32 st = g & 1, s = g % TC_RAW, tseg = t % TC_SEG_TILES;
+                    if (tseg == 0) {
+                        if (unit > 0 && !wait(11, (unit - 1) & 1)) { okk = false; break; }  // accumulators read out
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                    }
                     if (!wait(6 + st, (g >> 1) & 1)) { okk = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const u32 a_base = smem_u32(tsm + st * TC_STAGE_BYTES), b_base = smem_u32(tsm + TC_BS_OFF + s * TC_B_BYTES);
@@ -783,7 +830,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                         for (int ks = 0; ks < TC_KTILE / 16; ks++) {
                             const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
                             const u64 bd = smem_desc(b_base + ks * 256);
-                            const u32 acc = (t > 0 || ks > 0) ? 1u : 0u;
+                            const u32 acc = (tseg > 0 || ks > 0) ? 1u : 0u;
                             const u32 dt = tmem + (u32)(c * it.nrows);
                             asm volatile(
                                 "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -793,18 +840,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(8 + st)));
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(3 + s)));
+                    if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(10)));
+                        unit++;
+                    }
                 }
                 if (!okk) break;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(10)));
             }
         }
         __syncwarp();
     } else {
         // ---------------------------------------------------------------- converters (+ epilogue)
-        u32 g = 0, n_items = 0;
+        u32 g = 0, unit = 0;
         TcItem it;
         const u32 cw = warp - 2;  // converter index 0..13
-        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x, n_items++) {
+        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
             const LayerDev& Ly = *it.ly;
             const u32 K = Ly.K;
             bool okk = true;
@@ -847,12 +897,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                     arrive(6 + st);  // stage written
                     arrive(3 + s);   // raw slot read
                 }
-            }
-            if (!okk) break;
-            if (warp >= 4) {
-                // epilogue: warp w reads TMEM lanes 32 (w % 4) + lane; the three warps of a
-                // sub-partition take every third 8-column block of output rows
-                if (!__all_sync(0xffffffffu, wait(10, n_items & 1))) break;
+                if (warp < 4 || (t % TC_SEG_TILES != TC_SEG_TILES - 1 && t + 1 != it.n_tiles)) continue;
+                // epilogue of segment seg: warp w reads TMEM lanes 32 (w % 4) + lane; the three
+                // warps of a sub-partition take every third 8-column block of output rows
+                const u32 seg = t / TC_SEG_TILES;
+                if (!__all_sync(0xffffffffu, wait(10, unit & 1))) { okk = false; break; }
+                unit++;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const u32 sp = warp & 3, third = (warp - 4) >> 2;
                 const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
@@ -872,7 +922,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                     u64 red[8];
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
-                        const long long b = Ly.bias[row0 + cb + j];  // 512 S: the offset of every chunk's sum
+                        const long long b = Ly.bias[(size_t)seg * Ly.tc_rows + row0 + cb + j];  // 512 S of the segment
                         const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
                                              (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
                                              (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
@@ -888,13 +938,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                         if (gg >= Ly.out_groups) continue;
                         u64 out = red[j];
                         if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
-                        Ly.O[((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x] = out;
+                        u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
+                        if (seg > 0) out = addq(out, *o, m.q);  // this thread stored the earlier segments
+                        *o = out;
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
                 if (lane == 0) arrive(11);  // accumulators free
             }
+            if (!okk) break;
         }
     }
     // drain: every copy that was issued is waited for by the converters in the normal path; after an
@@ -1382,12 +1435,12 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
         }
         double est = estimate_noise_log2(p, p->w, worst0, worst1, worst_abs, P->packed);
         if (est >= p->log2_delta - 1.0) fail(HE_ENOISE, "estimated noise exceeds Delta/2 for this layer");
-        // tensor-core contraction: exact while |s| <= 16 and K <= 2048 (fp32 sums below 2^24)
+        // tensor-core contraction: exact while |s| <= 16 (fp32 sums of 2048-term segments below 2^24)
         int max_abs_s = 0;
         for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
         const u32 impl = tune ? tune->mac_impl : 0;
-        const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && P->K <= (u32)TC_KMAX;
-        if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, K <= 2048 and a non-depthwise layer");
+        const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX;
+        if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16 and a non-depthwise layer");
         if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
         if (impl > 3) fail(HE_EINVAL, "mac_impl must be 0..3");
         P->eager = impl == 3;
@@ -1429,20 +1482,20 @@ extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_c
             const u32 rpc = P->tc_rows_per_cta, ktiles = P->tc_kpad / TC_KTILE;
             const u32 mtiles = (P->tc_rows + rpc - 1) / rpc;
             std::vector<__half> h16((size_t)mtiles * ktiles * rpc * TC_KTILE, __float2half(0.0f));
-            std::vector<int> bias(P->tc_rows, 0);
+            // bias [segment][row] = 512 x the sum of the row's scalars over the segment's terms
+            const u32 n_seg = (ktiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
+            std::vector<int> bias((size_t)n_seg * P->tc_rows, 0);
             for (u32 g = 0; g < lay.out_groups; g++)
                 for (u32 r = 0; r < NR; r++) {
                     const u32 row = g * NR + r, mt = row / rpc, rl = row % rpc;
-                    long long S = 0;
                     for (u32 kk = 0; kk < P->K; kk++) {
                         int v = sc[((size_t)g * NR + r) * P->K + kk];
                         const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
                         const size_t byte = ((size_t)mt * ktiles + kt) * rpc * TC_KTILE * 2 +
                                             (rl >> 3) * TC_SBO + (kl >> 3) * 128 + (rl & 7) * 16 + (kl & 7) * 2;
                         h16[byte / 2] = __float2half((float)v);
-                        S += v;
+                        bias[(size_t)(kt / TC_SEG_TILES) * P->tc_rows + row] += 512 * v;
                     }
-                    bias[g * NR + r] = (int)(512 * S);
                 }
             CUDA_OK(cudaMalloc(&P->d_sc16, h16.size() * sizeof(__half)));
             CUDA_OK(cudaMemcpy(P->d_sc16, h16.data(), h16.size() * sizeof(__half), cudaMemcpyHostToDevice));

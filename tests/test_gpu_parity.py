@@ -255,11 +255,14 @@ def test_tensor_core_mac_is_chosen_when_exact(small):
         H.he_conv_plan(small.p, gk, d, np.full((4, 4, 3, 3), 9), mac_impl=2)
 
 
-def test_tensor_core_mac_at_the_exactness_bound():
-    """K = 2048 terms, every scalar 16 and every chunk at -512: the fp32 sums reach 2^24 exactly.
-    A zero ciphertext makes every rotated residue 0 (all chunks 0 -> -512 after the offset)."""
+@pytest.mark.parametrize("pairs", [2048 // 18, 228])
+def test_tensor_core_mac_at_the_exactness_bound(pairs):
+    """Every scalar 16 and every chunk at -512 drive each fp32 sum to its largest magnitude.
+    A zero ciphertext makes every rotated residue 0 (all chunks 0 -> -512 after the offset).
+    113 pairs: K = 2034 terms in one accumulation.  228 pairs: K = 4104 terms, three segments
+    (2048 + 2048 + 8) whose results add mod q in the output."""
     S = Setup(1024, 2, 25)
-    C_in = 2 * (2048 // 18)  # 113 pairs -> K = 2034 <= 2048
+    C_in = 2 * pairs
     spec = dict(C_in=C_in, C_out=4, H=2, W=2, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
     d = H.conv_desc(**spec)
     gk = H.he_galois_keys(S.p, S.sk, H.he_layer_galois(S.p, d), synth.SEED_KEYS)

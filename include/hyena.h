@@ -121,6 +121,11 @@ typedef struct {
     uint32_t depthwise;      /* 0 or 1 */
     uint32_t n_images;       /* images packed into the same ciphertexts (same client key) */
     uint32_t c_n;            /* channels per ciphertext: 2 (Hyena packing) or 1 (padded conv) */
+    uint32_t tile_h, tile_w; /* interior tile size, or both 0 for the default: the whole image if its
+                                padded block fits half a ring, else full-width strips, else square
+                                tiles, each as large as fits.  Given tiles must fit the image, be
+                                multiples of the stride unless they span the image, and their padded
+                                block (tile_h + kh - 1)(tile_w + kh - 1) must fit N/2 slots. */
 } he_conv_desc;
 
 typedef struct {

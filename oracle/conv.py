@@ -64,6 +64,8 @@ class Layout:
     depthwise: bool
     n_images: int
     c_n: int
+    tile_h: int = 0
+    tile_w: int = 0
     P: int = 0
     T_h: int = 0
     T_w: int = 0
@@ -74,7 +76,19 @@ class Layout:
         if self.depthwise and self.C_in != self.C_out:
             raise ValueError("depthwise needs C_in == C_out")
         self.P = (self.kh - 1) // 2
-        self.T_h, self.T_w = choose_tile(self.N // 2, self.H, self.W, self.P, self.stride)
+        if self.tile_h or self.tile_w:
+            # a caller-chosen tile: any size whose padded block fits one slot row, with tile
+            # origins on the stride grid (sides a multiple of S unless one tile spans the image)
+            th, tw, S = self.tile_h, self.tile_w, self.stride
+            if not (0 < th <= self.H and 0 < tw <= self.W):
+                raise ValueError("tile must lie within the image, in both directions")
+            if (th % S and th != self.H) or (tw % S and tw != self.W):
+                raise ValueError("tile sides must be multiples of the stride")
+            if (th + 2 * self.P) * (tw + 2 * self.P) > self.N // 2:
+                raise ValueError("padded tile does not fit one slot row")
+            self.T_h, self.T_w = th, tw
+        else:
+            self.T_h, self.T_w = choose_tile(self.N // 2, self.H, self.W, self.P, self.stride)
 
     # geometry -------------------------------------------------------------
     @property

@@ -732,7 +732,15 @@ void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* o) {
     std::memset(o, 0, sizeof(*o));
     const u32 half = p->N / 2, P = (d->kh - 1) / 2;
     o->P = P;
-    choose_tile(half, d->H, d->W, P, d->stride, &o->T_h, &o->T_w);
+    if (d->tile_h || d->tile_w) {
+        const u32 S = d->stride, th = d->tile_h, tw = d->tile_w;
+        if (!th || !tw || th > d->H || tw > d->W) fail(HE_EINVAL, "tile must be given in both directions, within the image");
+        if ((th % S && th != d->H) || (tw % S && tw != d->W)) fail(HE_EINVAL, "tile sides must be multiples of the stride");
+        if ((u64)(th + 2 * P) * (tw + 2 * P) > half) fail(HE_EINVAL, "padded tile does not fit N/2 slots");
+        o->T_h = th, o->T_w = tw;
+    } else {
+        choose_tile(half, d->H, d->W, P, d->stride, &o->T_h, &o->T_w);
+    }
     o->W_b = o->T_w + 2 * P;
     o->block_slots = (o->T_h + 2 * P) * o->W_b;
     o->blocks_per_row = half / o->block_slots;

@@ -159,6 +159,9 @@ SMALL = [
     dict(C_in=2, C_out=2, H=6, W=6, kh=5, stride=1, depthwise=False, n_images=1, c_n=2),
     dict(C_in=1, C_out=1, H=1, W=1, kh=3, stride=1, depthwise=False, n_images=1, c_n=2),
     dict(C_in=20, C_out=18, H=5, W=5, kh=3, stride=1, depthwise=False, n_images=5, c_n=2),
+    # caller-chosen tiles (ragged last tiles; stride-2 strips)
+    dict(C_in=3, C_out=4, H=10, W=9, kh=3, stride=1, depthwise=False, n_images=2, c_n=2, tile_h=4, tile_w=5),
+    dict(C_in=4, C_out=6, H=12, W=13, kh=3, stride=2, depthwise=False, n_images=2, c_n=1, tile_h=6, tile_w=13),
 ]
 
 

@@ -111,6 +111,10 @@ LAYERS = [
     dict(C_in=2, C_out=2, H=12, W=200, kh=3, stride=2, depthwise=False, n_images=1, c_n=2),
     dict(C_in=6, C_out=4, H=5, W=5, kh=1, stride=1, depthwise=False, n_images=2, c_n=2),
     dict(C_in=2, C_out=2, H=6, W=6, kh=5, stride=1, depthwise=False, n_images=1, c_n=2),
+    # caller-chosen tiles: ragged last tiles, strips, stride-aligned squares, a tile spanning an odd side
+    dict(C_in=3, C_out=4, H=10, W=9, kh=3, stride=1, depthwise=False, n_images=2, c_n=2, tile_h=4, tile_w=5),
+    dict(C_in=2, C_out=2, H=30, W=40, kh=3, stride=1, depthwise=False, n_images=1, c_n=1, tile_h=7, tile_w=40),
+    dict(C_in=4, C_out=4, H=12, W=13, kh=3, stride=2, depthwise=True, n_images=2, c_n=2, tile_h=6, tile_w=13),
 ]
 
 
@@ -120,8 +124,7 @@ def test_layout_and_image_encryption_match_oracle(spec):
     p = H.he_params_create(N, L, decomp_bits=w)
     info = H.he_params_info(p)
     P = prm.make_params(N=N, L=L, w=w)
-    d = H.conv_desc(**{k: spec[k] for k in ("C_in", "C_out", "H", "W", "kh", "stride", "depthwise", "n_images",
-                                            "c_n")})
+    d = H.conv_desc(**spec)
     lay = H.he_layout_for_layer(p, d)
     ol = conv.Layout(N=N, **spec)
     assert (lay.T_h, lay.T_w, lay.blocks_per_row, lay.n_ct_in, lay.n_ct_out, lay.Ho, lay.Wo) == \
@@ -134,6 +137,21 @@ def test_layout_and_image_encryption_match_oracle(spec):
     ct = H.he_encrypt_image(p, sk, d, act, 2, info)
     assert (ct == conv.encrypt_image(P, ol, s, act, 2)).all()
     # decrypting the (unrotated) input through the output path reads the input back
-    if spec["kh"] == 3 and spec["stride"] == 1 and spec["C_in"] == spec["C_out"]:
+    if spec["kh"] == 3 and spec["stride"] == 1 and spec["C_in"] == spec["C_out"] and not spec.get("tile_h"):
         back = H.he_decrypt_image(p, sk, d, ct, unscale=False)
         assert (back == act).all()
+
+
+@pytest.mark.parametrize("tile,why", [((4, 0), "one side only"), ((11, 4), "taller than the image"),
+                                      ((3, 4), "not a multiple of the stride"), ((10, 60), "block beyond N/2")])
+def test_tile_override_rejected_like_the_oracle(tile, why):
+    N = 1024
+    p = H.he_params_create(N, 2, decomp_bits=25)
+    spec = dict(C_in=2, C_out=2, H=10, W=60, kh=3, stride=2, depthwise=False, n_images=1, c_n=2,
+                tile_h=tile[0], tile_w=tile[1])
+    with pytest.raises(H.HyenaError) as e:
+        H.he_layout_for_layer(p, H.conv_desc(**spec))
+    assert e.value.code == H.HE_EINVAL, why
+    with pytest.raises(ValueError):
+        conv.Layout(N=N, **spec)
+    H.he_params_destroy(p)

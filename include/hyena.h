@@ -172,7 +172,8 @@ typedef struct {
     uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block (0 -> default) */
     uint32_t mac_impl;       /* 0 auto, 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL if not exact),
                                 3 CUDA-core eager MAC (reduced after every term; for ablations) */
-    uint32_t reserved[6];
+    uint32_t tc_rows;        /* tensor-core MAC: output rows per CTA, a multiple of 16 up to 96 (0 -> 96) */
+    uint32_t reserved[5];
 } he_tune;
 
 /* Uploads the layer's Galois keys (NTT form), the Hadamard scalars
@@ -204,6 +205,16 @@ int he_conv_status(const he_plan* plan);
  * accumulation) is chosen automatically when it is exact: no depthwise and
  * |s| <= 16. */
 int he_conv_info(const he_plan* plan, int* mac_impl);
+/* Device time of one forward of this layer configuration, for tuning and for
+ * training the cost model: builds a plan whose key-switching keys and input
+ * ciphertexts are uniform residues made on the device (the kernels do the same
+ * work on any residues), runs one warm-up and `reps` (1..1000) timed forwards
+ * on `stream`, and frees everything.  stage_ms[4] (may be NULL): median times
+ * of the input NTTs, key switch, MAC and output NTTs; *total_ms: median of the
+ * whole forward.  Errors: as he_conv_plan (HE_ENOISE if the weights would
+ * exceed the noise budget), HE_ENOMEM if the buffers do not fit the device. */
+int he_conv_time(const he_params* p, const he_conv_desc* d, const int32_t* weights, const he_tune* tune, int reps,
+                 void* stream, float* stage_ms, float* total_ms);
 void he_plan_destroy(he_plan* plan);
 
 /* Size of the static device scratch used by he_conv_forward_noalloc (32 MiB). */

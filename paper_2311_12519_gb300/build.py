@@ -1,7 +1,8 @@
 """Builds the library libhyena.so in-tree for sm_103a.
 
-Two translation units compiled in parallel (host.cpp with the host C++
-compiler, device.cu with nvcc), linked by nvcc with the static CUDA runtime.
+Three translation units compiled in parallel (host.cpp with the host C++
+compiler; device.cu, the encrypted-convolution kernels, and mlp.cu, the cost
+model's network, with nvcc), linked by nvcc with the static CUDA runtime.
 """
 from __future__ import annotations
 
@@ -24,8 +25,8 @@ def _nvcc() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("host.cpp", "device.cu", "internal.h")] + [
-        os.path.join(os.path.dirname(HERE), "include", "hyena.h")]
+    return [os.path.join(CSRC, f) for f in ("host.cpp", "device.cu", "mlp.cu", "internal.h")] + [
+        os.path.join(os.path.dirname(HERE), "include", h) for h in ("hyena.h", "hyena_costmodel.h")]
 
 
 def up_to_date() -> bool:
@@ -43,10 +44,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     inc = ["-I", os.path.join(os.path.dirname(HERE), "include")]
     host_o = os.path.join(OUT_DIR, "host.o")
     dev_o = os.path.join(OUT_DIR, "device.o")
+    mlp_o = os.path.join(OUT_DIR, "mlp.o")
     cmds = [
         ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-c", os.path.join(CSRC, "host.cpp"), "-o", host_o] + inc,
         [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v" if verbose else "-O3",
          "-c", os.path.join(CSRC, "device.cu"), "-o", dev_o] + inc,
+        [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v" if verbose else "-O3",
+         "-c", os.path.join(CSRC, "mlp.cu"), "-o", mlp_o] + inc,
     ]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     for c, pr in zip(cmds, procs):
@@ -56,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if pr.returncode != 0:
             raise RuntimeError(f"build failed: {' '.join(c)}\n{out}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, host_o, dev_o], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, host_o, dev_o, mlp_o], check=True)
     os.replace(tmp, LIB)
     return LIB
 

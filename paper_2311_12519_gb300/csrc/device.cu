@@ -51,6 +51,10 @@ struct RotDev {
 #define CUDA_OK(x)                                                                         \
     do {                                                                                   \
         cudaError_t e_ = (x);                                                              \
+        if (e_ == cudaErrorMemoryAllocation) {                                              \
+            cudaGetLastError();                                                            \
+            fail(HE_ENOMEM, std::string(#x ": ") + cudaGetErrorString(e_));                \
+        }                                                                                  \
         if (e_ != cudaSuccess) fail(HE_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
@@ -1088,6 +1092,24 @@ u64* upload_keys(const he_params* p, const KP& kp, const std::vector<const std::
     return d;
 }
 
+// Residues for timing runs: word i of polynomial j (limb j % L) = SplitMix64(seed + i + j N) mod q.
+__global__ void k_fill_uniform(u64* __restrict__ a, size_t n_polys, KP kp, u64 seed) {
+    const size_t total = n_polys * kp.N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        u64 z = seed + i * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        a[i] = z % kp.limb[(i / kp.N) % kp.L].q;
+    }
+}
+
+void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s) {
+    if (!n_polys) return;
+    k_fill_uniform<<<(u32)std::min<size_t>(4096, (n_polys * kp.N + 255) / 256), 256, 0, s>>>(d, n_polys, kp, seed);
+    check_launch("k_fill_uniform");
+}
+
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
     bool tc = false, packed = false, dw = false, eager = false;
@@ -1228,7 +1250,12 @@ void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector
 
 // Runs the four stages over a list of layers.  Layers of one MAC variant share a launch.
 void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>& layers, cudaStream_t s, bool timed,
-                bool do_mac = true) {
+                bool do_mac = true, const cudaEvent_t* marks = nullptr) {
+    // marks (optional): five events recorded at the stage boundaries
+    auto mark = [&](int i) {
+        if (marks) CUDA_OK(cudaEventRecord(marks[i], s));
+    };
+    mark(0);
     std::vector<const StageLayer*> all;
     for (auto& l : layers) all.push_back(&l);
     const bool single = layers.size() == 1;
@@ -1240,10 +1267,12 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
         StageTimer t(HE_STAGE_NTT_IN, s, timed);
         go(ST_NTT, all);
     }
+    mark(1);
     {
         StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
         go(ST_KS, all);
     }
+    mark(2);
     if (do_mac) {
         StageTimer t(HE_STAGE_MAC, s, timed);
         std::vector<bool> done(layers.size(), false);
@@ -1255,10 +1284,12 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
             go(ST_MAC, grp);
         }
     }
+    mark(3);
     {
         StageTimer t(HE_STAGE_NTT_OUT, s, timed);
         go(ST_INTT, all);
     }
+    mark(4);
 }
 
 }  // namespace
@@ -1361,163 +1392,180 @@ struct he_plan {
     }
 };
 
+// Builds a plan.  gk == nullptr: timing plan, whose key-switching keys are
+// uniform residues made on the device (same sizes and kernels, no secret).
+static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys* gk, const he_conv_desc* d,
+                                           const int32_t* weights, const he_tune* tune) {
+    auto P = std::make_unique<he_plan>();
+    P->p = p;
+    P->d = *d;
+    compute_layout(p, d, &P->lay);
+    const he_layout& lay = P->lay;
+    P->packed = d->c_n == 2;
+    P->dw = d->depthwise != 0;
+    std::vector<RotEntry> rl = rotation_list(p, d, lay);
+    P->n_rot = (u32)rl.size();
+    const u32 taps = d->kh * d->kh;
+    // rotations that need a key switch, grouped by distinct Galois element
+    std::vector<u32> gal;
+    std::vector<RotDev> rots;
+    bool have_id = false;
+    for (u32 r = 0; r < rl.size(); r++) {
+        if (rl[r].galois == 1) {
+            P->rot_id = r;
+            have_id = true;
+            continue;
+        }
+        auto it = std::find(gal.begin(), gal.end(), rl[r].galois);
+        u32 key = (u32)(it - gal.begin());
+        if (it == gal.end()) gal.push_back(rl[r].galois);
+        rots.push_back({rl[r].galois, r, key, 0});
+    }
+    if (!have_id) fail(HE_EINVAL, "internal: identity rotation missing");
+    std::vector<const std::vector<u64>*> keys;
+    for (u32 g : gal) {
+        if (!gk) break;
+        const std::vector<u64>* k = gk->find(g);
+        if (!k) fail(HE_EMISSINGKEY, "missing Galois key " + std::to_string(g));
+        keys.push_back(k);
+    }
+    if (p->L * p->l > 16) fail(HE_EINVAL, "L * l must be at most 16");
+    // Hadamard scalars s0 = v0 + v1, s1 = v0 - v1 (Eq. 1 without the 1/2)
+    const u32 NR = P->packed ? 2 : 1;
+    P->K = P->dw ? P->n_rot : lay.in_groups * P->n_rot;
+    if (P->K > (1u << 14)) fail(HE_EINVAL, "too many accumulation terms (C_in kh^2 > 16384)");
+    std::vector<int16_t> sc((size_t)lay.out_groups * NR * P->K, 0);
+    const u32 wcin = P->dw ? 1 : d->C_in;
+    auto W = [&](u32 o, u32 i, u32 tap) -> i64 {
+        if (o >= d->C_out || i >= d->C_in) return 0;
+        if (P->dw) return o == i ? weights[(size_t)o * taps + tap] : 0;
+        return weights[((size_t)o * wcin + i) * taps + tap];
+    };
+    double worst0 = 0, worst1 = 0, worst_abs = 0;
+    for (u32 g = 0; g < lay.out_groups; g++) {
+        double s0q = 0, s1q = 0, sab = 0;
+        for (u32 kk = 0; kk < P->K; kk++) {
+            u32 j = P->dw ? g : kk / P->n_rot, r = kk % P->n_rot;
+            u32 tap = rl[r].tap, dg = rl[r].d;
+            i64 s0, s1 = 0;
+            if (P->packed) {
+                i64 v0 = dg == 0 ? W(2 * g, 2 * j, tap) : W(2 * g, 2 * j + 1, tap);
+                i64 v1 = dg == 0 ? W(2 * g + 1, 2 * j + 1, tap) : W(2 * g + 1, 2 * j, tap);
+                s0 = v0 + v1, s1 = v0 - v1;
+            } else {
+                s0 = W(g, j, tap);
+            }
+            if (s0 < -32768 || s0 > 32767 || s1 < -32768 || s1 > 32767)
+                fail(HE_EINVAL, "weights must satisfy |w| <= 16383");
+            sc[((size_t)g * NR + 0) * P->K + kk] = (int16_t)s0;
+            if (P->packed) sc[((size_t)g * NR + 1) * P->K + kk] = (int16_t)s1;
+            s0q += (double)s0 * s0, s1q += (double)s1 * s1, sab += std::fabs((double)s0) + std::fabs((double)s1);
+        }
+        worst0 = std::max(worst0, s0q), worst1 = std::max(worst1, s1q), worst_abs = std::max(worst_abs, sab);
+    }
+    double est = estimate_noise_log2(p, p->w, worst0, worst1, worst_abs, P->packed);
+    if (est >= p->log2_delta - 1.0) fail(HE_ENOISE, "estimated noise exceeds Delta/2 for this layer");
+    // tensor-core contraction: exact while |s| <= 16 (fp32 sums of 2048-term segments below 2^24)
+    int max_abs_s = 0;
+    for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
+    const u32 impl = tune ? tune->mac_impl : 0;
+    const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX;
+    if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16 and a non-depthwise layer");
+    if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
+    if (impl > 3) fail(HE_EINVAL, "mac_impl must be 0..3");
+    P->eager = impl == 3;
+    P->use_tc = tc_ok && impl != 1 && impl != 3;
+    if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
+    const u32 tc_rows_req = tune ? tune->tc_rows : 0;
+    if (tc_rows_req && (tc_rows_req % 16 || tc_rows_req > (u32)TC_NMAX))
+        fail(HE_EINVAL, "tc_rows must be a multiple of 16, at most 96");
+    // device data
+    CUDA_OK(cudaGetDevice(&P->device));
+    P->kp = make_kp(p);
+    cudaStream_t s = 0;
+    if (gk) {
+        P->d_ksk = upload_keys(p, P->kp, keys, s);
+    } else if (!gal.empty()) {
+        const size_t per = (size_t)p->L * p->l * 2 * p->L * p->N;
+        CUDA_OK(cudaMalloc(&P->d_ksk, per * gal.size() * 8));
+        fill_uniform(P->kp, P->d_ksk, per * gal.size() / p->N, 0x5eed, s);
+    }
+    P->n_ks = (u32)rots.size();
+    if (!rots.empty()) {
+        CUDA_OK(cudaMalloc(&P->d_rots, rots.size() * sizeof(RotDev)));
+        CUDA_OK(cudaMemcpy(P->d_rots, rots.data(), rots.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
+    }
+    CUDA_OK(cudaMalloc(&P->d_scal, sc.size() * sizeof(int16_t)));
+    CUDA_OK(cudaMemcpy(P->d_scal, sc.data(), sc.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+    // NTT(P_k): P_k = kh (X^(N/4) + X^(3N/4)) lifted into every limb
+    if (P->packed) {
+        std::vector<u64> pk((size_t)p->L * p->N, 0);
+        for (u32 k = 0; k < p->L; k++) {
+            u64 v = p->mod[k].from_signed(p->kh);
+            pk[(size_t)k * p->N + p->N / 4] = v;
+            pk[(size_t)k * p->N + 3 * p->N / 4] = v;
+            p->ntt[k].forward(pk.data() + (size_t)k * p->N);
+        }
+        CUDA_OK(cudaMalloc(&P->d_pk, pk.size() * 8));
+        CUDA_OK(cudaMemcpy(P->d_pk, pk.data(), pk.size() * 8, cudaMemcpyHostToDevice));
+    }
+    CUDA_OK(cudaMalloc(&P->d_err, sizeof(int)));
+    CUDA_OK(cudaMemset(P->d_err, 0, sizeof(int)));
+    if (P->use_tc) {
+        const u32 rows = lay.out_groups * NR;
+        P->tc_rows = (rows + 15) / 16 * 16;
+        P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
+        P->tc_kpad = (P->K + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
+        // scalar tiles stored as the exact shared-memory image the MMA reads (K-major, no
+        // swizzle), one block of rows_per_cta x 32 terms per (row tile, K tile)
+        const u32 rpc = P->tc_rows_per_cta, ktiles = P->tc_kpad / TC_KTILE;
+        const u32 mtiles = (P->tc_rows + rpc - 1) / rpc;
+        std::vector<__half> h16((size_t)mtiles * ktiles * rpc * TC_KTILE, __float2half(0.0f));
+        // bias [segment][row] = 512 x the sum of the row's scalars over the segment's terms
+        const u32 n_seg = (ktiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
+        std::vector<int> bias((size_t)n_seg * P->tc_rows, 0);
+        for (u32 g = 0; g < lay.out_groups; g++)
+            for (u32 r = 0; r < NR; r++) {
+                const u32 row = g * NR + r, mt = row / rpc, rl = row % rpc;
+                for (u32 kk = 0; kk < P->K; kk++) {
+                    int v = sc[((size_t)g * NR + r) * P->K + kk];
+                    const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
+                    const size_t byte = ((size_t)mt * ktiles + kt) * rpc * TC_KTILE * 2 +
+                                        (rl >> 3) * TC_SBO + (kl >> 3) * 128 + (rl & 7) * 16 + (kl & 7) * 2;
+                    h16[byte / 2] = __float2half((float)v);
+                    bias[(size_t)(kt / TC_SEG_TILES) * P->tc_rows + row] += 512 * v;
+                }
+            }
+        CUDA_OK(cudaMalloc(&P->d_sc16, h16.size() * sizeof(__half)));
+        CUDA_OK(cudaMemcpy(P->d_sc16, h16.data(), h16.size() * sizeof(__half), cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMalloc(&P->d_bias, bias.size() * sizeof(int)));
+        CUDA_OK(cudaMemcpy(P->d_bias, bias.data(), bias.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    if (P->use_tc) {
+        u32 cols = 32;
+        while (cols < (u32)TC_CHUNKS * P->tc_rows_per_cta) cols <<= 1;
+        P->tmem_cols = cols;
+    }
+    CUDA_OK(cudaStreamSynchronize(s));
+    // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
+    P->r_slots = P->n_rot;
+    P->r_id = P->rot_id;
+    const size_t ctw = 2ull * p->L * p->N;
+    P->off_R = 0;
+    P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);
+    P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
+    P->ws_bytes = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
+    (void)taps;
+    return P;
+}
+
 extern "C" int he_conv_plan(const he_params* p, const he_galkeys* gk, const he_conv_desc* d, const int32_t* weights,
                             const he_tune* tune, he_plan** out) {
     return guard([&] {
         if (!p || !gk || !d || !weights || !out) fail(HE_EINVAL, "null argument");
         if (gk->p != p) fail(HE_EINVAL, "Galois keys belong to other parameters");
         *out = nullptr;
-        auto P = std::make_unique<he_plan>();
-        P->p = p;
-        P->d = *d;
-        compute_layout(p, d, &P->lay);
-        const he_layout& lay = P->lay;
-        P->packed = d->c_n == 2;
-        P->dw = d->depthwise != 0;
-        std::vector<RotEntry> rl = rotation_list(p, d, lay);
-        P->n_rot = (u32)rl.size();
-        const u32 taps = d->kh * d->kh;
-        // rotations that need a key switch, grouped by distinct Galois element
-        std::vector<u32> gal;
-        std::vector<RotDev> rots;
-        bool have_id = false;
-        for (u32 r = 0; r < rl.size(); r++) {
-            if (rl[r].galois == 1) {
-                P->rot_id = r;
-                have_id = true;
-                continue;
-            }
-            auto it = std::find(gal.begin(), gal.end(), rl[r].galois);
-            u32 key = (u32)(it - gal.begin());
-            if (it == gal.end()) gal.push_back(rl[r].galois);
-            rots.push_back({rl[r].galois, r, key, 0});
-        }
-        if (!have_id) fail(HE_EINVAL, "internal: identity rotation missing");
-        std::vector<const std::vector<u64>*> keys;
-        for (u32 g : gal) {
-            const std::vector<u64>* k = gk->find(g);
-            if (!k) fail(HE_EMISSINGKEY, "missing Galois key " + std::to_string(g));
-            keys.push_back(k);
-        }
-        if (p->L * p->l > 16) fail(HE_EINVAL, "L * l must be at most 16");
-        // Hadamard scalars s0 = v0 + v1, s1 = v0 - v1 (Eq. 1 without the 1/2)
-        const u32 NR = P->packed ? 2 : 1;
-        P->K = P->dw ? P->n_rot : lay.in_groups * P->n_rot;
-        if (P->K > (1u << 14)) fail(HE_EINVAL, "too many accumulation terms (C_in kh^2 > 16384)");
-        std::vector<int16_t> sc((size_t)lay.out_groups * NR * P->K, 0);
-        const u32 wcin = P->dw ? 1 : d->C_in;
-        auto W = [&](u32 o, u32 i, u32 tap) -> i64 {
-            if (o >= d->C_out || i >= d->C_in) return 0;
-            if (P->dw) return o == i ? weights[(size_t)o * taps + tap] : 0;
-            return weights[((size_t)o * wcin + i) * taps + tap];
-        };
-        double worst0 = 0, worst1 = 0, worst_abs = 0;
-        for (u32 g = 0; g < lay.out_groups; g++) {
-            double s0q = 0, s1q = 0, sab = 0;
-            for (u32 kk = 0; kk < P->K; kk++) {
-                u32 j = P->dw ? g : kk / P->n_rot, r = kk % P->n_rot;
-                u32 tap = rl[r].tap, dg = rl[r].d;
-                i64 s0, s1 = 0;
-                if (P->packed) {
-                    i64 v0 = dg == 0 ? W(2 * g, 2 * j, tap) : W(2 * g, 2 * j + 1, tap);
-                    i64 v1 = dg == 0 ? W(2 * g + 1, 2 * j + 1, tap) : W(2 * g + 1, 2 * j, tap);
-                    s0 = v0 + v1, s1 = v0 - v1;
-                } else {
-                    s0 = W(g, j, tap);
-                }
-                if (s0 < -32768 || s0 > 32767 || s1 < -32768 || s1 > 32767)
-                    fail(HE_EINVAL, "weights must satisfy |w| <= 16383");
-                sc[((size_t)g * NR + 0) * P->K + kk] = (int16_t)s0;
-                if (P->packed) sc[((size_t)g * NR + 1) * P->K + kk] = (int16_t)s1;
-                s0q += (double)s0 * s0, s1q += (double)s1 * s1, sab += std::fabs((double)s0) + std::fabs((double)s1);
-            }
-            worst0 = std::max(worst0, s0q), worst1 = std::max(worst1, s1q), worst_abs = std::max(worst_abs, sab);
-        }
-        double est = estimate_noise_log2(p, p->w, worst0, worst1, worst_abs, P->packed);
-        if (est >= p->log2_delta - 1.0) fail(HE_ENOISE, "estimated noise exceeds Delta/2 for this layer");
-        // tensor-core contraction: exact while |s| <= 16 (fp32 sums of 2048-term segments below 2^24)
-        int max_abs_s = 0;
-        for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
-        const u32 impl = tune ? tune->mac_impl : 0;
-        const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX;
-        if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16 and a non-depthwise layer");
-        if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
-        if (impl > 3) fail(HE_EINVAL, "mac_impl must be 0..3");
-        P->eager = impl == 3;
-        P->use_tc = tc_ok && impl != 1 && impl != 3;
-        if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
-        // device data
-        CUDA_OK(cudaGetDevice(&P->device));
-        P->kp = make_kp(p);
-        cudaStream_t s = 0;
-        P->d_ksk = upload_keys(p, P->kp, keys, s);
-        P->n_ks = (u32)rots.size();
-        if (!rots.empty()) {
-            CUDA_OK(cudaMalloc(&P->d_rots, rots.size() * sizeof(RotDev)));
-            CUDA_OK(cudaMemcpy(P->d_rots, rots.data(), rots.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
-        }
-        CUDA_OK(cudaMalloc(&P->d_scal, sc.size() * sizeof(int16_t)));
-        CUDA_OK(cudaMemcpy(P->d_scal, sc.data(), sc.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-        // NTT(P_k): P_k = kh (X^(N/4) + X^(3N/4)) lifted into every limb
-        if (P->packed) {
-            std::vector<u64> pk((size_t)p->L * p->N, 0);
-            for (u32 k = 0; k < p->L; k++) {
-                u64 v = p->mod[k].from_signed(p->kh);
-                pk[(size_t)k * p->N + p->N / 4] = v;
-                pk[(size_t)k * p->N + 3 * p->N / 4] = v;
-                p->ntt[k].forward(pk.data() + (size_t)k * p->N);
-            }
-            CUDA_OK(cudaMalloc(&P->d_pk, pk.size() * 8));
-            CUDA_OK(cudaMemcpy(P->d_pk, pk.data(), pk.size() * 8, cudaMemcpyHostToDevice));
-        }
-        CUDA_OK(cudaMalloc(&P->d_err, sizeof(int)));
-        CUDA_OK(cudaMemset(P->d_err, 0, sizeof(int)));
-        if (P->use_tc) {
-            const u32 rows = lay.out_groups * NR;
-            P->tc_rows = (rows + 15) / 16 * 16;
-            P->tc_rows_per_cta = std::min<u32>(TC_NMAX, P->tc_rows);
-            P->tc_kpad = (P->K + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
-            // scalar tiles stored as the exact shared-memory image the MMA reads (K-major, no
-            // swizzle), one block of rows_per_cta x 32 terms per (row tile, K tile)
-            const u32 rpc = P->tc_rows_per_cta, ktiles = P->tc_kpad / TC_KTILE;
-            const u32 mtiles = (P->tc_rows + rpc - 1) / rpc;
-            std::vector<__half> h16((size_t)mtiles * ktiles * rpc * TC_KTILE, __float2half(0.0f));
-            // bias [segment][row] = 512 x the sum of the row's scalars over the segment's terms
-            const u32 n_seg = (ktiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
-            std::vector<int> bias((size_t)n_seg * P->tc_rows, 0);
-            for (u32 g = 0; g < lay.out_groups; g++)
-                for (u32 r = 0; r < NR; r++) {
-                    const u32 row = g * NR + r, mt = row / rpc, rl = row % rpc;
-                    for (u32 kk = 0; kk < P->K; kk++) {
-                        int v = sc[((size_t)g * NR + r) * P->K + kk];
-                        const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
-                        const size_t byte = ((size_t)mt * ktiles + kt) * rpc * TC_KTILE * 2 +
-                                            (rl >> 3) * TC_SBO + (kl >> 3) * 128 + (rl & 7) * 16 + (kl & 7) * 2;
-                        h16[byte / 2] = __float2half((float)v);
-                        bias[(size_t)(kt / TC_SEG_TILES) * P->tc_rows + row] += 512 * v;
-                    }
-                }
-            CUDA_OK(cudaMalloc(&P->d_sc16, h16.size() * sizeof(__half)));
-            CUDA_OK(cudaMemcpy(P->d_sc16, h16.data(), h16.size() * sizeof(__half), cudaMemcpyHostToDevice));
-            CUDA_OK(cudaMalloc(&P->d_bias, bias.size() * sizeof(int)));
-            CUDA_OK(cudaMemcpy(P->d_bias, bias.data(), bias.size() * sizeof(int), cudaMemcpyHostToDevice));
-        }
-        if (P->use_tc) {
-            u32 cols = 32;
-            while (cols < (u32)TC_CHUNKS * P->tc_rows_per_cta) cols <<= 1;
-            P->tmem_cols = cols;
-        }
-        CUDA_OK(cudaStreamSynchronize(s));
-        // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
-        P->r_slots = P->n_rot;
-        P->r_id = P->rot_id;
-        const size_t ctw = 2ull * p->L * p->N;
-        P->off_R = 0;
-        P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);
-        P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
-        P->ws_bytes = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
-        (void)taps;
-        *out = P.release();
+        *out = build_plan(p, gk, d, weights, tune).release();
     });
 }
 
@@ -1573,6 +1621,52 @@ extern "C" int he_conv_status(const he_plan* plan) {
         int v = 0;
         CUDA_OK(cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (v) fail(HE_ETIMEOUT, "a bounded device wait in the tensor-core MAC gave up");
+    });
+}
+
+extern "C" int he_conv_time(const he_params* p, const he_conv_desc* d, const int32_t* weights, const he_tune* tune,
+                            int reps, void* stream, float* stage_ms, float* total_ms) {
+    return guard([&] {
+        if (!p || !d || !weights || !total_ms || reps < 1 || reps > 1000) fail(HE_EINVAL, "bad argument");
+        std::unique_ptr<he_plan> P = build_plan(p, nullptr, d, weights, tune);
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t ctw = 2ull * p->L * p->N;
+        struct Buf {
+            void* ptr = nullptr;
+            ~Buf() {
+                if (ptr) cudaFree(ptr);
+            }
+        } in, out, ws;
+        CUDA_OK(cudaMalloc(&in.ptr, std::max<size_t>(256, P->lay.n_ct_in * ctw * 8)));
+        CUDA_OK(cudaMalloc(&out.ptr, std::max<size_t>(256, P->lay.n_ct_out * ctw * 8)));
+        CUDA_OK(cudaMalloc(&ws.ptr, std::max<size_t>(256, P->ws_bytes)));
+        fill_uniform(P->kp, (u64*)in.ptr, (size_t)P->lay.n_ct_in * 2 * p->L, 0xc0ffee, s);
+        struct Events {
+            cudaEvent_t e[5] = {};
+            ~Events() {
+                for (auto x : e)
+                    if (x) cudaEventDestroy(x);
+            }
+        } ev;
+        for (auto& x : ev.e) CUDA_OK(cudaEventCreate(&x));
+        std::vector<StageLayer> ls{P->stage_layer((const u64*)in.ptr, (u64*)out.ptr, (char*)ws.ptr)};
+        run_layers(p, P->kp, ls, s, false);  // warm-up (also sets the kernels' attributes)
+        std::vector<std::vector<float>> t(5, std::vector<float>(reps));
+        for (int r = 0; r < reps; r++) {
+            run_layers(p, P->kp, ls, s, false, true, ev.e);
+            CUDA_OK(cudaEventSynchronize(ev.e[4]));
+            for (int i = 0; i < 4; i++) CUDA_OK(cudaEventElapsedTime(&t[i][r], ev.e[i], ev.e[i + 1]));
+            CUDA_OK(cudaEventElapsedTime(&t[4][r], ev.e[0], ev.e[4]));
+        }
+        int v = 0;
+        CUDA_OK(cudaMemcpy(&v, P->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v) fail(HE_ETIMEOUT, "a bounded device wait in the tensor-core MAC gave up");
+        auto median = [](std::vector<float> x) {
+            std::sort(x.begin(), x.end());
+            return x[x.size() / 2];
+        };
+        for (int i = 0; i < 4 && stage_ms; i++) stage_ms[i] = median(t[i]);
+        *total_ms = median(t[4]);
     });
 }
 

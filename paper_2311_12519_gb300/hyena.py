@@ -47,7 +47,7 @@ class he_layout(ctypes.Structure):
 
 
 class he_tune(ctypes.Structure):
-    _fields_ = [("mac_groups", u32), ("mac_impl", u32), ("reserved", u32 * 6)]
+    _fields_ = [("mac_groups", u32), ("mac_impl", u32), ("tc_rows", u32), ("reserved", u32 * 5)]
 
 
 class he_stage_times(ctypes.Structure):
@@ -103,6 +103,7 @@ def load(build_if_stale: bool = True):
         "he_conv_forward_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
         "he_conv_status": (ctypes.c_int, [vp]),
         "he_conv_info": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "he_conv_time": (ctypes.c_int, [vp, P(he_conv_desc), vp, P(he_tune), ctypes.c_int, vp, vp, P(ctypes.c_float)]),
         "he_batch_create": (ctypes.c_int, [vp, ctypes.c_int, P(vp)]),
         "he_batch_create_limited": (ctypes.c_int, [vp, ctypes.c_int, sz, P(vp)]),
         "he_batch_waves": (ctypes.c_int, [vp, P(ctypes.c_int)]),
@@ -116,6 +117,15 @@ def load(build_if_stale: bool = True):
         "he_rotate": (ctypes.c_int, [vp, vp, u32, vp, vp, ctypes.c_int, vp, vp]),
         "he_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "he_profile_collect": (ctypes.c_int, [P(he_stage_times)]),
+        "he_mlp_create": (ctypes.c_int, [u32, u64, P(vp)]),
+        "he_mlp_param_count": (ctypes.c_int, [vp, P(u32)]),
+        "he_mlp_get_params": (ctypes.c_int, [vp, vp]),
+        "he_mlp_set_params": (ctypes.c_int, [vp, vp]),
+        "he_mlp_fit_scaling": (ctypes.c_int, [vp, vp, vp, u32, vp]),
+        "he_mlp_step": (ctypes.c_int, [vp, vp, vp, u32, u32, ctypes.c_float, u64, vp, P(ctypes.c_float)]),
+        "he_mlp_train": (ctypes.c_int, [vp, vp, vp, u32, u32, u32, ctypes.c_float, u64, vp, P(ctypes.c_float)]),
+        "he_mlp_predict": (ctypes.c_int, [vp, vp, u32, vp, vp]),
+        "he_mlp_destroy": (None, [vp]),
     }
     for name, (res, args) in A.items():
         f = getattr(lib, name)
@@ -252,12 +262,23 @@ def he_decrypt_slots(p, sk, ct, N):
 
 
 # ---------------------------------------------------------------------- server
-def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0, mac_impl=0):
+def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0):
     w = np.ascontiguousarray(weights, dtype=np.int32)
-    t = he_tune(mac_groups, mac_impl)
+    t = he_tune(mac_groups, mac_impl, tc_rows)
     h = vp()
     _check(load().he_conv_plan(p, gk, ctypes.byref(d), _ptr(w), ctypes.byref(t), ctypes.byref(h)), "he_conv_plan")
     return h.value
+
+
+def he_conv_time(p, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0, reps=3, stream=0):
+    """(total ms, [ntt_in, keyswitch, mac, ntt_out] ms): medians over `reps` timed forwards."""
+    w = np.ascontiguousarray(weights, dtype=np.int32)
+    t = he_tune(mac_groups, mac_impl, tc_rows)
+    st = (ctypes.c_float * 4)()
+    tot = ctypes.c_float()
+    _check(load().he_conv_time(p, ctypes.byref(d), _ptr(w), ctypes.byref(t), reps, stream, st, ctypes.byref(tot)),
+           "he_conv_time")
+    return tot.value, list(st)
 
 
 def he_conv_status(plan):
@@ -373,3 +394,47 @@ def he_profile_collect():
     t = he_stage_times()
     _check(load().he_profile_collect(ctypes.byref(t)), "he_profile_collect")
     return {STAGES[i]: (t.ms[i], t.launches[i]) for i in range(4)}
+
+
+# ------------------------------------------------------------------ cost model network
+def he_mlp_create(n_features, seed):
+    h = vp()
+    _check(load().he_mlp_create(n_features, seed, ctypes.byref(h)), "he_mlp_create")
+    return h.value
+
+
+def he_mlp_params(m):
+    n = u32()
+    _check(load().he_mlp_param_count(m, ctypes.byref(n)), "he_mlp_param_count")
+    out = np.zeros(n.value, dtype=np.float32)
+    _check(load().he_mlp_get_params(m, _ptr(out)), "he_mlp_get_params")
+    return out
+
+
+def he_mlp_set_params(m, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().he_mlp_set_params(m, _ptr(a)), "he_mlp_set_params")
+
+
+def he_mlp_fit_scaling(m, d_X, d_y, n, stream=0):
+    _check(load().he_mlp_fit_scaling(m, d_X, d_y, n, stream), "he_mlp_fit_scaling")
+
+
+def he_mlp_step(m, d_X, d_y, n, batch, lr, seed, stream=0):
+    loss = ctypes.c_float()
+    _check(load().he_mlp_step(m, d_X, d_y, n, batch, lr, seed, stream, ctypes.byref(loss)), "he_mlp_step")
+    return loss.value
+
+
+def he_mlp_train(m, d_X, d_y, n, steps, batch, lr, seed, stream=0):
+    loss = ctypes.c_float()
+    _check(load().he_mlp_train(m, d_X, d_y, n, steps, batch, lr, seed, stream, ctypes.byref(loss)), "he_mlp_train")
+    return loss.value
+
+
+def he_mlp_predict(m, d_X, n, d_y, stream=0):
+    _check(load().he_mlp_predict(m, d_X, n, d_y, stream), "he_mlp_predict")
+
+
+def he_mlp_destroy(m):
+    load().he_mlp_destroy(m)

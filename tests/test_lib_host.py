@@ -14,7 +14,9 @@ from paper_2311_12519_gb300 import hyena as H
 
 
 def _declared():
-    src = open(H._build.os.path.join(H._build.os.path.dirname(H._build.HERE), "include", "hyena.h")).read()
+    inc = H._build.os.path.join(H._build.os.path.dirname(H._build.HERE), "include")
+    src = "".join(open(H._build.os.path.join(inc, f)).read() for f in sorted(H._build.os.listdir(inc))
+                  if f.endswith(".h"))
     return sorted(set(re.findall(r"\b(he_[a-z0-9_]+)\s*\(", src)))
 
 

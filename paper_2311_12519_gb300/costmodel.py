@@ -216,13 +216,14 @@ def random_shape(rng) -> Shape:
                  int(rng.choice([1, 2, 4, 8])))
 
 
-def collect(rings: Rings, n_samples: int, seed: int = 1, max_ws_gb: float = 6.0, log=None):
-    """Times n_samples random (shape, configuration) pairs; returns X [4n][F], y [4n] (log2 ms)
-    and the raw records."""
+def collect(rings: Rings, n_samples: int, seed: int = 1, max_ws_gb: float = 6.0, log=None,
+            max_seconds: float = float("inf")):
+    """Times n_samples random (shape, configuration) pairs (fewer if max_seconds runs out);
+    returns X [4n][F], y [4n] (log2 ms) and the raw records."""
     rng = np.random.default_rng(seed)
     X, y, recs = [], [], []
     t0 = time.time()
-    while len(recs) < n_samples:
+    while len(recs) < n_samples and time.time() - t0 < max_seconds:
         s = random_shape(rng)
         N, L = TRAIN_RINGS[rng.integers(len(TRAIN_RINGS))]
         c_n = int(rng.choice([1, 2]))
@@ -331,6 +332,7 @@ def main():
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--out", default="costmodel_out")
     ap.add_argument("--stacks", default="resnet20,vgg16,mobilenet")
+    ap.add_argument("--collect-seconds", type=float, default=600.0)
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     torch.cuda.set_device(0)
@@ -340,7 +342,7 @@ def main():
 
     rings = Rings()
     t0 = time.time()
-    X, y, recs = collect(rings, args.samples, log=log)
+    X, y, recs = collect(rings, args.samples, log=log, max_seconds=args.collect_seconds)
     t_collect = time.time() - t0
     np.savez_compressed(os.path.join(args.out, "latencies.npz"), X=X, y=y)
     # hold out every fifth layer to measure the model's error on unseen layers
@@ -375,6 +377,7 @@ def main():
             "speedup_pick_vs_default": tot["default_ms"] / tot["pick_ms"],
             "speedup_best_vs_default": tot["default_ms"] / tot["best_ms"]}
         log(json.dumps({k: v for k, v in report["stacks"][name].items() if k != "layers"}))
+        json.dump(report, open(os.path.join(args.out, "report.json"), "w"), indent=1)
     json.dump(report, open(os.path.join(args.out, "report.json"), "w"), indent=1)
     log(json.dumps({k: v for k, v in report.items() if k != "stacks"}))
     model.close()

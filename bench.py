@@ -48,7 +48,7 @@ L2_BYTES = 129 * 2**20
 # DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the device source with this sha256 prefix;
 # reported as roofline traffic only while device.cu is unchanged
-PROFILED_TRAFFIC = {"source": "03c81fc60a59f009", "k_keyswitch": 2.712e9, "k_mac_tc": 2.359e9, "k_ntt_inputs": 0.380e9,
+PROFILED_TRAFFIC = {"source": "610fe83b17ca5fff", "k_keyswitch": 2.714e9, "k_mac_tc": 2.358e9, "k_ntt_inputs": 0.381e9,
                     "k_intt": 0.223e9}
 
 
@@ -352,7 +352,8 @@ def run_gpu(args, rank, world):
     src = hashlib.sha256(open(os.path.join(ROOT, "paper_2311_12519_gb300", "csrc", "device.cu"), "rb").read())
     kname = {"mac": "k_mac_tc" if mac_tc else "k_mac", "keyswitch": "k_keyswitch", "ntt_in": "k_ntt_inputs",
              "ntt_out": "k_intt"}[top]
-    if src.hexdigest().startswith(PROFILED_TRAFFIC["source"]) and kname in PROFILED_TRAFFIC:
+    if (src.hexdigest().startswith(PROFILED_TRAFFIC["source"]) and kname in PROFILED_TRAFFIC
+            and args.workload == "resnet20"):
         roof["traffic"] = PROFILED_TRAFFIC[kname]
     roof["kernel"] = kname
     roof["stage_share"] = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages_b.values())), 4)

@@ -185,6 +185,28 @@ def run_gpu(args, rank, world):
     info = H.he_params_info(p)
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
+    tunes = [{} for _ in specs]
+    tuned = None
+    if args.tuned:
+        # per layer, the fastest packing, tile and MAC schedule on this ring, timed exhaustively
+        from paper_2311_12519_gb300 import costmodel as CM
+
+        rings = CM.Rings()
+        rings.p[(N, L)] = p
+        t_tune = time.perf_counter()
+        tuned = []
+        for i, s in enumerate(specs):
+            shape = CM.Shape(s["C_in"], s["C_out"], s["H"], s["W"], s["kh"], s["stride"], s["depthwise"], images)
+            best, best_ms, times = CM.autotune(rings, shape, CM.candidates(rings, shape, [(N, L)]))
+            specs[i] = dict(s, c_n=best.c_n, tile_h=best.tile[0], tile_w=best.tile[1])
+            tunes[i] = dict(mac_groups=best.mac_groups, mac_impl=best.mac_impl, tc_rows=best.tc_rows)
+            # the untuned plan: packing 2, default tile, tensor core with 96 rows (CUDA cores if depthwise)
+            default = times.get(CM.Config(N, L, 2, (0, 0), 1, 0, 0) if s["depthwise"] else
+                                CM.Config(N, L, 2, (0, 0), 2, 96, 0))
+            tuned.append({"layer": i, "c_n": best.c_n, "tile": list(best.tile), **tunes[i], "ms": round(best_ms, 4),
+                          "default_ms": None if default is None else round(default, 4), "candidates": len(times)})
+        rings.p = {}
+        tune_s = time.perf_counter() - t_tune
     descs = [H.conv_desc(**s) for s in specs]
     gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
     gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
@@ -196,10 +218,10 @@ def run_gpu(args, rank, world):
         act = synth.activations((images, s["C_in"], s["H"], s["W"]), info.t, label=i + ri["act_label"])
         wt = synth.weights((s["C_out"], 1 if s["depthwise"] else s["C_in"], s["kh"], s["kh"]), label=i)
         cts = H.he_encrypt_image(p, sk, d, act, ri["enc_seed"], info)
-        plan = H.he_conv_plan(p, gk, d, wt)
+        plan = H.he_conv_plan(p, gk, d, wt, **tunes[i])
         n_in, n_out, ws = H.he_conv_sizes(plan)
         lay = H.he_layout_for_layer(p, d)
-        n_rot = s["kh"] ** 2 * (1 if s["depthwise"] else 2)
+        n_rot = s["kh"] ** 2 * (2 if s["c_n"] == 2 and not s["depthwise"] else 1)
         cm, km = modmacs(s, lay, n_rot, L, l, N)
         conv_mm += cm
         ks_mm += km
@@ -387,6 +409,8 @@ def run_gpu(args, rank, world):
                             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
                             "clocks": clk.summary()},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages_b.items()},
+        "tuning": None if tuned is None else {"per_layer": tuned, "seconds": round(tune_s, 1),
+                                              "method": "exhaustive timing of every packing x tile x schedule"},
     }
     print(json.dumps(line), flush=True)
 
@@ -512,6 +536,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="resnet20", choices=sorted(WORKLOADS),
                     help="the headline ResNet-20 stack, or the VGG-16 (8 images) or MobileNetV1 (32 images) stack")
+    ap.add_argument("--tuned", action="store_true",
+                    help="pick each layer's packing, tile and MAC schedule by timing every candidate first")
     ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation"],
                     help="batch: only the batched forward, W + K times, no JSON (for profiler captures); "
                          "ablation: one JSON line per variant of the latency study (reduction, w, c_n, MAC unit)")

@@ -878,15 +878,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                         const u32 r = o * 8 + e;
                         v[e] = (kk0 + r < K) ? raw[r * TC_MTILE + nl] : 0;
                     }
+                    // the five 10-bit chunks of each residue as the low bits of 32-bit words, taken
+                    // from its 32-bit halves (chunk 3 straddles them: a funnel shift)
+                    u32 cw8[TC_CHUNKS][8];
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const u32 lo = (u32)v[e], hi = (u32)(v[e] >> 32);
+                        cw8[0][e] = lo;
+                        cw8[1][e] = lo >> 10;
+                        cw8[2][e] = lo >> 20;
+                        cw8[3][e] = __funnelshift_r(lo, hi, 30);
+                        cw8[4][e] = hi >> 8;
+                    }
 #pragma unroll
                     for (int c = 0; c < TC_CHUNKS; c++) {
                         u32 w[4];
 #pragma unroll
                         for (int e = 0; e < 8; e += 2) {
                             // fp16 bits of 1024 + x are 0x6400 | x; subtracting 1536 gives x - 512 exactly
-                            const u32 x0 = 0x6400u | (u32)((v[e] >> (10 * c)) & 0x3FF);
-                            const u32 x1 = 0x6400u | (u32)((v[e + 1] >> (10 * c)) & 0x3FF);
-                            const u32 packed = x0 | (x1 << 16);
+                            const u32 packed = (cw8[c][e] & 0x3FFu) | ((cw8[c][e + 1] << 16) & 0x3FF0000u) | 0x64006400u;
                             __half2 h = *reinterpret_cast<const __half2*>(&packed);
                             h = __hsub2(h, __float2half2_rn(1536.0f));
                             w[e / 2] = *reinterpret_cast<u32*>(&h);

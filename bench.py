@@ -415,6 +415,88 @@ def run_gpu(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ learned configuration
+def run_learned(args):
+    """The stack with every layer in the configuration the learned cost model picks (ring,
+    packing, tile, MAC schedule; no timing of candidates), layers of one ring batched and
+    replayed as CUDA graphs; a step runs every ring's batch once."""
+    import torch
+
+    from paper_2311_12519_gb300 import costmodel as CM
+    from paper_2311_12519_gb300 import hyena as H
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    if not os.path.exists(CM.WEIGHTS):
+        print(json.dumps({"mode": "learned", "unavailable": "no trained cost model weights in the package"}))
+        return
+    _, n_ring, n_limbs, images, ws_limit, workload = WORKLOADS[args.workload]
+    specs = layer_descs(args.workload)
+    model = CM.CostModel.load(CM.WEIGHTS)
+    rings = CM.Rings()
+    t0 = time.perf_counter()
+    shapes = [CM.Shape(s["C_in"], s["C_out"], s["H"], s["W"], s["kh"], s["stride"], s["depthwise"], images)
+              for s in specs]
+    picks = [CM.pick(rings, model, sh) for sh in shapes]
+    pick_s = time.perf_counter() - t0
+    groups = {}
+    for i, c in enumerate(picks):
+        groups.setdefault((c.N, c.L), []).append(i)
+    batches, keep = [], []
+    for (N, L), idx in sorted(groups.items()):
+        p = rings.get(N, L)
+        info = H.he_params_info(p)
+        sk = H.he_keygen(p, synth.SEED_KEYS)
+        descs = {i: picks[i].desc(shapes[i]) for i in idx}
+        gal = sorted(set(int(g) for d in descs.values() for g in H.he_layer_galois(p, d)))
+        gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
+        plans, ins, outs = [], [], []
+        for i in idx:
+            s, c = specs[i], picks[i]
+            act = synth.activations((images, s["C_in"], s["H"], s["W"]), info.t, label=i)
+            wt = synth.weights((s["C_out"], 1 if s["depthwise"] else s["C_in"], s["kh"], s["kh"]), label=i)
+            cts = H.he_encrypt_image(p, sk, descs[i], act, synth.SEED_ENC, info)
+            plans.append(H.he_conv_plan(p, gk, descs[i], wt, mac_groups=c.mac_groups, mac_impl=c.mac_impl,
+                                        tc_rows=c.tc_rows))
+            ins.append(torch.from_numpy(cts.reshape(-1).view(np.int64)).to(dev))
+            outs.append(torch.empty(H.he_conv_sizes(plans[-1])[1], dtype=torch.int64, device=dev))
+        b = H.he_batch_create(plans) if ws_limit is None else H.he_batch_create_limited(plans, ws_limit)
+        ws = torch.empty(H.he_batch_workspace_bytes(b) // 8 + 1, dtype=torch.int64, device=dev)
+        batches.append((b, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], ws.data_ptr()))
+        keep += [ins, outs, ws, plans, gk, sk]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        for b, i_p, o_p, w in batches:
+            H.he_batch_graph_launch(b, i_p, o_p, w, sp)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(0) as clk:
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            torch.cuda.synchronize()
+    for plan in [pl for k in keep[3::6] for pl in k]:
+        H.he_conv_status(plan)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / args.steps
+    print(json.dumps({
+        "mode": "learned", "metric": METRIC if args.workload == "resnet20" else METRIC.replace("ResNet-20", args.workload),
+        "value": len(specs) * 1000.0 / ms, "unit": "layers/s", "ms_per_step": ms, "steps": args.steps,
+        "workload": workload.split(", N=")[0] + ", ring, packing, tile and MAC schedule per layer by the cost model",
+        "rings": {f"{N},{L}": len(idx) for (N, L), idx in sorted(groups.items())}, "pick_seconds": round(pick_s, 2),
+        "picks": [dict(layer=i, N=c.N, L=c.L, c_n=c.c_n, tile=list(c.tile), mac_impl=c.mac_impl, tc_rows=c.tc_rows,
+                       mac_groups=c.mac_groups) for i, c in enumerate(picks)],
+        "clocks": clk.summary(), "l2": "flushed before each timed step (256 MiB write)"}), flush=True)
+
+
 # ------------------------------------------------------------------ ablation
 ABLATION = [
     # (name, counterpart in the paper's latency study, decomp_bits, c_n, mac_impl)
@@ -538,9 +620,10 @@ def main():
                     help="the headline ResNet-20 stack, or the VGG-16 (8 images) or MobileNetV1 (32 images) stack")
     ap.add_argument("--tuned", action="store_true",
                     help="pick each layer's packing, tile and MAC schedule by timing every candidate first")
-    ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation"],
+    ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation", "learned"],
                     help="batch: only the batched forward, W + K times, no JSON (for profiler captures); "
-                         "ablation: one JSON line per variant of the latency study (reduction, w, c_n, MAC unit)")
+                         "ablation: one JSON line per variant of the latency study (reduction, w, c_n, MAC unit); "
+                         "learned: every layer in the configuration the trained cost model picks")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -550,6 +633,10 @@ def main():
     if args.mode == "ablation":
         if rank == 0:
             run_ablation(args)
+        return
+    if args.mode == "learned":
+        if rank == 0:
+            run_learned(args)
         return
     if world > 1:
         import torch

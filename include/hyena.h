@@ -205,6 +205,11 @@ int he_conv_status(const he_plan* plan);
  * accumulation) is chosen automatically when it is exact: no depthwise and
  * |s| <= 16. */
 int he_conv_info(const he_plan* plan, int* mac_impl);
+/* The host-side checks of he_conv_plan alone (layout, scalars, the noise
+ * estimate, the tensor-core exactness bound, the tune fields), without keys
+ * and without touching the device: HE_OK if he_conv_plan would accept this
+ * configuration, else the error it would return (HE_EINVAL, HE_ENOISE). */
+int he_conv_check(const he_params* p, const he_conv_desc* d, const int32_t* weights, const he_tune* tune);
 /* Device time of one forward of this layer configuration, for tuning and for
  * training the cost model: builds a plan whose key-switching keys and input
  * ciphertexts are uniform residues made on the device (the kernels do the same

@@ -233,6 +233,9 @@ def collect(rings: Rings, n_samples: int, seed: int = 1, max_ws_gb: float = 6.0,
         f = features(rings, s, c)
         if f is None or workspace_gb(rings, s, c) > max_ws_gb:
             continue
+        if H.he_conv_check(rings.get(N, L), c.desc(s), timing_weights(s), c.mac_groups, c.mac_impl,
+                           c.tc_rows) != H.HE_OK:
+            continue
         r = measure(rings, s, c)
         if r is None:
             continue
@@ -272,8 +275,33 @@ class CostModel:
         rows = self.predict_rows(np.concatenate(feats))
         return (2.0 ** rows.reshape(-1, 4)).sum(axis=1)
 
+    def save(self, path):
+        json.dump({"n_features": N_FEATURES, "params": [float(x) for x in H.he_mlp_params(self.m)]},
+                  open(path, "w"))
+
+    @classmethod
+    def load(cls, path):
+        d = json.load(open(path))
+        if d["n_features"] != N_FEATURES:
+            raise ValueError("cost model weights were trained on another feature set")
+        m = cls()
+        H.he_mlp_set_params(m.m, np.array(d["params"], dtype=np.float32))
+        return m
+
     def close(self):
         H.he_mlp_destroy(self.m)
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.json")
+
+
+def pick(rings: Rings, model: CostModel, s: Shape, ring_list=SELECT_RINGS, max_ws_gb: float = 60.0) -> Config:
+    """The model's choice among the candidate configurations of a layer (no timing)."""
+    w = timing_weights(s)
+    cands = [c for c in candidates(rings, s, ring_list) if workspace_gb(rings, s, c) <= max_ws_gb
+             and H.he_conv_check(rings.get(c.N, c.L), c.desc(s), w, c.mac_groups, c.mac_impl, c.tc_rows) == H.HE_OK]
+    pred = model.predict_layers([features(rings, s, c) for c in cands])
+    return cands[int(np.argmin(pred))]
 
 
 def autotune(rings: Rings, s: Shape, cands: list, reps: int = 2):
@@ -333,6 +361,7 @@ def main():
     ap.add_argument("--out", default="costmodel_out")
     ap.add_argument("--stacks", default="resnet20,vgg16,mobilenet")
     ap.add_argument("--collect-seconds", type=float, default=600.0)
+    ap.add_argument("--save-model", default=None, help="also write the trained weights (JSON) here")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     torch.cuda.set_device(0)
@@ -363,10 +392,13 @@ def main():
     model.close()
     model = CostModel()
     model.train(X, y, steps=args.steps)
+    if args.save_model:
+        model.save(args.save_model)
     report = {"samples_layers": n, "kernel_latencies": int(len(y)), "collect_s": t_collect, "train_s": t_train,
               "final_train_loss": loss, "holdout_median_rel_error_stage": err_stage,
               "holdout_median_rel_error_layer": err_layer, "stacks": {}}
-    for name in args.stacks.split(","):
+    json.dump(report, open(os.path.join(args.out, "report.json"), "w"), indent=1)
+    for name in [x for x in args.stacks.split(",") if x]:
         fn, ring = STACKS[name]
         res = evaluate(rings, model, fn(synth), ring, log=log)
         tot = {k: sum(r[k] for r in res) for k in ("best_ms", "pick_ms", "default_ms")}

@@ -1405,7 +1405,7 @@ struct he_plan {
 // Builds a plan.  gk == nullptr: timing plan, whose key-switching keys are
 // uniform residues made on the device (same sizes and kernels, no secret).
 static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys* gk, const he_conv_desc* d,
-                                           const int32_t* weights, const he_tune* tune) {
+                                           const int32_t* weights, const he_tune* tune, bool host_only = false) {
     auto P = std::make_unique<he_plan>();
     P->p = p;
     P->d = *d;
@@ -1489,6 +1489,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     const u32 tc_rows_req = tune ? tune->tc_rows : 0;
     if (tc_rows_req && (tc_rows_req % 16 || tc_rows_req > (u32)TC_NMAX))
         fail(HE_EINVAL, "tc_rows must be a multiple of 16, at most 96");
+    if (host_only) return P;
     // device data
     CUDA_OK(cudaGetDevice(&P->device));
     P->kp = make_kp(p);
@@ -1631,6 +1632,13 @@ extern "C" int he_conv_status(const he_plan* plan) {
         int v = 0;
         CUDA_OK(cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (v) fail(HE_ETIMEOUT, "a bounded device wait in the tensor-core MAC gave up");
+    });
+}
+
+extern "C" int he_conv_check(const he_params* p, const he_conv_desc* d, const int32_t* weights, const he_tune* tune) {
+    return guard([&] {
+        if (!p || !d || !weights) fail(HE_EINVAL, "null argument");
+        build_plan(p, nullptr, d, weights, tune, true);
     });
 }
 

@@ -97,3 +97,23 @@ def test_collect_and_evaluate_pipeline_with_a_synthetic_clock(monkeypatch):
         assert r["regret"] >= 0 and r["pick_ms"] >= r["best_ms"] > 0 and 1 <= r["rank_of_pick"] <= r["n_candidates"]
         assert r["default_ms"] > 0
     rings.close()
+
+
+def test_conv_check_matches_the_plan_rules_on_the_host():
+    """he_conv_check runs the plan's host checks without a device: valid configurations pass,
+    a tensor-core request beyond the exactness bound and a bad tune field are refused, and a
+    layer whose weights exceed the noise budget is refused with HE_ENOISE."""
+    p = H.he_params_create(4096, 2, decomp_bits=25)
+    d = H.conv_desc(16, 16, 16, 16)
+    w = np.full((16, 16, 3, 3), 8, dtype=np.int32)
+    assert H.he_conv_check(p, d, w) == H.HE_OK
+    assert H.he_conv_check(p, d, w, mac_impl=2, tc_rows=64) == H.HE_OK
+    assert H.he_conv_check(p, d, w, mac_impl=2, tc_rows=40) == H.HE_EINVAL
+    assert H.he_conv_check(p, d, np.full((16, 16, 3, 3), 9, dtype=np.int32), mac_impl=2) == H.HE_EINVAL
+    H.he_params_destroy(p)
+    # a 50-bit decomposition base at two limbs leaves no room for large weights
+    p = H.he_params_create(4096, 2, decomp_bits=50)
+    assert H.he_conv_check(p, H.conv_desc(64, 16, 7, 7), np.full((16, 64, 3, 3), 8, dtype=np.int32)) == H.HE_OK
+    assert H.he_conv_check(p, H.conv_desc(64, 16, 7, 7), np.full((16, 64, 3, 3), 16000, dtype=np.int32)) == \
+        H.HE_ENOISE
+    H.he_params_destroy(p)

@@ -6,8 +6,9 @@ per GPU, N = 8192, L = 3 RNS limbs of 50 bits, t = 1032193, Hyena packing
 resident in HBM.  value = layers/s over all ranks of the batched form (one
 launch per stage for all layers, replayed as a CUDA graph); the plain
 per-layer form (he_conv_forward per layer) is reported beside it, with
-modMAC/s.  e2e repeats the step through he_conv_forward_host with pinned
-host buffers (copies inside the timed region).  --workload vgg16|mobilenet
+modMAC/s.  e2e repeats the step from pinned host buffers through
+he_batch_forward_host (copies inside the timed region; layer by layer through
+he_conv_forward_host beside it).  --workload vgg16|mobilenet
 measures the VGG-16 (8 images, N = 16384) or MobileNetV1 (32 images) stack
 the same way; --mode ablation prints one line per variant of the latency
 study; --impl reference times the CPU oracle instead.
@@ -323,18 +324,24 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         H.he_profile_enable(False)
         stages_b = H.he_profile_collect()
-        # end to end through host buffers
-        for _ in range(2):
-            step_host()
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step_host()
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        barrier()
-    ms, ms_plain, e2e_s = reduce_max([ms, ms_plain, e2e_s], dev, world)
+        # end to end through host buffers: the batch (he_batch_forward_host), and layer by layer
+        def step_host_batch():
+            H.he_batch_forward_host(batch, h_ins, h_outs, d_ins, d_outs, d_wsb.data_ptr(), sp)
+
+        e2e = {}
+        for name, fn in (("batch", step_host_batch), ("plain", step_host)):
+            for _ in range(2):
+                fn()
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                fn()
+            torch.cuda.synchronize()
+            e2e[name] = time.perf_counter() - t0
+            barrier()
+        e2e_s, e2e_plain_s = e2e["batch"], e2e["plain"]
+    ms, ms_plain, e2e_s, e2e_plain_s = reduce_max([ms, ms_plain, e2e_s, e2e_plain_s], dev, world)
     if rank != 0:
         return
     ms_step = ms / args.steps
@@ -397,7 +404,9 @@ def run_gpu(args, rank, world):
         "modmac_per_step": {"conv": conv_mm, "keyswitch": ks_mm},
         "e2e": {"value": layers_per_second(world, n_layers, args.steps, e2e_s), "unit": "layers/s",
                 "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": out_bytes},
+                "d2h_bytes_per_step": out_bytes,
+                "call": "he_batch_forward_host (pinned host buffers, copies and graph replay in the timed region)",
+                "plain_per_layer": layers_per_second(world, n_layers, args.steps, e2e_plain_s)},
         "gpu_launches": sum(v[1] for v in stages_b.values()),
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -278,6 +278,12 @@ int he_batch_forward(const he_batch* b, const uint64_t* const* d_in, uint64_t* c
  * calls with the same pointers replay it.  Needs a non-default stream. */
 int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_workspace,
                           void* stream);
+/* The batch end to end from host memory: copies every layer's input
+ * ciphertexts h_in[i] (pinned host memory for asynchronous copies) to d_in[i],
+ * replays the batch's graph, copies every output d_out[i] to h_out[i], and
+ * synchronises the stream (non-default).  Outputs equal he_batch_forward's. */
+int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, uint64_t* const* h_out, uint64_t* const* d_in,
+                          uint64_t* const* d_out, void* d_workspace, void* stream);
 void he_batch_destroy(he_batch* b);
 
 /* ------------------------------------------------------------------ */

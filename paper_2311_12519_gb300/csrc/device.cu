@@ -1789,41 +1789,63 @@ extern "C" int he_batch_forward(const he_batch* b, const uint64_t* const* d_in, 
     });
 }
 
+static void batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_ws,
+                               cudaStream_t s) {
+    check_device(b->device);
+    bool same = b->exec && b->g_ws == d_ws && b->g_stream == s;
+    for (size_t i = 0; same && i < b->plans.size(); i++) same = b->g_in[i] == d_in[i] && b->g_out[i] == d_out[i];
+    if (!same) {
+        for (size_t i = 0; i < b->plans.size(); i++) check_ptrs(d_in[i], d_out[i], d_ws);
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        // one ordinary pass sets the kernels' attributes before capture
+        b->run(d_in, d_out, (char*)d_ws, s, false);
+        cudaGraph_t g = nullptr;
+        CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            b->run(d_in, d_out, (char*)d_ws, s, false);
+        } catch (...) {
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CUDA_OK(cudaStreamEndCapture(s, &g));
+        cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) fail(HE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        b->g_in.assign(d_in, d_in + b->plans.size());
+        b->g_out.assign(d_out, d_out + b->plans.size());
+        b->g_ws = d_ws;
+        b->g_stream = s;
+    }
+    CUDA_OK(cudaGraphLaunch(b->exec, s));
+}
+
 extern "C" int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* const* d_out, void* d_ws,
                                      void* stream) {
     return guard([&] {
         if (!b || !d_in || !d_out || !d_ws || !stream) fail(HE_EINVAL, "graph launches need pointers and a non-default stream");
-        check_device(b->device);
+        batch_graph_launch(b, d_in, d_out, d_ws, (cudaStream_t)stream);
+    });
+}
+
+extern "C" int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, uint64_t* const* h_out,
+                                     uint64_t* const* d_in, uint64_t* const* d_out, void* d_ws, void* stream) {
+    return guard([&] {
+        if (!b || !h_in || !h_out || !d_in || !d_out || !d_ws || !stream)
+            fail(HE_EINVAL, "null argument (host and device buffers of every layer, a non-default stream)");
         cudaStream_t s = (cudaStream_t)stream;
-        bool same = b->exec && b->g_ws == d_ws && b->g_stream == s;
-        for (size_t i = 0; same && i < b->plans.size(); i++) same = b->g_in[i] == d_in[i] && b->g_out[i] == d_out[i];
-        if (!same) {
-            for (size_t i = 0; i < b->plans.size(); i++) check_ptrs(d_in[i], d_out[i], d_ws);
-            if (b->exec) {
-                cudaGraphExecDestroy(b->exec);
-                b->exec = nullptr;
-            }
-            // one ordinary pass sets the kernels' attributes before capture
-            b->run(d_in, d_out, (char*)d_ws, s, false);
-            cudaGraph_t g = nullptr;
-            CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            try {
-                b->run(d_in, d_out, (char*)d_ws, s, false);
-            } catch (...) {
-                cudaStreamEndCapture(s, &g);
-                if (g) cudaGraphDestroy(g);
-                throw;
-            }
-            CUDA_OK(cudaStreamEndCapture(s, &g));
-            cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) fail(HE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-            b->g_in.assign(d_in, d_in + b->plans.size());
-            b->g_out.assign(d_out, d_out + b->plans.size());
-            b->g_ws = d_ws;
-            b->g_stream = s;
+        const size_t ctw = 2ull * b->p->L * b->p->N;
+        for (size_t i = 0; i < b->plans.size(); i++) {
+            if (!h_in[i] || !h_out[i]) fail(HE_EINVAL, "null host buffer");
+            CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice, s));
         }
-        CUDA_OK(cudaGraphLaunch(b->exec, s));
+        batch_graph_launch(b, d_in, d_out, d_ws, s);
+        for (size_t i = 0; i < b->plans.size(); i++)
+            CUDA_OK(cudaMemcpyAsync(h_out[i], d_out[i], b->plans[i]->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaStreamSynchronize(s));
     });
 }
 

@@ -111,6 +111,7 @@ def load(build_if_stale: bool = True):
         "he_batch_workspace_bytes": (ctypes.c_int, [vp, P(sz)]),
         "he_batch_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "he_batch_graph_launch": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "he_batch_forward_host": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp]),
         "he_batch_destroy": (None, [vp]),
         "he_ntt_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "he_ntt_inverse": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
@@ -368,6 +369,11 @@ def he_batch_forward(b, d_ins, d_outs, d_ws, stream=0):
 def he_batch_graph_launch(b, d_ins, d_outs, d_ws, stream):
     a, o = _ptr_array(d_ins), _ptr_array(d_outs)
     _check(load().he_batch_graph_launch(b, a, o, _ptr(d_ws), stream or None), "he_batch_graph_launch")
+
+
+def he_batch_forward_host(b, h_ins, h_outs, d_ins, d_outs, d_ws, stream):
+    _check(load().he_batch_forward_host(b, _ptr_array(h_ins), _ptr_array(h_outs), _ptr_array(d_ins),
+                                        _ptr_array(d_outs), d_ws, stream), "he_batch_forward_host")
 
 
 def he_batch_destroy(b):

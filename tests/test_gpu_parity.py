@@ -327,6 +327,15 @@ def test_batch_equals_single_layers(small):
         for i in range(len(plans)):
             assert torch.equal(d_outs[i], refs[i]), f"layer {i} differs in the graph replay"
             d_outs[i].fill_(-1)
+    # end to end from pinned host buffers
+    h_ins = [t.cpu().pin_memory() for t in d_ins]
+    h_outs = [torch.full((t.numel(),), -1, dtype=torch.int64).pin_memory() for t in d_outs]
+    for t in d_ins:
+        t.fill_(0)
+    H.he_batch_forward_host(b, [t.data_ptr() for t in h_ins], [t.data_ptr() for t in h_outs],
+                            [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(), s.cuda_stream)
+    for i in range(len(plans)):
+        assert torch.equal(h_outs[i], refs[i].cpu()), f"layer {i} differs through the host path"
     H.he_batch_destroy(b)
     for plan, gk, _ in items:
         H.he_conv_status(plan)

@@ -205,6 +205,13 @@ int he_conv_status(const he_plan* plan);
  * accumulation) is chosen automatically when it is exact: no depthwise and
  * |s| <= 16. */
 int he_conv_info(const he_plan* plan, int* mac_impl);
+/* Failure-detection self-test (no paper counterpart).  One CTA waits, through
+ * the bounded mbarrier wait every role of the tensor-core MAC uses, on a
+ * barrier that nothing arrives at; the wait gives up after its poll limit and
+ * reports through a device status word, as a stalled MAC pipeline would.
+ * Returns HE_ETIMEOUT when that happened (the expected result; the context
+ * stays usable), HE_OK if the wait wrongly completed, or HE_ECUDA. */
+int he_selftest_bounded_wait(void* stream);
 /* The host-side checks of he_conv_plan alone (layout, scalars, the noise
  * estimate, the tensor-core exactness bound, the tune fields), without keys
  * and without touching the device: HE_OK if he_conv_plan would accept this

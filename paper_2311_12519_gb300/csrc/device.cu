@@ -671,6 +671,40 @@ constexpr long long TC_SPIN_LIMIT = 1ll << 22;                     // bounded mb
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
 
+// Waits for phase `parity` of the mbarrier at shared address bar, for at most `limit` polls.
+// Gives up at once when *abort_flag is set (another role gave up) and, when the limit runs out,
+// sets *abort_flag and *err so that every role leaves and the host sees the failure.
+__device__ __forceinline__ bool mbar_wait_bounded(u32 bar, u32 parity, long long limit, volatile int* abort_flag,
+                                                  int* err) {
+    for (long long it = 0; it < limit; it++) {
+        if (*abort_flag) return false;
+        u32 ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    *abort_flag = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+// Failure-detection self-test: one CTA waits on an mbarrier that nothing arrives at, through the
+// tensor-core MAC's bounded wait, which must give up and report through *err.
+__global__ void k_wait_selftest(int* err, long long limit) {
+    __shared__ __align__(8) u64 bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    mbar_wait_bounded(smem_u32(&bar), 0, limit, &abort_flag, err);
+}
+
 // byte offset of element (row, kk) inside a K-major no-swizzle tile with 64-term rows
 __device__ __forceinline__ u32 kmajor_off(u32 row, u32 kk) {
     return (row >> 3) * TC_SBO + (kk >> 3) * 128u + (row & 7u) * 16u + (kk & 7u) * 2u;
@@ -760,21 +794,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     int* err = B.L[0].err;
 
     // bounded wait that gives up at once when another role has given up
-    auto wait = [&](int i, u32 parity) -> bool {
-        for (long long it = 0; it < TC_SPIN_LIMIT; it++) {
-            if (*abort_flag) return false;
-            u32 ok;
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(ok)
-                : "r"(bar(i)), "r"(parity)
-                : "memory");
-            if (ok) return true;
-        }
-        *abort_flag = 1;
-        atomicExch(err, 1);
-        return false;
-    };
+    auto wait = [&](int i, u32 parity) -> bool { return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, err); };
     auto arrive = [&](int i) { asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(i)) : "memory"); };
 
     if (warp == 0) {
@@ -1632,6 +1652,25 @@ extern "C" int he_conv_status(const he_plan* plan) {
         int v = 0;
         CUDA_OK(cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (v) fail(HE_ETIMEOUT, "a bounded device wait in the tensor-core MAC gave up");
+    });
+}
+
+extern "C" int he_selftest_bounded_wait(void* stream) {
+    return guard([&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        int* d_err = nullptr;
+        CUDA_OK(cudaMalloc(&d_err, sizeof(int)));
+        struct Free {
+            int* p;
+            ~Free() { cudaFree(p); }
+        } f{d_err};
+        CUDA_OK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+        k_wait_selftest<<<1, 32, 0, s>>>(d_err, TC_SPIN_LIMIT >> 6);
+        check_launch("k_wait_selftest");
+        int v = 0;
+        CUDA_OK(cudaMemcpyAsync(&v, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaStreamSynchronize(s));
+        if (v) fail(HE_ETIMEOUT, "bounded wait gave up as designed");
     });
 }
 

@@ -103,6 +103,7 @@ def load(build_if_stale: bool = True):
         "he_conv_forward_noalloc": (ctypes.c_int, [vp, vp, vp, vp]),
         "he_conv_status": (ctypes.c_int, [vp]),
         "he_conv_info": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "he_selftest_bounded_wait": (ctypes.c_int, [vp]),
         "he_conv_check": (ctypes.c_int, [vp, P(he_conv_desc), vp, P(he_tune)]),
         "he_conv_time": (ctypes.c_int, [vp, P(he_conv_desc), vp, P(he_tune), ctypes.c_int, vp, vp, P(ctypes.c_float)]),
         "he_batch_create": (ctypes.c_int, [vp, ctypes.c_int, P(vp)]),
@@ -270,6 +271,11 @@ def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_r
     h = vp()
     _check(load().he_conv_plan(p, gk, ctypes.byref(d), _ptr(w), ctypes.byref(t), ctypes.byref(h)), "he_conv_plan")
     return h.value
+
+
+def he_selftest_bounded_wait(stream=0):
+    """The status code of the bounded-wait self-test (HE_ETIMEOUT is the expected result)."""
+    return load().he_selftest_bounded_wait(stream)
 
 
 def he_conv_check(p, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0):

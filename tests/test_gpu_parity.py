@@ -379,3 +379,16 @@ def test_batch_of_resnet20_stack_matches_oracle_samples(resnet):
         H.he_conv_status(plan)
         H.he_plan_destroy(plan)
         H.he_galkeys_destroy(gk)
+
+
+# ---------------------------------------------------------------- failure detection
+def test_bounded_wait_gives_up_and_the_context_stays_usable(small):
+    """A wait on an mbarrier that nothing arrives at gives up after its poll limit and reports
+    HE_ETIMEOUT through the device status word (no fault, no hang); afterwards the same context
+    still runs a tensor-core layer to the oracle's words."""
+    import time
+
+    t0 = time.time()
+    assert H.he_selftest_bounded_wait() == H.HE_ETIMEOUT
+    assert time.time() - t0 < 30
+    small.layer(SMALL[0], mac_impl=2)

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -1040,6 +1041,12 @@ struct StageTimer {
     }
 };
 
+// NVTX range for profilers' timelines (plan, forward, batch); free when no tool is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 void check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) fail(HE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -1426,6 +1433,7 @@ struct he_plan {
 // uniform residues made on the device (same sizes and kernels, no secret).
 static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys* gk, const he_conv_desc* d,
                                            const int32_t* weights, const he_tune* tune, bool host_only = false) {
+    NvtxRange r("he_conv_plan");
     auto P = std::make_unique<he_plan>();
     P->p = p;
     P->d = *d;
@@ -1620,6 +1628,7 @@ static void check_device(int device) {
 }
 
 static void forward_impl(const he_plan* P, const u64* d_in, u64* d_out, void* ws, cudaStream_t s, bool timed = true) {
+    NvtxRange r("he_conv_forward");
     check_ptrs(d_in, d_out, ws);
     check_device(P->device);
     std::vector<StageLayer> ls{P->stage_layer(d_in, d_out, (char*)ws)};
@@ -1760,6 +1769,7 @@ struct he_batch {
         return ls;
     }
     void run(const uint64_t* const* d_in, uint64_t* const* d_out, char* ws, cudaStream_t s, bool timed) const {
+        NvtxRange r("he_batch");
         for (const auto& w : waves) run_layers(p, plans[0]->kp, layers(w, d_in, d_out, ws), s, timed);
     }
 };

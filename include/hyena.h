@@ -202,8 +202,8 @@ int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_
 int he_conv_status(const he_plan* plan);
 /* *mac_impl = 1 (CUDA-core MAC), 2 (tensor-core MAC) or 3 (eager) for this plan.  The
  * tensor-core form (fp16 10-bit chunks, fp32 sums of at most 2048 terms per
- * accumulation) is chosen automatically when it is exact: no depthwise and
- * |s| <= 16. */
+ * accumulation) is chosen automatically when it is exact: no depthwise,
+ * |s| <= 16 and every limb below 2^50 (five chunks). */
 int he_conv_info(const he_plan* plan, int* mac_impl);
 /* Failure-detection self-test (no paper counterpart).  One CTA waits, through
  * the bounded mbarrier wait every role of the tensor-core MAC uses, on a

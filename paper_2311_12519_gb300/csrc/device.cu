@@ -1507,8 +1507,12 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     int max_abs_s = 0;
     for (int16_t v : sc) max_abs_s = std::max(max_abs_s, std::abs((int)v));
     const u32 impl = tune ? tune->mac_impl : 0;
-    const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX;
-    if (impl == 2 && !tc_ok) fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16 and a non-depthwise layer");
+    // five 10-bit chunks carry a residue only while every limb is below 2^50
+    bool limbs_fit = true;
+    for (u64 qi : p->q) limbs_fit = limbs_fit && qi < (1ull << (10 * TC_CHUNKS));
+    const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && limbs_fit;
+    if (impl == 2 && !tc_ok)
+        fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
     if (impl > 3) fail(HE_EINVAL, "mac_impl must be 0..3");
     P->eager = impl == 3;

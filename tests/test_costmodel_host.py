@@ -117,3 +117,13 @@ def test_conv_check_matches_the_plan_rules_on_the_host():
     assert H.he_conv_check(p, H.conv_desc(64, 16, 7, 7), np.full((16, 64, 3, 3), 16000, dtype=np.int32)) == \
         H.HE_ENOISE
     H.he_params_destroy(p)
+
+
+def test_tensor_core_needs_limbs_below_2_to_the_50():
+    w = np.full((16, 16, 3, 3), 8, dtype=np.int32)
+    d = H.conv_desc(16, 16, 16, 16)
+    for bits, L, wb, ok in ((50, 2, 25, True), (54, 2, 27, False), (30, 4, 15, True)):
+        p = H.he_params_create(4096, L, limb_bits=bits, decomp_bits=wb)
+        assert (H.he_conv_check(p, d, w, mac_impl=2) == H.HE_OK) == ok, bits
+        assert H.he_conv_check(p, d, w, mac_impl=1) == H.HE_OK
+        H.he_params_destroy(p)

@@ -49,11 +49,11 @@ def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0, mac_impl=0):
 
 
 class Setup:
-    def __init__(self, N, L, w):
+    def __init__(self, N, L, w, limb_bits=50):
         self.N, self.L, self.w = N, L, w
-        self.p = H.he_params_create(N, L, decomp_bits=w)
+        self.p = H.he_params_create(N, L, limb_bits=limb_bits, decomp_bits=w)
         self.info = H.he_params_info(self.p)
-        self.P = prm.make_params(N=N, L=L, w=w)
+        self.P = prm.make_params(N=N, L=L, w=w, limb_bits=limb_bits)
         self.sk = H.he_keygen(self.p, synth.SEED_KEYS)
         self.s = bfv.keygen(self.P, synth.SEED_KEYS)
         self._ksk = {}
@@ -392,3 +392,16 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(small):
     assert H.he_selftest_bounded_wait() == H.HE_ETIMEOUT
     assert time.time() - t0 < 30
     small.layer(SMALL[0], mac_impl=2)
+
+
+# ---------------------------------------------------------------- limb widths and digit counts
+@pytest.mark.parametrize("limb_bits,L,w", [(54, 2, 27), (30, 3, 15), (40, 4, 13)])
+def test_other_limb_widths_and_digit_counts(limb_bits, L, w):
+    """Limbs of 54 bits (the widest the key switch's 25-bit split allows; the tensor core needs
+    limbs below 2^50, so the CUDA-core MAC runs), 30 bits (two digits per limb) and 40 bits with
+    4 digits per limb (L l = 16, the largest key-switch template)."""
+    S = Setup(1024, L, w, limb_bits)
+    assert S.info.l * L <= 16 and max(S.info.q[:L]).bit_length() == limb_bits
+    spec = dict(C_in=4, C_out=6, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=2)
+    S.layer(spec)
+    S.layer(dict(spec, c_n=1))

@@ -32,8 +32,8 @@ namespace {
 
 // ------------------------------------------------------------------ constants
 struct LimbC {
-    u64 q, mu;     // Barrett constant for x < 2^(s+63)
-    u32 sm1, pad;  // s - 1
+    u64 q, mu;       // Barrett constant for x < 2^(s+63)
+    u32 sm1, delta;  // s - 1; delta = 2^50 - q if that is below 2^22 (else 0)
     u64 ninv, ninv_sh;
 };
 struct KP {
@@ -385,6 +385,29 @@ __device__ __forceinline__ u64 bred_split50(u64 lo, u64 mid, u64 hi, const LimbC
     return r;
 }
 
+// The same sum x = hi 2^50 + mid 2^25 + lo modulo q = 2^50 - delta (0 < delta < 2^22), without a
+// 64x64-bit product: 2^50 = delta (mod q), so the part of x above bit 50 folds down as a multiple of
+// delta, twice, with 32x32-bit products.  lo < 2^55, mid < 2^56, hi < 2^55 (at most 16 digit terms).
+//   x = A 2^50 + B                 A = hi + mid / 2^25 + carry < 2^55,  B < 2^50
+//     = A delta + B = C 2^50 + D   (A delta split at bit 32, the high product folded again)
+//     = C delta + D = z  < 1.5 2^50 < 2q
+__device__ __forceinline__ u64 fold_reduce50(u64 lo, u64 mid, u64 hi, const LimbC& m) {
+    const u64 M50 = (1ull << 50) - 1;
+    u64 A = hi + (mid >> 25);
+    u64 B = ((mid & 0x1FFFFFFull) << 25) + lo;
+    A += B >> 50;
+    B &= M50;
+    const u32 d = m.delta;
+    const u64 P0 = (u64)(u32)A * d;          // < 2^54
+    const u64 P1 = (u64)(u32)(A >> 32) * d;  // < 2^45
+    u64 C = P1 >> 18;
+    u64 D = ((P1 & 0x3FFFFull) << 32) + P0 + B;
+    C += D >> 50;
+    D &= M50;
+    const u64 z = (u64)(u32)C * d + D;
+    return z >= m.q ? z - m.q : z;
+}
+
 // acc += a * b with one unsigned 32x32 -> 64-bit multiply-add
 __device__ __forceinline__ void mad_wide_u(u64& acc, u32 a, u32 b) {
     asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
@@ -449,7 +472,14 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             mid1 -= lo1 + hi1;
             u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
             lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];  // + sigma(c0); lo stays below 2^57
-            const u64 r0 = bred_split50(lo0, mid0, hi0, m), r1 = bred_split50(lo1, mid1, hi1, m);
+            u64 r0, r1;
+            if (m.delta) {
+                r0 = fold_reduce50(lo0, mid0, hi0, m);
+                r1 = fold_reduce50(lo1, mid1, hi1, m);
+            } else {
+                r0 = bred_split50(lo0, mid0, hi0, m);
+                r1 = bred_split50(lo1, mid1, hi1, m);
+            }
             // R streams out once and is read once by the MAC: evict-first keeps D and the keys in L2
             __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), r0);
             __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)(L + k) * N + x), r1);
@@ -1063,6 +1093,8 @@ KP make_kp(const he_params* p) {
         kp.limb[k].q = p->q[k];
         kp.limb[k].mu = p->mod[k].mu;
         kp.limb[k].sm1 = p->mod[k].sm1;
+        const u64 d50 = (1ull << 50) - p->q[k];
+        kp.limb[k].delta = (p->q[k] < (1ull << 50) && d50 < (1ull << 22)) ? (u32)d50 : 0u;
         kp.limb[k].ninv = p->ntt[k].ninv;
         kp.limb[k].ninv_sh = p->ntt[k].ninv_sh;
     }

@@ -49,7 +49,7 @@ L2_BYTES = 129 * 2**20
 # DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source with this digest prefix
 # (kernel_source_digest); reported as roofline traffic only while the kernels are unchanged
-PROFILED_TRAFFIC = {"source": "f0a6c5f7b884e72b", "k_keyswitch": 2.714e9, "k_mac_tc": 2.359e9, "k_ntt_inputs": 0.380e9,
+PROFILED_TRAFFIC = {"source": "422e55e9eeffa8a8", "k_keyswitch": 2.715e9, "k_mac_tc": 2.358e9, "k_ntt_inputs": 0.381e9,
                     "k_intt": 0.223e9}
 
 

@@ -287,8 +287,12 @@ int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* co
                           void* stream);
 /* The batch end to end from host memory: copies every layer's input
  * ciphertexts h_in[i] (pinned host memory for asynchronous copies) to d_in[i],
- * replays the batch's graph, copies every output d_out[i] to h_out[i], and
- * synchronises the stream (non-default).  Outputs equal he_batch_forward's. */
+ * runs the batch, copies every output d_out[i] to h_out[i], and synchronises
+ * the stream (non-default).  A batch of one wave runs as two halves of about
+ * equal input size on `stream` and on a second stream the batch owns, each
+ * half its own graph, so that one half's copies overlap the other's kernels;
+ * a batch of several waves runs in order on `stream`.  Outputs equal
+ * he_batch_forward's. */
 int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, uint64_t* const* h_out, uint64_t* const* d_in,
                           uint64_t* const* d_out, void* d_workspace, void* stream);
 void he_batch_destroy(he_batch* b);

@@ -1795,8 +1795,17 @@ struct he_batch {
     std::vector<const void*> g_in, g_out;
     const void* g_ws = nullptr;
     cudaStream_t g_stream = nullptr;
+    // end-to-end form: two halves of a one-wave batch on two streams, so that the copies of one
+    // half overlap the kernels of the other (see he_batch_forward_host)
+    std::unique_ptr<he_batch> half[2];
+    std::vector<u32> half_idx[2];
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~he_batch() {
         if (exec) cudaGraphExecDestroy(exec);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (s2) cudaStreamDestroy(s2);
     }
     std::vector<StageLayer> layers(const std::vector<u32>& wave, const uint64_t* const* d_in, uint64_t* const* d_out,
                                    char* ws) const {
@@ -1916,6 +1925,40 @@ extern "C" int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, u
     });
 }
 
+// Splits a one-wave batch into two halves of about equal input size (layers keep their workspace
+// offsets, so the halves can run at the same time), each with its own graph.
+static void make_halves(he_batch* b) {
+    const size_t ctw = 2ull * b->p->L * b->p->N;
+    size_t total = 0, acc = 0;
+    for (auto* pl : b->plans) total += pl->lay.n_ct_in * ctw;
+    for (u32 i = 0; i < b->plans.size(); i++) {
+        const int h = (acc * 2 < total) ? 0 : 1;
+        b->half_idx[h].push_back(i);
+        acc += b->plans[i]->lay.n_ct_in * ctw;
+    }
+    if (b->half_idx[1].empty()) {  // one layer holds most of the input: it alone is the second half
+        b->half_idx[1].push_back(b->half_idx[0].back());
+        b->half_idx[0].pop_back();
+    }
+    for (int h = 0; h < 2; h++) {
+        auto c = std::make_unique<he_batch>();
+        c->p = b->p;
+        c->device = b->device;
+        c->waves.emplace_back();
+        for (u32 j = 0; j < b->half_idx[h].size(); j++) {
+            const u32 i = b->half_idx[h][j];
+            c->plans.push_back(b->plans[i]);
+            c->ws_off.push_back(b->ws_off[i]);
+            c->waves[0].push_back(j);
+        }
+        c->ws_bytes = b->ws_bytes;
+        b->half[h] = std::move(c);
+    }
+    CUDA_OK(cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking));
+    CUDA_OK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    CUDA_OK(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+}
+
 extern "C" int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, uint64_t* const* h_out,
                                      uint64_t* const* d_in, uint64_t* const* d_out, void* d_ws, void* stream) {
     return guard([&] {
@@ -1923,13 +1966,39 @@ extern "C" int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, u
             fail(HE_EINVAL, "null argument (host and device buffers of every layer, a non-default stream)");
         cudaStream_t s = (cudaStream_t)stream;
         const size_t ctw = 2ull * b->p->L * b->p->N;
-        for (size_t i = 0; i < b->plans.size(); i++) {
-            if (!h_in[i] || !h_out[i]) fail(HE_EINVAL, "null host buffer");
-            CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice, s));
-        }
-        batch_graph_launch(b, d_in, d_out, d_ws, s);
         for (size_t i = 0; i < b->plans.size(); i++)
-            CUDA_OK(cudaMemcpyAsync(h_out[i], d_out[i], b->plans[i]->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, s));
+            if (!h_in[i] || !h_out[i]) fail(HE_EINVAL, "null host buffer");
+        check_device(b->device);
+        if (b->waves.size() != 1 || b->plans.size() < 2) {
+            // several waves share one workspace region: one stream, in order
+            for (size_t i = 0; i < b->plans.size(); i++)
+                CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice, s));
+            batch_graph_launch(b, d_in, d_out, d_ws, s);
+            for (size_t i = 0; i < b->plans.size(); i++)
+                CUDA_OK(cudaMemcpyAsync(h_out[i], d_out[i], b->plans[i]->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, s));
+            CUDA_OK(cudaStreamSynchronize(s));
+            return;
+        }
+        if (!b->half[0]) make_halves(b);
+        // the second stream starts after the caller's earlier work on s
+        CUDA_OK(cudaEventRecord(b->ev_fork, s));
+        CUDA_OK(cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
+        for (int h = 0; h < 2; h++) {
+            cudaStream_t sh = h ? b->s2 : s;
+            const auto& idx = b->half_idx[h];
+            std::vector<const uint64_t*> di;
+            std::vector<uint64_t*> dout;
+            for (u32 i : idx) {
+                CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice, sh));
+                di.push_back(d_in[i]);
+                dout.push_back(d_out[i]);
+            }
+            batch_graph_launch(b->half[h].get(), di.data(), dout.data(), d_ws, sh);
+            for (u32 i : idx)
+                CUDA_OK(cudaMemcpyAsync(h_out[i], d_out[i], b->plans[i]->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, sh));
+        }
+        CUDA_OK(cudaEventRecord(b->ev_join, b->s2));
+        CUDA_OK(cudaStreamWaitEvent(s, b->ev_join, 0));
         CUDA_OK(cudaStreamSynchronize(s));
     });
 }

@@ -336,6 +336,18 @@ def test_batch_equals_single_layers(small):
                             [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(), s.cuda_stream)
     for i in range(len(plans)):
         assert torch.equal(h_outs[i], refs[i].cpu()), f"layer {i} differs through the host path"
+    # the same through a batch of one layer per wave (the in-order host path)
+    b1 = H.he_batch_create_limited(plans, 1)
+    assert H.he_batch_waves(b1) == len(plans)
+    ws1 = torch.empty(H.he_batch_workspace_bytes(b1) // 8 + 1, dtype=torch.int64, device="cuda")
+    for t in h_outs:
+        t.fill_(-1)
+    H.he_batch_forward_host(b1, [t.data_ptr() for t in h_ins], [t.data_ptr() for t in h_outs],
+                            [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws1.data_ptr(),
+                            s.cuda_stream)
+    for i in range(len(plans)):
+        assert torch.equal(h_outs[i], refs[i].cpu()), f"layer {i} differs through the host path in waves"
+    H.he_batch_destroy(b1)
     H.he_batch_destroy(b)
     for plan, gk, _ in items:
         H.he_conv_status(plan)

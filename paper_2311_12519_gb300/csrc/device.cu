@@ -6,10 +6,13 @@
 //                     input ciphertext (the "decompose once" half of hoisting)
 //   2. k_keyswitch    per rotation: NTT-domain automorphism (an index
 //                     permutation) of c0 and the digits, key inner product
-//                     with one 128-bit lazy sum and one reduction
-//   3. k_mac          lazy CMult/HAdd over input channels, taps and diagonals
-//                     with 64-bit split accumulators; one reduction per sum;
-//                     epilogue k*A0 + A1 * NTT(P_k) (the [k,-k] PMult)
+//                     with lazy split sums and one reduction per sum
+//   3. k_mac_tc       lazy CMult/HAdd over input channels, taps and diagonals
+//                     on the tensor cores (exact fp16 chunks, fp32 sums), or
+//      k_mac          on CUDA cores with 64-bit split accumulators (depthwise
+//                     layers, |s| > 16, limbs of 2^50 or more); one reduction
+//                     per sum; epilogue k*A0 + A1 * NTT(P_k) (the [k,-k] PMult).
+//                     k_mac_eager is the conventional eager form, for ablations.
 //   4. k_intt         inverse NTT to coefficient form
 // Every stage kernel takes a table of layers, so one launch per stage runs a
 // whole batch of layers (he_batch_*); a single layer is a table of one.

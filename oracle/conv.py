@@ -4,7 +4,7 @@ packing) with the rotations of Sec. 2.3 hoisted.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Readings of the paper (also listed in the design doc):
+Readings of the paper:
   * Layout (Sec. 2.4 pads the input; Sec. 3.1 packs c_n channels per
     ciphertext).  A slot row (N/2 slots) holds whole zero-padded halo
     tiles ("blocks") of (T_h + 2P) x (T_w + 2P) slots, row-major with width

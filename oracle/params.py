@@ -10,7 +10,7 @@ The procedure (Sec. 3.2.1, "Optimal Parameter Selection"):
   3. pick the integer k minimising k*h_{p,n} (mod p), because PMult with the
      [k, -k] plaintext grows the noise by 2|[k h]_p| instead of 2h.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * p is the largest prime below 2^bits with p = 1 (mod 2n) unless given;
   * each RNS limb q_i is one of the largest primes below 2^limb_bits with
     q_i = 1 (mod 2n), in descending order;

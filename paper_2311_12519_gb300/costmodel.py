@@ -8,7 +8,7 @@ Sec. 3.2.1 (N by input size, Sec. 4.1); here the noise estimate only decides
 which configurations are admissible, and time decides between them:
 
   * autotune(): the exhaustive search, timing every admissible configuration
-    of a layer on the GPU through he_conv_time (the fallback and the judge);
+    of a layer on the GPU through he_conv_time (the fallback, and the yardstick the model is scored against);
   * CostModel: the perceptron of hyena_costmodel.h, trained on kernel
     latencies (four stages per timed layer) of random layers, which ranks the
     same configurations without running them.

@@ -3,7 +3,7 @@
  * packing, tile shape, MAC schedule).  It has no counterpart in the paper,
  * which fixes its parameters by the noise analysis of Sec. 3.2.1; the model
  * ranks the configurations that analysis allows by predicted time, and
- * exhaustive timing (he_conv_time in hyena.h) is its fallback and judge.
+ * exhaustive timing (he_conv_time in hyena.h) is its fallback and its yardstick.
  *
  * Network: F features -> 64 -> 64 -> 1, ReLU after the two hidden layers,
  * fp32.  Features and target are standardised with the mean and standard

@@ -261,7 +261,11 @@ int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in, uint64_t*
  * each stage (input NTT, key switch, channel MAC, output NTT) of all its
  * layers in one launch, so small layers fill the GPU; outputs are identical
  * to he_conv_forward of every plan.  All plans must share one he_params and
- * one device.  The batch keeps pointers to the plans, which must outlive it. */
+ * one device.  The batch keeps pointers to the plans, which must outlive it.
+ * A batch caches its CUDA graphs (and, for he_batch_forward_host, a second
+ * stream): calls on one batch object must not run concurrently from several
+ * host threads.  Plans are read-only after he_conv_plan and may be used by
+ * concurrent forwards on different streams with separate workspaces. */
 typedef struct he_batch he_batch;
 int he_batch_create(const he_plan* const* plans, int n, he_batch** out);
 /* The same, with the layers split into waves whose workspaces together fit

@@ -157,3 +157,23 @@ def test_tile_override_rejected_like_the_oracle(tile, why):
     with pytest.raises(ValueError):
         conv.Layout(N=N, **spec)
     H.he_params_destroy(p)
+
+
+@pytest.mark.parametrize("desc,why", [
+    (dict(C_in=2048, C_out=4, H=8, W=8), "more than 16384 accumulation terms"),
+    (dict(C_in=4, C_out=6, H=8, W=8, depthwise=True), "depthwise with C_in != C_out"),
+    (dict(C_in=4, C_out=4, H=8, W=8, stride=3), "stride 3"),
+    (dict(C_in=4, C_out=4, H=8, W=8, c_n=3), "c_n = 3"),
+    (dict(C_in=4, C_out=4, H=8, W=8, kh=9), "kernel 9"),
+    (dict(C_in=0, C_out=4, H=8, W=8), "no input channels"),
+    (dict(C_in=4, C_out=4, H=0, W=8), "empty image"),
+])
+def test_plan_checks_refuse_invalid_layers(desc, why):
+    """The plan's host checks (he_conv_check: no device needed) refuse malformed layers."""
+    p = H.he_params_create(1024, 2, decomp_bits=25)
+    d = H.conv_desc(**desc)
+    cw = 1 if desc.get("depthwise") else max(1, desc["C_in"])
+    kh = desc.get("kh", 3)
+    w = np.ones((max(1, desc["C_out"]), cw, kh, kh), dtype=np.int32)
+    assert H.he_conv_check(p, d, w) == H.HE_EINVAL, why
+    H.he_params_destroy(p)

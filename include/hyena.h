@@ -294,8 +294,10 @@ int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* co
  * runs the batch, copies every output d_out[i] to h_out[i], and synchronises
  * the stream (non-default).  A batch of one wave runs as two halves of about
  * equal input size on `stream` and on a second stream the batch owns, each
- * half its own graph, so that one half's copies overlap the other's kernels;
- * a batch of several waves runs in order on `stream`.  Outputs equal
+ * half its own graph, so that one half's copies overlap the other's kernels.
+ * A batch of several waves runs its waves in order on `stream`, while the
+ * inputs stream in ahead of them and a finished wave's outputs stream out
+ * during the next wave, on two more streams the batch owns.  Outputs equal
  * he_batch_forward's. */
 int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, uint64_t* const* h_out, uint64_t* const* d_in,
                           uint64_t* const* d_out, void* d_workspace, void* stream);

@@ -1802,13 +1802,17 @@ struct he_batch {
     // half overlap the kernels of the other (see he_batch_forward_host)
     std::unique_ptr<he_batch> half[2];
     std::vector<u32> half_idx[2];
-    cudaStream_t s2 = nullptr;
+    cudaStream_t s2 = nullptr, s3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_done;  // per wave: inputs copied, kernels done
     ~he_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        for (auto e : ev_in) cudaEventDestroy(e);
+        for (auto e : ev_done) cudaEventDestroy(e);
         if (s2) cudaStreamDestroy(s2);
+        if (s3) cudaStreamDestroy(s3);
     }
     std::vector<StageLayer> layers(const std::vector<u32>& wave, const uint64_t* const* d_in, uint64_t* const* d_out,
                                    char* ws) const {
@@ -1972,13 +1976,51 @@ extern "C" int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, u
         for (size_t i = 0; i < b->plans.size(); i++)
             if (!h_in[i] || !h_out[i]) fail(HE_EINVAL, "null host buffer");
         check_device(b->device);
-        if (b->waves.size() != 1 || b->plans.size() < 2) {
-            // several waves share one workspace region: one stream, in order
-            for (size_t i = 0; i < b->plans.size(); i++)
-                CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice, s));
+        if (b->plans.size() < 2) {
+            CUDA_OK(cudaMemcpyAsync(d_in[0], h_in[0], b->plans[0]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice, s));
             batch_graph_launch(b, d_in, d_out, d_ws, s);
-            for (size_t i = 0; i < b->plans.size(); i++)
-                CUDA_OK(cudaMemcpyAsync(h_out[i], d_out[i], b->plans[i]->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, s));
+            CUDA_OK(cudaMemcpyAsync(h_out[0], d_out[0], b->plans[0]->lay.n_ct_out * ctw * 8, cudaMemcpyDeviceToHost, s));
+            CUDA_OK(cudaStreamSynchronize(s));
+            return;
+        }
+        if (b->waves.size() > 1) {
+            // waves run one after another on s (they share the workspace region); the inputs of
+            // every wave stream in on s2 ahead of its kernels, the outputs of a finished wave leave
+            // on s3 while the next wave computes
+            const size_t nw = b->waves.size();
+            if (!b->s2) {
+                CUDA_OK(cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking));
+                CUDA_OK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+                CUDA_OK(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+            }
+            if (!b->s3) CUDA_OK(cudaStreamCreateWithFlags(&b->s3, cudaStreamNonBlocking));
+            while (b->ev_in.size() < nw) {
+                cudaEvent_t a, c;
+                CUDA_OK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+                b->ev_in.push_back(a);
+                CUDA_OK(cudaEventCreateWithFlags(&c, cudaEventDisableTiming));
+                b->ev_done.push_back(c);
+            }
+            CUDA_OK(cudaEventRecord(b->ev_fork, s));
+            CUDA_OK(cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
+            CUDA_OK(cudaStreamWaitEvent(b->s3, b->ev_fork, 0));
+            for (size_t w = 0; w < nw; w++) {
+                for (u32 i : b->waves[w])
+                    CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice,
+                                            b->s2));
+                CUDA_OK(cudaEventRecord(b->ev_in[w], b->s2));
+            }
+            for (size_t w = 0; w < nw; w++) {
+                CUDA_OK(cudaStreamWaitEvent(s, b->ev_in[w], 0));
+                run_layers(b->p, b->plans[0]->kp, b->layers(b->waves[w], d_in, d_out, (char*)d_ws), s, true);
+                CUDA_OK(cudaEventRecord(b->ev_done[w], s));
+                CUDA_OK(cudaStreamWaitEvent(b->s3, b->ev_done[w], 0));
+                for (u32 i : b->waves[w])
+                    CUDA_OK(cudaMemcpyAsync(h_out[i], d_out[i], b->plans[i]->lay.n_ct_out * ctw * 8,
+                                            cudaMemcpyDeviceToHost, b->s3));
+            }
+            CUDA_OK(cudaEventRecord(b->ev_join, b->s3));
+            CUDA_OK(cudaStreamWaitEvent(s, b->ev_join, 0));
             CUDA_OK(cudaStreamSynchronize(s));
             return;
         }

@@ -274,15 +274,14 @@ struct LayerDev {
     u32 n_ct_in, n_ct_out, n_rot, rot_id, n_ks, K, Kpad, in_groups, out_groups, row_units, tc_rows, tc_rows_per_cta;
     u32 tmem_cols;             // TMEM columns of a tensor-core MAC CTA (power of two >= 5 rows)
     u32 r_slots, r_id;         // rotated copies stored per input ciphertext in R, and the identity's slot
-    unsigned char* a16;        // tensor-core MAC operand tiles converted once (layers of several row tiles), or null
 };
 
-enum { ST_NTT = 0, ST_KS = 1, ST_MAC = 2, ST_INTT = 3, ST_CHUNK = 4 };
+enum { ST_NTT = 0, ST_KS = 1, ST_MAC = 2, ST_INTT = 3 };
 
 template <int MAXB>
 struct Batch {
     u32 n;
-    u32 start[5][MAXB + 1];
+    u32 start[4][MAXB + 1];
     LayerDev L[MAXB];
 };
 
@@ -787,58 +786,6 @@ __device__ __forceinline__ bool tc_item(const Batch<MAXB>& B, u32 item, u32 N, u
     return true;
 }
 
-// Layers with more than one row tile: the rotated copies of every (row unit, polynomial, limb,
-// slot tile, K tile) converted once into the exact shared-memory image the MMA reads (five 8 KB
-// chunk planes, K-major canonical layout), 40 KB per tile at
-//   a16 + ((z nt_n + nt) ktiles + t) 40 KB,   z = (ru 2 + p) L + k,
-// so that the tensor-core MAC of every row tile copies it instead of converting it again.
-// Block = one tile; a thread converts (slot, octet) pieces as the MAC's converter warps do.
-constexpr int TC_CHUNK_THREADS = 256;
-template <int MAXB>
-__global__ void __launch_bounds__(TC_CHUNK_THREADS) k_tc_chunks(const __grid_constant__ Batch<MAXB> B, KP kp) {
-    const u32 li = find_layer(B, ST_CHUNK, blockIdx.x);
-    const LayerDev& Ly = B.L[li];
-    const u32 N = kp.N, L = kp.L, nt_n = N / TC_MTILE, ktiles = Ly.Kpad / TC_KTILE;
-    const u32 tile = blockIdx.x - B.start[ST_CHUNK][li];
-    const u32 t = tile % ktiles, nt = (tile / ktiles) % nt_n, z = tile / (ktiles * nt_n);
-    const u32 k = z % L, p = (z / L) & 1, ru = z / (2 * L);
-    const size_t ctw = 2ull * L * N;
-    const u32 row0 = ru * Ly.in_groups * Ly.n_rot + t * TC_KTILE, kk0 = t * TC_KTILE;
-    const u64* base = Ly.R + (size_t)(p * L + k) * N + (size_t)nt * TC_MTILE;
-    unsigned char* A = Ly.a16 + (size_t)tile * TC_A_BYTES;
-    for (u32 i = threadIdx.x; i < TC_MTILE * (TC_KTILE / 8); i += TC_CHUNK_THREADS) {
-        const u32 nl = i & (TC_MTILE - 1), o = i >> 7;
-        u64 v[8];
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const u32 r = o * 8 + e;
-            v[e] = (kk0 + r < Ly.K) ? __ldg(base + (size_t)(row0 + r) * ctw + nl) : 0;
-        }
-        u32 cw8[TC_CHUNKS][8];
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const u32 lo = (u32)v[e], hi = (u32)(v[e] >> 32);
-            cw8[0][e] = lo;
-            cw8[1][e] = lo >> 10;
-            cw8[2][e] = lo >> 20;
-            cw8[3][e] = __funnelshift_r(lo, hi, 30);
-            cw8[4][e] = hi >> 8;
-        }
-#pragma unroll
-        for (int c = 0; c < TC_CHUNKS; c++) {
-            u32 w[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                const u32 packed = (cw8[c][e] & 0x3FFu) | ((cw8[c][e + 1] << 16) & 0x3FF0000u) | 0x64006400u;
-                __half2 h = *reinterpret_cast<const __half2*>(&packed);
-                h = __hsub2(h, __float2half2_rn(1536.0f));
-                w[e / 2] = *reinterpret_cast<u32*>(&h);
-            }
-            *reinterpret_cast<uint4*>(A + c * TC_A_CHUNK_BYTES + kmajor_off(nl, o * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-    }
-}
-
 // Warp roles: warp 0 issues the copies, warp 1 (lane 0) issues the MMAs, warps 2..15 convert
 // residues to fp16 chunks, warps 4..15 also run the epilogue.  Barriers (all bounded waits):
 //   raw_full[s]   copies of stream position g landed in slot s = g % TC_RAW   (1 arrive + tx)
@@ -847,16 +794,11 @@ __global__ void __launch_bounds__(TC_CHUNK_THREADS) k_tc_chunks(const __grid_con
 //   a_empty[st]   MMAs of stage st done                                          (1, commit)
 //   acc_full      last MMA of a work item done                                   (1, commit)
 //   acc_empty     accumulators read by every epilogue warp                       (TC_EPI)
-// PRE (operand tiles converted by k_tc_chunks): slot s = g % TC_RAW receives the 40 KB operand image
-// and the MMAs read it in place; raw_empty[s] then counts the MMAs' commit alone, and the stage
-// barriers and the converters are idle.
 constexpr int TC_CONV = TC_THREADS / 32 - 2;  // converter warps 2..15
 constexpr int TC_EPI = TC_THREADS / 32 - 4;   // epilogue warps 4..15
 static_assert(TC_THREADS == 512, "warp roles assume 16 warps");
 
-static_assert(TC_RAW * TC_A_BYTES <= TC_BS_OFF, "pre-converted slots must fit below the scalar tiles");
-
-template <bool PACKED, int MAXB, bool PRE>
+template <bool PACKED, int MAXB>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant__ Batch<MAXB> B, KP kp, u32 tmem_cols) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
@@ -869,8 +811,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + TC_BAR_OFF + 12 * 8 + 4);
 
     if (tid == 0) {
-        constexpr u32 RE = PRE ? 1 : TC_CONV + 1;
-        const u32 counts[12] = {1, 1, 1, RE, RE, RE, TC_CONV, TC_CONV, 1, 1, 1, TC_EPI};
+        const u32 counts[12] = {1, 1, 1, TC_CONV + 1, TC_CONV + 1, TC_CONV + 1, TC_CONV, TC_CONV, 1, 1, 1, TC_EPI};
         for (int i = 0; i < 12; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(counts[i]));
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -904,25 +845,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                 if (!__all_sync(0xffffffffu, fr)) break;
                 if (lane == 0) {
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)),
-                                 "r"((PRE ? TC_A_BYTES : TC_RAW_BYTES) + bbytes)
+                                 "r"(TC_RAW_BYTES + bbytes)
                                  : "memory");
-                    if (PRE) {
-                        const size_t zi = ((size_t)it.ru * 2 + it.p) * L + it.k;
-                        const size_t tile = (zi * (N / TC_MTILE) + it.n0 / TC_MTILE) * ktiles + t;
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                smem_u32(tsm + s * TC_A_BYTES)),
-                            "l"(Ly.a16 + tile * TC_A_BYTES), "r"(TC_A_BYTES), "r"(bar(s))
-                            : "memory");
-                    } else {
-                        const int x = (int)it.n0, y = (int)(it.p * L + it.k);
-                        const int z = (int)(it.ru * Ly.in_groups * Ly.n_rot + t * TC_KTILE);
-                        asm volatile(
-                            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-                                "r"(smem_u32(tsm + TC_RAW_OFF + s * TC_RAW_BYTES)),
-                            "l"(reinterpret_cast<u64>(&Ly.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar(s))
-                            : "memory");
-                    }
+                    const int x = (int)it.n0, y = (int)(it.p * L + it.k);
+                    const int z = (int)(it.ru * Ly.in_groups * Ly.n_rot + t * TC_KTILE);
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+                            "r"(smem_u32(tsm + TC_RAW_OFF + s * TC_RAW_BYTES)),
+                        "l"(reinterpret_cast<u64>(&Ly.rmap)), "r"(x), "r"(y), "r"(z), "r"(bar(s))
+                        : "memory");
                     const __half* bsrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (Ly.tc_rows_per_cta * TC_KTILE);
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -948,11 +879,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                         if (unit > 0 && !wait(11, (unit - 1) & 1)) { okk = false; break; }  // accumulators read out
                         asm volatile("tcgen05.fence::after_thread_sync;");
                     }
-                    // operands ready: converted stage st, or (PRE) the copied image in slot s
-                    if (!(PRE ? wait(s, (g / TC_RAW) & 1) : wait(6 + st, (g >> 1) & 1))) { okk = false; break; }
+                    if (!wait(6 + st, (g >> 1) & 1)) { okk = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const u32 a_base = smem_u32(tsm + (PRE ? s * TC_A_BYTES : st * TC_STAGE_BYTES));
-                    const u32 b_base = smem_u32(tsm + TC_BS_OFF + s * TC_B_BYTES);
+                    const u32 a_base = smem_u32(tsm + st * TC_STAGE_BYTES), b_base = smem_u32(tsm + TC_BS_OFF + s * TC_B_BYTES);
 #pragma unroll
                     for (int c = 0; c < TC_CHUNKS; c++) {
 #pragma unroll
@@ -967,8 +896,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                         }
                     }
-                    if (!PRE)
-                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(8 + st)));
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(8 + st)));
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(3 + s)));
                     if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(10)));
@@ -989,7 +917,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
             const u32 K = Ly.K;
             bool okk = true;
             for (u32 t = 0; t < it.n_tiles; t++, g++) {
-              if (!PRE) {
                 const u32 st = g & 1, s = g % TC_RAW, kk0 = t * TC_KTILE;
                 bool w = wait(s, (g / TC_RAW) & 1);                    // raw data landed
                 w = w && (g < 2 || wait(8 + st, ((g >> 1) - 1) & 1));  // stage free
@@ -1038,7 +965,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                     arrive(6 + st);  // stage written
                     arrive(3 + s);   // raw slot read
                 }
-              }
                 if (warp < 4 || (t % TC_SEG_TILES != TC_SEG_TILES - 1 && t + 1 != it.n_tiles)) continue;
                 // epilogue of segment seg: warp w reads TMEM lanes 32 (w % 4) + lane; the three
                 // warps of a sub-partition take every third 8-column block of output rows
@@ -1258,11 +1184,10 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
-    bool tc = false, packed = false, dw = false, eager = false, pre = false;
+    bool tc = false, packed = false, dw = false, eager = false;
     u32 gt = 8;
     bool operator==(const MacVariant& o) const {
-        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && pre == o.pre &&
-               (tc || eager || gt == o.gt);
+        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && (tc || eager || gt == o.gt);
     }
 };
 
@@ -1281,7 +1206,6 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
             if (s.mv.eager) return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + 3) / 4);
             if (s.mv.tc) return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta);
             return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + s.mv.gt - 1) / s.mv.gt);
-        case ST_CHUNK: return s.mv.pre ? d.row_units * 2 * L * (N / TC_MTILE) * (d.Kpad / TC_KTILE) : 0;
         default: return d.n_ct_out * 2 * L;
     }
 }
@@ -1321,16 +1245,12 @@ void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const 
         u32 cols = 32;
         for (u32 i = 0; i < B.n; i++) cols = std::max(cols, B.L[i].tmem_cols);
         const u32 grid = std::min(blocks, (u32)sm_count());
-        auto go = [&](auto kern) {
-            allow_smem(kern, TC_SMEM_BYTES);
-            kern<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp, cols);
-        };
         if (mv.packed) {
-            if (mv.pre) go(k_mac_tc<true, MAXB, true>);
-            else go(k_mac_tc<true, MAXB, false>);
+            allow_smem(k_mac_tc<true, MAXB>, TC_SMEM_BYTES);
+            k_mac_tc<true, MAXB><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp, cols);
         } else {
-            if (mv.pre) go(k_mac_tc<false, MAXB, true>);
-            else go(k_mac_tc<false, MAXB, false>);
+            allow_smem(k_mac_tc<false, MAXB>, TC_SMEM_BYTES);
+            k_mac_tc<false, MAXB><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp, cols);
         }
         return;
     }
@@ -1390,10 +1310,6 @@ void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector
                 launch_mac_b<MAXB>(layers[c0]->mv, total, B, kp, s);
                 check_launch("k_mac");
                 break;
-            case ST_CHUNK:
-                k_tc_chunks<MAXB><<<total, TC_CHUNK_THREADS, 0, s>>>(B, kp);
-                check_launch("k_tc_chunks");
-                break;
             default: {
                 const size_t smem = ntt_smem_bytes(p->N);
                 allow_smem(k_intt<MAXB>, smem);
@@ -1437,7 +1353,6 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
             std::vector<const StageLayer*> grp;
             for (size_t j = i; j < layers.size(); j++)
                 if (!done[j] && layers[j].mv == layers[i].mv) grp.push_back(&layers[j]), done[j] = true;
-            if (layers[i].mv.pre) go(ST_CHUNK, grp);  // operand tiles converted once for all row tiles
             go(ST_MAC, grp);
         }
     }
@@ -1505,7 +1420,6 @@ struct he_plan {
     bool packed = false, dw = false;
     u32 mac_groups = 8;
     bool use_tc = false, eager = false;
-    bool tc_pre = false;  // tensor-core MAC over several row tiles: operands converted once (k_tc_chunks)
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
@@ -1515,7 +1429,7 @@ struct he_plan {
     int* d_bias = nullptr;
     int* d_err = nullptr;
     u32 tmem_cols = 0, r_slots = 0, r_id = 0;
-    size_t off_R = 0, off_D = 0, off_O = 0, off_A16 = 0, ws_bytes = 0;
+    size_t off_R = 0, off_D = 0, off_O = 0, ws_bytes = 0;
     KP kp{};
     ~he_plan() {
         int cur = -1;
@@ -1545,9 +1459,7 @@ struct he_plan {
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
         L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
         if (use_tc) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
-        L.a16 = tc_pre ? (unsigned char*)(ws + off_A16) : nullptr;
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
-        s.mv.pre = tc_pre;
         return s;
     }
 };
@@ -1720,11 +1632,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     P->off_R = 0;
     P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);
     P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
-    P->off_A16 = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
-    // A16 [row unit][polynomial][limb][slot tile][K tile] of 40 KB operand images
-    P->tc_pre = P->use_tc && P->tc_rows > P->tc_rows_per_cta;
-    const size_t a16 = P->tc_pre ? (size_t)lay.row_units * 2 * p->L * (p->N / TC_MTILE) * (P->tc_kpad / TC_KTILE) * TC_A_BYTES : 0;
-    P->ws_bytes = align256(P->off_A16 + a16);
+    P->ws_bytes = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
     (void)taps;
     return P;
 }

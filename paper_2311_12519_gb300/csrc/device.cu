@@ -1507,6 +1507,15 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     const u32 NR = P->packed ? 2 : 1;
     P->K = P->dw ? P->n_rot : lay.in_groups * P->n_rot;
     if (P->K > (1u << 14)) fail(HE_EINVAL, "too many accumulation terms (C_in kh^2 > 16384)");
+    {
+        // every stage of the layer must fit one launch (grid x < 2^31) and 32-bit block indices
+        const u64 L = p->L, Nn = p->N, limit = (1ull << 31) - 1;
+        const u64 ntt = (u64)lay.n_ct_in * (2 * L + L * p->l * L), intt = (u64)lay.n_ct_out * 2 * L;
+        const u64 ks = (u64)rl.size() * L * (Nn / 256);
+        const u64 mac = (u64)lay.row_units * 2 * L * (Nn / 128) * lay.out_groups;  // the largest MAC grid
+        if (ntt > limit || intt > limit || ks > limit || mac > limit)
+            fail(HE_EINVAL, "layer too large for one launch per stage: split its images into several layers");
+    }
     std::vector<int16_t> sc((size_t)lay.out_groups * NR * P->K, 0);
     const u32 wcin = P->dw ? 1 : d->C_in;
     auto W = [&](u32 o, u32 i, u32 tap) -> i64 {

@@ -177,3 +177,25 @@ def test_plan_checks_refuse_invalid_layers(desc, why):
     w = np.ones((max(1, desc["C_out"]), cw, kh, kh), dtype=np.int32)
     assert H.he_conv_check(p, d, w) == H.HE_EINVAL, why
     H.he_params_destroy(p)
+
+
+def test_plan_checks_accept_the_network_stacks_and_refuse_oversized_launches():
+    """Every layer of the three stacks passes the launch-size check; a layer whose stages would
+    not fit one launch each is refused (host only)."""
+    import synth as sy
+
+    for shapes, N, L, images in ((sy.resnet20_convs(), 8192, 3, 1), (sy.vgg16_convs(), 16384, 4, 8),
+                                 (sy.mobilenet_v1_convs(), 8192, 4, 32)):
+        p = H.he_params_create(N, L, decomp_bits=50)
+        for s in shapes:
+            d = H.conv_desc(s.C_in, s.C_out, s.H, s.W, s.k, s.stride, s.depthwise, images, 2)
+            w = np.ones((s.C_out, 1 if s.depthwise else s.C_in, s.k, s.k), dtype=np.int32)
+            assert H.he_conv_check(p, d, w) == H.HE_OK, (s, H.load().he_last_error())
+        H.he_params_destroy(p)
+    # 1024 images of 224x224 with 1024 channels in one 1x1 layer at N = 1024: the MAC grid alone
+    # would need 114688 row units x 2 x 4 limbs x 8 slot tiles x 512 output groups > 2^31 blocks
+    p = H.he_params_create(1024, 4, decomp_bits=50)
+    d = H.conv_desc(1024, 1024, 224, 224, 1, 1, False, 1024, 2)
+    assert H.he_conv_check(p, d, np.ones((1024, 1024, 1, 1), dtype=np.int32)) == H.HE_EINVAL
+    assert "too large" in H.load().he_last_error().decode()
+    H.he_params_destroy(p)

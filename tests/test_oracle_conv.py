@@ -141,3 +141,20 @@ def test_mistake_wrong_rotation_sign(P256, monkeypatch):
     orig = bfv.rotation_element
     lay = conv.Layout(N=256, **LAY)
     assert _fails(P256, lay, monkeypatch, (bfv, "rotation_element"), lambda P, step: orig(P, -step))
+
+
+@pytest.mark.parametrize("case,tile", [
+    ((3, 4, 10, 9, 3, 1, False, 2, 2), (4, 5)),    # ragged tiles in both directions, two images
+    ((4, 6, 12, 13, 3, 2, False, 2, 1), (6, 13)),  # stride-2 strips spanning an odd width, unpacked
+    ((4, 4, 12, 12, 3, 2, True, 1, 2), (4, 6)),    # depthwise, stride 2, stride-aligned tiles
+])
+def test_he_conv_with_chosen_tiles_decrypts_to_conv(P256, case, tile):
+    """Caller-chosen tiles (any size that fits a row, origins on the stride grid) give the same
+    convolution as the default tiles, by the decryption invariant."""
+    C_in, C_out, H, W, k, S, dw, I, cn = case
+    lay = conv.Layout(N=P256.N, C_in=C_in, C_out=C_out, H=H, W=W, kh=k, stride=S, depthwise=dw, n_images=I, c_n=cn,
+                      tile_h=tile[0], tile_w=tile[1])
+    assert (lay.T_h, lay.T_w) == tile
+    got, ref, out, s = _run(P256, lay)
+    assert (got == ref).all()
+    assert max(bfv.noise_of(P256, s, c) for c in out) < P256.delta // 2

@@ -249,7 +249,11 @@ void he_plan_destroy(he_plan* plan);
  * call's contents (every word a kernel reads is written earlier in the same
  * call, so nothing needs clearing); calls whose work overlaps on the GPU --
  * on different streams, or from different threads -- race on it.  The
- * caller still owns d_in and d_out; per-stage event timing is not recorded. */
+ * caller still owns d_in and d_out; per-stage event timing is not recorded.
+ * The plan's device must be current; a call refused for a wrong device or a
+ * misaligned pointer touches no device.  The looked-up address is kept per
+ * device ordinal for the life of the process, so a cudaDeviceReset after the
+ * first call on a device is not supported (the cached address would be stale). */
 int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in, uint64_t* d_out, void* stream);
 
 /* ------------------------------------------------------------------ */

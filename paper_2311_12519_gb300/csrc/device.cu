@@ -707,7 +707,7 @@ __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_gene
 
 // Waits for phase `parity` of the mbarrier at shared address bar, for at most `limit` polls.
 // Gives up at once when *abort_flag is set (another role gave up) and, when the limit runs out,
-// sets *abort_flag and *err so that every role leaves and the host sees the failure.
+// sets *abort_flag (so that every role leaves) and, if err is not null, *err.
 __device__ __forceinline__ bool mbar_wait_bounded(u32 bar, u32 parity, long long limit, volatile int* abort_flag,
                                                   int* err) {
     for (long long it = 0; it < limit; it++) {
@@ -721,7 +721,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(u32 bar, u32 parity, long long
         if (ok) return true;
     }
     *abort_flag = 1;
-    atomicExch(err, 1);
+    if (err) atomicExch(err, 1);
     return false;
 }
 
@@ -825,10 +825,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const u32 tmem = *tmem_slot;
-    int* err = B.L[0].err;
 
-    // bounded wait that gives up at once when another role has given up
-    auto wait = [&](int i, u32 parity) -> bool { return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, err); };
+    // bounded wait that gives up at once when another role has given up; an abort leaves the
+    // CTA's remaining items of every layer of the table unfinished, so the drain below marks the
+    // status word of every layer
+    auto wait = [&](int i, u32 parity) -> bool {
+        return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, nullptr);
+    };
     auto arrive = [&](int i) { asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(i)) : "memory"); };
 
     if (warp == 0) {
@@ -1020,8 +1023,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     }
     // drain: every copy that was issued is waited for by the converters in the normal path; after an
     // abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
-    if (*abort_flag && tid == 0)
+    if (*abort_flag && tid == 0) {
+        for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
         for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
@@ -2092,6 +2097,10 @@ extern "C" int he_conv_forward_noalloc(const he_plan* plan, const uint64_t* d_in
         if (plan->ws_bytes > (size_t)HE_NOALLOC_MAX_SCRATCH_BYTES)
             fail(HE_EINVAL, "layer needs " + std::to_string(plan->ws_bytes) + " bytes of scratch; the static scratch holds " +
                                 std::to_string((size_t)HE_NOALLOC_MAX_SCRATCH_BYTES) + " (use he_conv_forward)");
+        // a call that will be refused touches no device: the plan's device and the caller's
+        // pointers are checked before the scratch address is looked up
+        check_device(plan->device);
+        check_ptrs(d_in, d_out, nullptr);
         void* ws = noalloc_scratch();
         // every scratch word a kernel reads was written earlier in the same call,
         // so nothing has to be cleared between calls
@@ -2137,10 +2146,19 @@ extern "C" int he_rotate(const he_params* p, const he_galkeys* gk, uint32_t galo
         check_ptrs(d_in, d_out, d_ws);
         cudaStream_t s = (cudaStream_t)stream;
         KP kp = make_kp(p);
+        // device copies of the key and the rotation record, freed on every path out
+        struct Free {
+            void* p = nullptr;
+            ~Free() {
+                if (p) cudaFree(p);
+            }
+        } fkey, frot;
         u64* dkey = upload_keys(p, kp, {key}, s);
+        fkey.p = dkey;
         RotDev rd{galois, 1, 0, 0};
         RotDev* drot = nullptr;
         CUDA_OK(cudaMalloc(&drot, sizeof(RotDev)));
+        frot.p = drot;
         CUDA_OK(cudaMemcpyAsync(drot, &rd, sizeof(RotDev), cudaMemcpyHostToDevice, s));
         size_t offD, total;
         rotate_offsets(p, n_ct, &offD, &total);
@@ -2156,8 +2174,6 @@ extern "C" int he_rotate(const he_params* p, const he_galkeys* gk, uint32_t galo
         L.r_slots = 2, L.r_id = 0;
         run_layers(p, kp, {sl}, s, false, /*do_mac=*/false);
         CUDA_OK(cudaStreamSynchronize(s));
-        cudaFree(dkey);
-        cudaFree(drot);
     });
 }
 

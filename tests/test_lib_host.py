@@ -199,3 +199,10 @@ def test_plan_checks_accept_the_network_stacks_and_refuse_oversized_launches():
     assert H.he_conv_check(p, d, np.ones((1024, 1024, 1, 1), dtype=np.int32)) == H.HE_EINVAL
     assert "too large" in H.load().he_last_error().decode()
     H.he_params_destroy(p)
+
+
+def test_noalloc_scratch_size_matches_the_header():
+    """The binding's copy of the static scratch size is the header's #define."""
+    inc = H._build.os.path.join(H._build.os.path.dirname(H._build.HERE), "include", "hyena.h")
+    m = re.search(r"#define\s+HE_NOALLOC_MAX_SCRATCH_BYTES\s+(\d+)u?", open(inc).read())
+    assert m and int(m.group(1)) == H.HE_NOALLOC_MAX_SCRATCH_BYTES

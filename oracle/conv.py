@@ -22,6 +22,9 @@ Readings of the paper:
 """
 from __future__ import annotations
 
+import os
+import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -184,12 +187,15 @@ def choose_tile(half: int, H: int, W: int, P: int, S: int) -> tuple[int, int]:
     return min(Th, H), Tw
 
 
-def pack_slots(lay: Layout, act: np.ndarray) -> np.ndarray:
-    """Input activations [I][C_in][H][W] -> slot vectors [n_ct_in][N]."""
+def pack_slots(lay: Layout, act: np.ndarray, row_units=None) -> np.ndarray:
+    """Input activations [I][C_in][H][W] -> slot vectors [n_ct_in][N].
+    `row_units` (optional) fills only the ciphertexts of those row-units."""
     N, half, P = lay.N, lay.N // 2, lay.P
     out = np.zeros((lay.n_ct_in, N), dtype=np.int64)
     for unit in range(lay.units):
         ru, u_local = divmod(unit, lay.units_per_ct)
+        if row_units is not None and ru not in row_units:
+            continue
         img, ty, tx = lay.unit_coords(unit)
         for j in range(lay.in_groups):
             ct = ru * lay.in_groups + j
@@ -240,6 +246,35 @@ def unpack_slots(lay: Layout, slots: np.ndarray) -> np.ndarray:
     return out
 
 
+def ct_positions(lay: Layout, c: int) -> list[tuple[int, int, int, int, int]]:
+    """Valid outputs carried by output ciphertext c: (image, channel, y, x, flat slot) tuples,
+    the same placement as unpack_slots, for checking one ciphertext of a large layer."""
+    half, P, S = lay.N // 2, lay.P, lay.stride
+    ru, g = divmod(c, lay.out_groups)
+    res = []
+    for u_local in range(lay.units_per_ct):
+        unit = ru * lay.units_per_ct + u_local
+        if unit >= lay.units:
+            break
+        img, ty, tx = lay.unit_coords(unit)
+        for yl in range(P, P + lay.T_h):
+            Y = ty * lay.T_h + yl - P
+            if Y >= lay.H or Y % S:
+                continue
+            for xl in range(P, P + lay.T_w):
+                X = tx * lay.T_w + xl - P
+                if X >= lay.W or X % S:
+                    continue
+                row, pos = lay.slot_of(u_local, yl, xl)
+                if lay.c_n == 2:
+                    for r in range(2):
+                        if 2 * g + r < lay.C_out:
+                            res.append((img, 2 * g + r, Y // S, X // S, r * half + pos))
+                else:
+                    res.append((img, g, Y // S, X // S, row * half + pos))
+    return res
+
+
 # ---------------------------------------------------------------- keys used
 def rotation_plan(P: Params, lay: Layout):
     """List of (tap index, d, Galois element) for every rotated copy of an
@@ -285,8 +320,15 @@ def output_scale(P: Params, lay: Layout) -> int:
     return (2 * P.k) % P.t if lay.c_n == 2 else 1
 
 
+def oracle_threads() -> int:
+    """Threads the oracle runs on: every host core (HYENA_ORACLE_THREADS overrides)."""
+    v = os.environ.get("HYENA_ORACLE_THREADS", "")
+    return max(1, int(v)) if v.isdigit() else (os.cpu_count() or 1)
+
+
 def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk: dict,
-            out_cts: list[int] | None = None) -> np.ndarray:
+            out_cts: list[int] | None = None, threads: int | None = None,
+            timings: dict | None = None) -> np.ndarray:
     """Homomorphic convolution of one layer.
 
     For every input ciphertext: decompose once, then one hoisted rotation per
@@ -296,7 +338,14 @@ def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk
     out = k * A0 + PMult(A1, [k, -k]) (Sec. 3.1, Sec. 3.2.1).
 
     `out_cts` restricts the work to a subset of output ciphertexts (the
-    others are left zero), for sampled comparisons at full size."""
+    others are left zero), for sampled comparisons at full size.
+
+    The rotations of different input ciphertexts and the sums of different
+    output ciphertexts are independent; they run on `threads` threads (default:
+    every host core).  Each job is the same plain code as the one-thread form
+    and writes only its own results, so the words do not depend on the count.
+    `timings` (optional dict) receives the wall seconds of the two phases,
+    "rotations" and "sums" (for the CPU baseline's timing)."""
     plan = rotation_plan(P, lay)
     n_out = lay.n_ct_out
     todo = range(n_out) if out_cts is None else sorted(set(out_cts))
@@ -305,53 +354,78 @@ def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk
     need_ru = sorted({c // lay.out_groups for c in todo})
     out = np.zeros((n_out, 2, P.L, P.N), dtype=np.uint64)
     pk = bfv.hadamard_plaintext(P) if lay.c_n == 2 else None
+    pool = ThreadPoolExecutor(max_workers=threads or oracle_threads())
 
-    for ru in need_ru:
-        # rotated copies of this row-unit's input ciphertexts
-        rot = {}
-        needed_j = range(lay.in_groups)
-        if lay.depthwise:
-            needed_j = sorted({c % lay.out_groups for c in todo if c // lay.out_groups == ru})
-        for j in needed_j:
-            ct = cts_in[ru * lay.in_groups + j]
-            digits = bfv.decompose(P, ct)
-            for ti, d, g in plan:
-                rot[(j, ti, d)] = ct.copy() if g == 1 else bfv.rotate_hoisted(P, ct, digits, ksk[g], g)
-        for c in todo:
-            if c // lay.out_groups != ru:
-                continue
-            g_out = c % lay.out_groups
-            if lay.c_n == 2:
-                A0 = np.zeros((2, P.L, P.N), dtype=np.uint64)
-                A1 = np.zeros((2, P.L, P.N), dtype=np.uint64)
-                js = [g_out] if lay.depthwise else range(lay.in_groups)
-                for j in js:
-                    for ti, d, _ in plan:
-                        s0, s1 = hadamard_scalars(lay, weights, g_out, j, ti, d)
-                        if s0:
-                            bfv.cmult_add(P, A0, rot[(j, ti, d)], s0)
-                        if s1:
-                            bfv.cmult_add(P, A1, rot[(j, ti, d)], s1)
-                res = bfv.cmult(P, A0, P.k)
-                res = bfv.hadd(P, res, bfv.pmult(P, A1, pk))
-            else:
-                res = np.zeros((2, P.L, P.N), dtype=np.uint64)
-                js = [g_out] if lay.depthwise else range(lay.in_groups)
-                for j in js:
-                    for ti, _, _ in plan:
-                        dy, dx = divmod(ti, lay.kh)
-                        f = int(weights[g_out, 0 if lay.depthwise else j, dy, dx]) \
-                            if (g_out < lay.C_out and j < lay.C_in) else 0
-                        if f:
-                            bfv.cmult_add(P, res, rot[(j, ti, 0)], f)
-            out[c] = res
+    def rotations_of(ru: int, j: int) -> dict:
+        ct = cts_in[ru * lay.in_groups + j]
+        digits = bfv.decompose(P, ct)
+        return {(j, ti, d): ct.copy() if g == 1 else bfv.rotate_hoisted(P, ct, digits, ksk[g], g)
+                for ti, d, g in plan}
+
+    try:
+        for ru in need_ru:
+            # rotated copies of this row-unit's input ciphertexts
+            rot = {}
+            needed_j = range(lay.in_groups)
+            if lay.depthwise:
+                needed_j = sorted({c % lay.out_groups for c in todo if c // lay.out_groups == ru})
+            t0 = time.perf_counter()
+            for part in pool.map(lambda j: rotations_of(ru, j), needed_j):
+                rot.update(part)
+            t1 = time.perf_counter()
+            mine = [c for c in todo if c // lay.out_groups == ru]
+            for c, res in zip(mine, pool.map(lambda c: _output_ct(P, lay, weights, plan, rot, pk, c), mine)):
+                out[c] = res
+            if timings is not None:
+                timings["rotations"] = timings.get("rotations", 0.0) + t1 - t0
+                timings["sums"] = timings.get("sums", 0.0) + time.perf_counter() - t1
+    finally:
+        pool.shutdown()
     return out
 
 
+def _output_ct(P: Params, lay: Layout, weights: np.ndarray, plan, rot: dict, pk, c: int) -> np.ndarray:
+    """Output ciphertext c of the layer from the rotated copies of its row-unit's inputs."""
+    g_out = c % lay.out_groups
+    if lay.c_n == 2:
+        A0 = np.zeros((2, P.L, P.N), dtype=np.uint64)
+        A1 = np.zeros((2, P.L, P.N), dtype=np.uint64)
+        js = [g_out] if lay.depthwise else range(lay.in_groups)
+        for j in js:
+            for ti, d, _ in plan:
+                s0, s1 = hadamard_scalars(lay, weights, g_out, j, ti, d)
+                if s0:
+                    bfv.cmult_add(P, A0, rot[(j, ti, d)], s0)
+                if s1:
+                    bfv.cmult_add(P, A1, rot[(j, ti, d)], s1)
+        res = bfv.cmult(P, A0, P.k)
+        res = bfv.hadd(P, res, bfv.pmult(P, A1, pk))
+    else:
+        res = np.zeros((2, P.L, P.N), dtype=np.uint64)
+        js = [g_out] if lay.depthwise else range(lay.in_groups)
+        for j in js:
+            for ti, _, _ in plan:
+                dy, dx = divmod(ti, lay.kh)
+                f = int(weights[g_out, 0 if lay.depthwise else j, dy, dx]) \
+                    if (g_out < lay.C_out and j < lay.C_in) else 0
+                if f:
+                    bfv.cmult_add(P, res, rot[(j, ti, 0)], f)
+    return res
+
+
 # ------------------------------------------------------------ client helpers
-def encrypt_image(P: Params, lay: Layout, s: np.ndarray, act: np.ndarray, seed: int) -> np.ndarray:
-    slots = pack_slots(lay, act)
-    return np.stack([bfv.encrypt(P, s, bfv.encode(P, slots[c]), seed, c) for c in range(lay.n_ct_in)])
+def encrypt_image(P: Params, lay: Layout, s: np.ndarray, act: np.ndarray, seed: int, only=None,
+                  threads: int | None = None) -> np.ndarray:
+    """Input ciphertexts [n_ct_in][2][L][N] of a layer; ciphertext c uses the random streams of index c.
+    `only` (optional): encrypt just these ciphertext indices and leave the others zero."""
+    idx = range(lay.n_ct_in) if only is None else sorted(set(only))
+    ru_set = None if only is None else {c // lay.in_groups for c in idx}
+    slots = pack_slots(lay, act, ru_set)
+    out = np.zeros((lay.n_ct_in, 2, P.L, P.N), dtype=np.uint64)
+    with ThreadPoolExecutor(max_workers=threads or oracle_threads()) as pool:
+        for c, ct in zip(idx, pool.map(lambda c: bfv.encrypt(P, s, bfv.encode(P, slots[c]), seed, c), idx)):
+            out[c] = ct
+    return out
 
 
 def decrypt_image(P: Params, lay: Layout, s: np.ndarray, cts_out: np.ndarray, unscale: bool = True) -> np.ndarray:

@@ -103,3 +103,32 @@ def mobilenet_v1_convs() -> list[ConvShape]:
         ho = (h - 1) // s + 1
         L.append(ConvShape(cin, cout, ho, ho, k=1))
     return L
+
+
+def sample_index(label: int, n: int, seed: int = 5) -> int:
+    """A seeded index in [0, n): which output ciphertext of a layer a sampled comparison checks."""
+    return int(uniform_int(seed, label, (1,), 0, n - 1)[0])
+
+
+# the network stacks as the tests and the benchmark run them: shapes, ring, images per step
+STACKS = {
+    "resnet20": (resnet20_convs, 8192, 3, 1),
+    "vgg16": (vgg16_convs, 16384, 4, 8),
+    "mobilenet": (mobilenet_v1_convs, 8192, 4, 32),
+}
+
+
+def stack_layer(stack: str, i: int) -> dict:
+    """Layer i of a stack as a layer description (3x3 or 1x1, Hyena packing c_n = 2)."""
+    shapes, _, _, images = STACKS[stack]
+    s = shapes()[i]
+    return dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
+                n_images=images, c_n=2)
+
+
+def stack_inputs(stack: str, i: int, t: int):
+    """Activations, weights and encryption seed of layer i of a stack (the same for every caller)."""
+    sp = stack_layer(stack, i)
+    act = activations((sp["n_images"], sp["C_in"], sp["H"], sp["W"]), t, label=i)
+    wt = weights((sp["C_out"], 1 if sp["depthwise"] else sp["C_in"], sp["kh"], sp["kh"]), label=i)
+    return act, wt, SEED_ENC + i

@@ -187,9 +187,12 @@ def test_autotuned_configuration_is_bit_exact():
     rings.close()
 
 
-def test_learned_picks_are_bit_exact():
-    """The shipped cost model's configurations for ResNet-20 layers (first layer, a 16-channel
-    layer, the first stride-2 layer), run with real keys, give the oracle's words."""
+@pytest.mark.parametrize("stack,li", [("resnet20", 0), ("resnet20", 1), ("resnet20", 7), ("vgg16", 11)])
+def test_learned_picks_are_bit_exact(stack, li):
+    """The shipped cost model's configuration for a layer (ResNet-20: the first layer, a 16-channel
+    layer, the first stride-2 layer; VGG-16: a 512 -> 512 layer on 8 images, K = 4608 terms), run
+    with real keys, gives the oracle's words on sampled output ciphertexts, and every output
+    decrypts to the plain convolution."""
     import os
 
     from oracle import bfv, conv
@@ -200,41 +203,38 @@ def test_learned_picks_are_bit_exact():
         pytest.skip("no trained weights in the package")
     model = CM.CostModel.load(CM.WEIGHTS)
     rings = CM.Rings()
-    shapes = synth.resnet20_convs()
-    for li in (0, 1, 7):
-        sh = shapes[li]
-        s = CM.Shape(sh.C_in, sh.C_out, sh.H, sh.W, sh.k, sh.stride, sh.depthwise, 1)
-        c = CM.pick(rings, model, s)
-        p = rings.get(c.N, c.L)
-        info = H.he_params_info(p)
-        d = c.desc(s)
-        spec = dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=False,
-                    n_images=1, c_n=c.c_n, tile_h=c.tile[0], tile_w=c.tile[1])
-        sk = H.he_keygen(p, synth.SEED_KEYS)
-        gk = H.he_galois_keys(p, sk, H.he_layer_galois(p, d), synth.SEED_KEYS)
-        act = synth.activations((1, s.C_in, s.H, s.W), info.t, label=li)
-        wt = synth.weights((s.C_out, s.C_in, 3, 3), label=li)
-        cts = H.he_encrypt_image(p, sk, d, act, synth.SEED_ENC, info)
-        plan = H.he_conv_plan(p, gk, d, wt, mac_groups=c.mac_groups, mac_impl=c.mac_impl, tc_rows=c.tc_rows)
-        _, n_out, ws = H.he_conv_sizes(plan)
-        d_in = torch.from_numpy(cts.reshape(-1).view(np.int64)).cuda()
-        d_out = torch.empty(n_out, dtype=torch.int64, device="cuda")
-        d_ws = torch.empty(ws // 8 + 1, dtype=torch.int64, device="cuda")
-        H.he_conv_forward(plan, d_in.data_ptr(), d_out.data_ptr(), d_ws.data_ptr())
-        torch.cuda.synchronize()
-        out = d_out.cpu().numpy().view(np.uint64).reshape(-1, 2, info.L, info.N)
-        P = prm.make_params(N=c.N, L=c.L, w=info.w)
-        s_or = bfv.keygen(P, synth.SEED_KEYS)
-        ol = conv.Layout(N=c.N, **spec)
-        ksk = {g: bfv.galois_key(P, s_or, g, synth.SEED_KEYS) for g in conv.galois_elements(P, ol)}
-        sample = [0, len(out) - 1]
-        ref = conv.he_conv(P, ol, wt, cts, ksk, out_cts=sample)
-        for i in sample:
-            assert (out[i] == ref[i]).all(), (li, c)
-        dec = H.he_decrypt_image(p, sk, d, out)
-        assert (dec == conv.conv_plain(act, wt, s.stride, 1, False, info.t)).all(), (li, c)
-        H.he_plan_destroy(plan)
-        H.he_galkeys_destroy(gk)
-        H.he_seckey_destroy(sk)
+    sp = synth.stack_layer(stack, li)
+    s = CM.Shape(sp["C_in"], sp["C_out"], sp["H"], sp["W"], sp["kh"], sp["stride"], sp["depthwise"], sp["n_images"])
+    c = CM.pick(rings, model, s)
+    p = rings.get(c.N, c.L)
+    info = H.he_params_info(p)
+    d = c.desc(s)
+    spec = dict(sp, c_n=c.c_n, tile_h=c.tile[0], tile_w=c.tile[1])
+    sk = H.he_keygen(p, synth.SEED_KEYS)
+    gk = H.he_galois_keys(p, sk, H.he_layer_galois(p, d), synth.SEED_KEYS)
+    act, wt, enc_seed = synth.stack_inputs(stack, li, info.t)
+    cts = H.he_encrypt_image(p, sk, d, act, enc_seed, info)
+    plan = H.he_conv_plan(p, gk, d, wt, mac_groups=c.mac_groups, mac_impl=c.mac_impl, tc_rows=c.tc_rows)
+    _, n_out, ws = H.he_conv_sizes(plan)
+    d_in = torch.from_numpy(cts.reshape(-1).view(np.int64)).cuda()
+    d_out = torch.empty(n_out, dtype=torch.int64, device="cuda")
+    d_ws = torch.empty(ws // 8 + 1, dtype=torch.int64, device="cuda")
+    H.he_conv_forward(plan, d_in.data_ptr(), d_out.data_ptr(), d_ws.data_ptr())
+    torch.cuda.synchronize()
+    H.he_conv_status(plan)
+    out = d_out.cpu().numpy().view(np.uint64).reshape(-1, 2, info.L, info.N)
+    P = prm.make_params(N=c.N, L=c.L, w=info.w)
+    s_or = bfv.keygen(P, synth.SEED_KEYS)
+    ol = conv.Layout(N=c.N, **spec)
+    ksk = {g: bfv.galois_key(P, s_or, g, synth.SEED_KEYS) for g in conv.galois_elements(P, ol)}
+    sample = sorted({0, synth.sample_index(li, len(out)), len(out) - 1})
+    ref = conv.he_conv(P, ol, wt, cts, ksk, out_cts=sample)
+    for i in sample:
+        assert (out[i] == ref[i]).all(), (stack, li, c, i)
+    dec = H.he_decrypt_image(p, sk, d, out)
+    assert (dec == conv.conv_plain(act, wt, s.stride, (s.k - 1) // 2, s.depthwise, info.t)).all(), (stack, li, c)
+    H.he_plan_destroy(plan)
+    H.he_galkeys_destroy(gk)
+    H.he_seckey_destroy(sk)
     model.close()
     rings.close()

@@ -6,16 +6,23 @@
   * MobileNetV1: the 27 convolutions (3x3 depthwise and 1x1 pointwise) on 32
     images of 224x224, N = 8192, L = 4, mixed layer sizes in one batch.
 
-For every layer the batched output equals he_conv_forward of that layer word
-for word (the bar is bit-exactness).  In the layers whose output ciphertexts
-depend on few input ciphertexts, sampled outputs are recomputed by the oracle
-from the same input ciphertexts (a deep layer's output ciphertext depends on
-hundreds of inputs, each rotated 17 times, which the plain oracle needs many
-minutes for).  Every output of the sampled layers and of the deepest layer is
-decrypted and compared with the plain convolution, computed by
-torch.nn.functional.conv2d in float64 (exact here: every partial sum is an
-integer below 2^20 * 8 * 4608 < 2^53).
+For every layer:
+  * the batched output equals he_conv_forward of that layer word for word;
+  * one seeded output ciphertext equals the oracle's, word for word.  A deep
+    layer's output ciphertext depends on all (up to 256) input ciphertexts of
+    its row-unit, each rotated 17 times, which takes the plain oracle minutes
+    per layer even on all cores, so the oracle's words for these samples are
+    stored as SHA-256 digests by tests/golden/make_network_samples.py (which
+    calls only the oracle; it also checks each sample's decryption against the
+    plain convolution).  The first layer is also recomputed by the oracle here.
+Every output of the first and the last layer is decrypted and compared with the
+plain convolution (torch.nn.functional.conv2d in float64, exact here: every
+partial sum is an integer below 2^20 * 8 * 4608 < 2^53).
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -29,6 +36,7 @@ from paper_2311_12519_gb300 import hyena as H  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 WAVE_LIMIT = 40 << 30  # bytes of workspace per wave
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "network_samples.json")
 
 
 def plain_conv(act, wt, stride, depthwise, t):
@@ -39,6 +47,10 @@ def plain_conv(act, wt, stride, depthwise, t):
     return np.mod(y.numpy().astype(np.int64), t)
 
 
+def digest(ct):
+    return hashlib.sha256(np.ascontiguousarray(ct, dtype="<u8").tobytes()).hexdigest()
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
     if not torch.cuda.is_available():
@@ -46,23 +58,26 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
-    p = H.he_params_create(N, L, decomp_bits=50)
+def _run_stack(stack, oracle_samples, decrypt_layers):
+    golden = json.load(open(GOLDEN))[stack]
+    shapes, N, L, n_images = synth.STACKS[stack]
+    assert (golden["N"], golden["L"], golden["images"]) == (N, L, n_images)
+    p = H.he_params_create(N, L, decomp_bits=golden["w"])
     info = H.he_params_info(p)
     sk = H.he_keygen(p, synth.SEED_KEYS)
-    specs = [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
-                  n_images=n_images, c_n=2) for s in shapes]
+    n_layers = len(shapes())
+    specs = [synth.stack_layer(stack, i) for i in range(n_layers)]
     descs = [H.conv_desc(**sp) for sp in specs]
     gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
     gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
     plans, d_ins, d_outs, host_in, acts, wts = [], [], [], [], [], []
     for i, (sp, d) in enumerate(zip(specs, descs)):
-        act = synth.activations((n_images, sp["C_in"], sp["H"], sp["W"]), info.t, label=i)
-        wt = synth.weights((sp["C_out"], 1 if sp["depthwise"] else sp["C_in"], sp["kh"], sp["kh"]), label=i)
-        cts = H.he_encrypt_image(p, sk, d, act, synth.SEED_ENC + i, info)
+        act, wt, enc_seed = synth.stack_inputs(stack, i, info.t)
+        cts = H.he_encrypt_image(p, sk, d, act, enc_seed, info)
         plans.append(H.he_conv_plan(p, gk, d, wt))
         n_in, n_out, _ = H.he_conv_sizes(plans[-1])
         assert n_in == cts.size
+        assert n_out // (2 * L * N) == golden["samples"][i]["n_ct_out"]
         d_ins.append(torch.from_numpy(cts.reshape(-1).view(np.int64)).cuda())
         d_outs.append(torch.full((n_out,), -1, dtype=torch.int64, device="cuda"))
         keep = i in oracle_samples or i in decrypt_layers
@@ -80,6 +95,13 @@ def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
     s.synchronize()
     for plan in plans:
         H.he_conv_status(plan)
+    # one seeded output ciphertext of every layer against the oracle's stored words
+    bad = []
+    for i, row in enumerate(golden["samples"]):
+        out = d_outs[i].cpu().numpy().view(np.uint64).reshape(-1, 2, L, N)
+        if digest(out[row["ct"]]) != row["sha256"]:
+            bad.append((i, row["ct"]))
+    assert not bad, f"(layer, ciphertext) samples that differ from the oracle: {bad}"
     # batched = plain per-layer, every layer, word for word (the workspace is free again)
     tmp = torch.empty(max(t.numel() for t in d_outs), dtype=torch.int64, device="cuda")
     for i, plan in enumerate(plans):
@@ -89,15 +111,13 @@ def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
         torch.cuda.synchronize()
         assert torch.equal(tmp[:n_out], d_outs[i]), f"layer {i}: batched output differs from he_conv_forward"
     del tmp, ws
-    # sampled output ciphertexts against the oracle, from the same input ciphertexts
-    P = prm.make_params(N=N, L=L, w=50)
+    # the first layer's samples recomputed by the oracle here, from the same input ciphertexts
+    P = prm.make_params(N=N, L=L, w=golden["w"])
     s_or = bfv.keygen(P, synth.SEED_KEYS)
     ksk = {}
     for i, cts in sorted(oracle_samples.items()):
-        sp = specs[i]
-        ol = conv.Layout(N=N, **sp)
-        gs = H.he_layer_galois(p, descs[i])
-        for g in gs:
+        ol = conv.Layout(N=N, **specs[i])
+        for g in H.he_layer_galois(p, descs[i]):
             if g not in ksk:
                 ksk[g] = bfv.galois_key(P, s_or, g, synth.SEED_KEYS)
         out = d_outs[i].cpu().numpy().view(np.uint64).reshape(-1, 2, L, N)
@@ -119,10 +139,8 @@ def _run_stack(N, L, shapes, n_images, oracle_samples, decrypt_layers):
 
 
 def test_vgg16_stack_8_images_batched_in_waves():
-    shapes = synth.vgg16_convs()
-    _run_stack(16384, 4, shapes, 8, oracle_samples={0: [0, 1791]}, decrypt_layers=[0, 12])
+    _run_stack("vgg16", oracle_samples={0: [0, 1791]}, decrypt_layers=[0, 12])
 
 
 def test_mobilenet_v1_stack_32_images_batched_in_waves():
-    shapes = synth.mobilenet_v1_convs()
-    _run_stack(8192, 4, shapes, 32, oracle_samples={0: [3], 2: [5], 3: [0, 77]}, decrypt_layers=[0, 3, 26])
+    _run_stack("mobilenet", oracle_samples={0: [3], 2: [5], 3: [0, 77]}, decrypt_layers=[0, 3, 26])

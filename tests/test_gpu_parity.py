@@ -188,12 +188,40 @@ def resnet():
     return Setup(8192, 3, 50)
 
 
-@pytest.mark.parametrize("li,sample", [(0, None), (1, None), (7, [0, 9]), (13, [3, 30])])
-def test_resnet20_layers(resnet, li, sample):
-    sh = synth.resnet20_convs()[li]
-    spec = dict(C_in=sh.C_in, C_out=sh.C_out, H=sh.H, W=sh.W, kh=sh.k, stride=sh.stride, depthwise=False,
-                n_images=1, c_n=2)
-    resnet.layer(spec, label=li, sample=sample)
+@pytest.fixture(scope="module")
+def resnet_stack(resnet):
+    """The 19 layers of the ResNet-20 stack with the stack's seeds: the library's input ciphertexts
+    (equal to the oracle's encryption) and the oracle's outputs for every output ciphertext."""
+    S = resnet
+    rows = []
+    for i in range(len(synth.resnet20_convs())):
+        sp = synth.stack_layer("resnet20", i)
+        d = H.conv_desc(**sp)
+        ol = conv.Layout(N=S.N, **sp)
+        act, wt, seed = synth.stack_inputs("resnet20", i, S.P.t)
+        gs = H.he_layer_galois(S.p, d)
+        gk = H.he_galois_keys(S.p, S.sk, gs, synth.SEED_KEYS)
+        cts = H.he_encrypt_image(S.p, S.sk, d, act, seed, S.info)
+        ref_in = conv.encrypt_image(S.P, ol, S.s, act, seed)
+        assert (cts == ref_in).all(), f"layer {i}: library encryption differs from the oracle's"
+        ref = conv.he_conv(S.P, ol, wt, ref_in, S.oracle_keys(gs))
+        rows.append(dict(spec=sp, d=d, act=act, wt=wt, gk=gk, cts=cts, ref=ref))
+    yield rows
+    for r in rows:
+        H.he_galkeys_destroy(r["gk"])
+
+
+@pytest.mark.parametrize("li", range(19))
+def test_resnet20_layer_matches_oracle(resnet, resnet_stack, li):
+    """Every output ciphertext of every ResNet-20 layer, per-layer form, word for word."""
+    r = resnet_stack[li]
+    out = gpu_layer(resnet.p, r["gk"], r["d"], r["wt"], r["cts"], resnet.L, resnet.N)
+    assert out.shape == r["ref"].shape
+    bad = [c for c in range(len(out)) if not (out[c] == r["ref"][c]).all()]
+    assert not bad, f"layer {li}: ciphertexts {bad[:8]} differ from the oracle"
+    dec = H.he_decrypt_image(resnet.p, resnet.sk, r["d"], out)
+    sp = r["spec"]
+    assert (dec == conv.conv_plain(r["act"], r["wt"], sp["stride"], 1, False, resnet.P.t)).all()
 
 
 # ---------------------------------------------------------------- largest ring
@@ -285,6 +313,15 @@ def test_tensor_core_mac_at_the_exactness_bound(pairs):
     assert (dec == conv.conv_plain(act, w, 1, 1, False, S.P.t)).all()
 
 
+@pytest.mark.parametrize("C_in", [240, 512])
+def test_tensor_core_multi_segment_matches_oracle(small, C_in):
+    """Contractions longer than one exact fp32 accumulation: K = 2160 terms (two segments of at
+    most 2048) and K = 4608 (three segments, the 512-channel layers of VGG-16), whose segment
+    results add mod q in the output; every output ciphertext word for word against the oracle."""
+    spec = dict(C_in=C_in, C_out=6, H=4, W=4, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
+    small.layer(spec, label=C_in, mac_impl=2)
+
+
 # ---------------------------------------------------------------- batched execution
 def _plan_and_inputs(S, spec, label, mac_impl=0):
     d = H.conv_desc(**spec)
@@ -355,42 +392,34 @@ def test_batch_equals_single_layers(small):
         H.he_galkeys_destroy(gk)
 
 
-def test_batch_of_resnet20_stack_matches_oracle_samples(resnet):
-    """The whole 19-layer stack in one batch; sampled outputs against the oracle, all decrypted."""
-    shapes = synth.resnet20_convs()
-    specs = [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=3, stride=s.stride, depthwise=False, n_images=1,
-                  c_n=2) for s in shapes]
-    items = [_plan_and_inputs(resnet, sp, i) for i, sp in enumerate(specs)]
-    d_ins, d_outs = [], []
-    for plan, gk, cts in items:
-        n_in, n_out, ws = H.he_conv_sizes(plan)
-        d_ins.append(to_dev(cts))
+def test_batch_of_resnet20_stack_matches_oracle(resnet, resnet_stack):
+    """The whole 19-layer stack in one batch, captured and replayed as a CUDA graph: every output
+    ciphertext of every layer equals the oracle's, word for word, on the capture and on a replay."""
+    plans, d_ins, d_outs = [], [], []
+    for r in resnet_stack:
+        plan = H.he_conv_plan(resnet.p, r["gk"], r["d"], r["wt"])
+        n_in, n_out, _ = H.he_conv_sizes(plan)
+        plans.append(plan)
+        d_ins.append(to_dev(r["cts"]))
         d_outs.append(torch.full((n_out,), -1, dtype=torch.int64, device="cuda"))
-    b = H.he_batch_create([it[0] for it in items])
+    b = H.he_batch_create(plans)
     ws = torch.empty(H.he_batch_workspace_bytes(b) // 8 + 1, dtype=torch.int64, device="cuda")
     s = torch.cuda.Stream()
-    H.he_batch_graph_launch(b, [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(),
-                            s.cuda_stream)
-    s.synchronize()
-    for i in (0, 8, 18):  # first layer, a stride-2 layer, the last 64-channel layer
-        plan, gk, cts = items[i]
-        sp = specs[i]
-        out = from_dev(d_outs[i], (-1, 2, 3, 8192))
-        ol = conv.Layout(N=8192, **sp)
-        act = synth.activations((1, sp["C_in"], sp["H"], sp["W"]), resnet.P.t, label=i)
-        wt = synth.weights((sp["C_out"], sp["C_in"], 3, 3), label=i)
-        ref_in = conv.encrypt_image(resnet.P, ol, resnet.s, act, synth.SEED_ENC + i)
-        assert (ref_in == cts).all()
-        ref = conv.he_conv(resnet.P, ol, wt, ref_in,
-                           resnet.oracle_keys(H.he_layer_galois(resnet.p, H.conv_desc(**sp))), out_cts=[0])
-        assert (out[0] == ref[0]).all()
-        dec = H.he_decrypt_image(resnet.p, resnet.sk, H.conv_desc(**sp), out)
-        assert (dec == conv.conv_plain(act, wt, sp["stride"], 1, False, resnet.P.t)).all()
+    for rep in range(2):
+        for t in d_outs:
+            t.fill_(-1)
+        torch.cuda.synchronize()
+        H.he_batch_graph_launch(b, [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws.data_ptr(),
+                                s.cuda_stream)
+        s.synchronize()
+        for i, r in enumerate(resnet_stack):
+            out = from_dev(d_outs[i], r["ref"].shape)
+            bad = [c for c in range(len(out)) if not (out[c] == r["ref"][c]).all()]
+            assert not bad, f"replay {rep}, layer {i}: ciphertexts {bad[:8]} differ from the oracle"
     H.he_batch_destroy(b)
-    for plan, gk, _ in items:
+    for plan in plans:
         H.he_conv_status(plan)
         H.he_plan_destroy(plan)
-        H.he_galkeys_destroy(gk)
 
 
 # ---------------------------------------------------------------- failure detection

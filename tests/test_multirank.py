@@ -29,16 +29,15 @@ def _rank_main(rank, world, port, out_dir):
     from oracle import params as prm
     from paper_2311_12519_gb300 import hyena as H
 
-    ri = bench.rank_inputs(rank)
-    N, L, w = 1024, 2, 25
-    spec = dict(C_in=3, C_out=4, H=5, W=6, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
+    # the first ResNet-20 layer (3 -> 16 channels, 32x32) on a small ring, with bench.py's per-rank inputs
+    N, L, w = 4096, 2, 25
+    spec = synth.stack_layer("resnet20", 0)
     p = H.he_params_create(N, L, decomp_bits=w)
     info = H.he_params_info(p)
     d = H.conv_desc(**spec)
-    act = synth.activations((1, 3, 5, 6), info.t, label=ri["act_label"])
-    wt = synth.weights((4, 3, 3, 3))
+    act, wt, enc_seed = bench.rank_inputs("resnet20", 0, rank, info.t)
     sk = H.he_keygen(p, synth.SEED_KEYS)
-    cts = H.he_encrypt_image(p, sk, d, act, ri["enc_seed"], info)
+    cts = H.he_encrypt_image(p, sk, d, act, enc_seed, info)
     P = prm.make_params(N=N, L=L, w=w)
     s = bfv.keygen(P, synth.SEED_KEYS)
     lay = conv.Layout(N=N, **spec)
@@ -68,5 +67,11 @@ def test_two_gloo_ranks(tmp_path):
 def test_throughput_counts_every_rank():
     import bench
 
+    import synth
+
     assert bench.layers_per_second(4, 19, 10, 2.0) == 4 * 19 * 10 / 2.0
-    assert bench.rank_inputs(0) != bench.rank_inputs(1)
+    a0, w0, s0 = bench.rank_inputs("vgg16", 3, 0, 786433)
+    a1, w1, s1 = bench.rank_inputs("vgg16", 3, 1, 786433)
+    assert not (a0 == a1).all() and s0 != s1 and (w0 == w1).all()  # own images, shared weights
+    a, w, s = synth.stack_inputs("vgg16", 3, 786433)
+    assert (a == a0).all() and (w == w0).all() and s == s0  # rank 0 runs the stack's own seeds

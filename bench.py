@@ -1,17 +1,21 @@
 """Throughput of encrypted convolution on the GB300 (one JSON line on stdout).
 
-Workload: the 19 3x3 convolutions of a ResNet-20 on 32x32 inputs, one image
-per GPU, N = 8192, L = 3 RNS limbs of 50 bits, t = 1032193, Hyena packing
-(c_n = 2).  A step runs all 19 layers once on fresh synthetic ciphertexts
-resident in HBM.  value = layers/s over all ranks of the batched form (one
-launch per stage for all layers, replayed as a CUDA graph); the plain
-per-layer form (he_conv_forward per layer) is reported beside it, with
-modMAC/s.  e2e repeats the step from pinned host buffers through
-he_batch_forward_host (copies inside the timed region; layer by layer through
-he_conv_forward_host beside it).  --workload vgg16|mobilenet
-measures the VGG-16 (8 images, N = 16384) or MobileNetV1 (32 images) stack
-the same way; --mode ablation prints one line per variant of the latency
-study; --impl reference times the CPU oracle instead.
+Default workload: the 13 3x3 convolutions of VGG-16 on 8 images of 224x224
+per GPU, N = 16384, L = 4 RNS limbs of 50 bits, t = 786433, Hyena packing
+(c_n = 2): 6128 input and 8704 output ciphertexts per step.  A step runs all
+13 layers once on synthetic ciphertexts resident in HBM.  value = layers/s
+over all ranks of the batched form (one launch per stage for all layers of a
+workspace wave, replayed as a CUDA graph); the plain per-layer form
+(he_conv_forward per layer) is reported beside it, with modMAC/s.  e2e
+repeats the step from pinned host buffers through he_batch_forward_host
+(copies inside the timed region).  After the timed region, one seeded output
+ciphertext of every layer is compared with the oracle's words (digests stored
+by tests/golden/make_network_samples.py) and the last layer is decrypted and
+compared with the plain convolution.  --workload resnet20|mobilenet measures
+the ResNet-20 (1 image, N = 8192, L = 3) or MobileNetV1 (32 images) stack the
+same way; --mode ablation prints one line per variant of the latency study;
+--mode learned runs every layer in the learned cost model's configuration;
+--impl reference times the CPU oracle instead.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under
 torch.distributed.run (one process per GPU, no collective on the data path).
@@ -19,6 +23,7 @@ torch.distributed.run (one process per GPU, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -34,30 +39,28 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-N_RING, L_LIMBS, LIMB_BITS = 8192, 3, 50
-WORKLOAD = "resnet20-3x3-stack, 32x32, 1 image/GPU, N=8192, L=3x50-bit, t=1032193, c_n=2"
-# other stacks (not the headline): name -> (shapes, N, L, images per GPU, batch workspace limit, description)
+LIMB_BITS = 50
+METRIC = "HE-conv layers/s and modMAC/s, batched vs plain per-layer, bit-exact; % HBM roof"
+# workload -> (batch workspace limit in bytes or None, description)
 WORKLOADS = {
-    "resnet20": (synth.resnet20_convs, N_RING, L_LIMBS, 1, None, WORKLOAD),
-    "vgg16": (synth.vgg16_convs, 16384, 4, 8, 64 << 30,
-              "vgg16-3x3-stack, 224x224, 8 images/GPU, N=16384, L=4x50-bit, t=786433, c_n=2"),
-    "mobilenet": (synth.mobilenet_v1_convs, 8192, 4, 32, 64 << 30,
-                  "mobilenetv1-dw+pw-stack, 224x224, 32 images/GPU, N=8192, L=4x50-bit, t=1032193, c_n=2"),
+    "vgg16": (64 << 30, "vgg16-3x3-stack (13 convs), 224x224, 8 images/GPU, N=16384, L=4x50-bit, t=786433, c_n=2"),
+    "resnet20": (None, "resnet20-3x3-stack (19 convs), 32x32, 1 image/GPU, N=8192, L=3x50-bit, t=1032193, c_n=2"),
+    "mobilenet": (64 << 30, "mobilenetv1-dw+pw-stack (27 convs), 224x224, 32 images/GPU, N=8192, L=4x50-bit, "
+                            "t=1032193, c_n=2"),
 }
-METRIC = "HE-conv layers/s (ResNet-20 stack, bit-exact)"
+DEFAULT_WORKLOAD = "vgg16"
 L2_BYTES = 129 * 2**20
+GOLDEN = os.path.join(ROOT, "tests", "golden", "network_samples.json")
 # DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source with this digest prefix
-# (kernel_source_digest); reported as roofline traffic only while the kernels are unchanged
-PROFILED_TRAFFIC = {"source": "6a8f6476f848e201", "k_keyswitch": 2.715e9, "k_mac_tc": 2.358e9, "k_ntt_inputs": 0.381e9,
-                    "k_intt": 0.223e9}
+# (kernel_source_digest), per workload; reported as roofline traffic only while the kernels are unchanged
+PROFILED_TRAFFIC = {}
 
 
 def kernel_source_digest():
     """sha256 of device.cu up to its device-table section, without comments and blank space: the
     kernels and their launch code, which fix what a profiled launch does (the host API below them
     does not)."""
-    import hashlib
     import re
 
     text = open(os.path.join(ROOT, "paper_2311_12519_gb300", "csrc", "device.cu"), "rb").read()
@@ -66,25 +69,53 @@ def kernel_source_digest():
     return hashlib.sha256(re.sub(rb"\s+", b" ", code))
 
 
-def layer_descs(workload="resnet20"):
-    shapes, _, _, images, _, _ = WORKLOADS[workload]
-    return [dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
-                 n_images=images, c_n=2) for s in shapes()]
+def host_cores():
+    """Host threads this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
-def modmacs(spec, lay, n_rot, L, l, N):
-    """Algorithmic modular multiply-accumulates of one layer (conv MAC + key switch)."""
+def layer_specs(workload, layers=None):
+    """The stack's layer descriptions (all, or the listed layer indices), ring and images."""
+    shapes, N, L, images = synth.STACKS[workload]
+    idx = range(len(shapes())) if layers is None else layers
+    return [synth.stack_layer(workload, i) for i in idx], N, L, images
+
+
+def layer_counts(spec, lay, L, l, N):
+    """Algorithmic counts of one layer (one image batch): conv and key-switch modMACs, and the
+    bytes of Sec. 8(d)'s rooflines for each stage."""
+    packed = spec["c_n"] == 2
+    n_rot = spec["kh"] ** 2 * (2 if packed and not spec["depthwise"] else 1)
     K = n_rot if spec["depthwise"] else lay.in_groups * n_rot
-    conv = lay.row_units * lay.out_groups * (2 if spec["c_n"] == 2 else 1) * K * 2 * L * N
+    conv = lay.row_units * lay.out_groups * (2 if packed else 1) * K * 2 * L * N
     ks = lay.n_ct_in * lay.n_galois * 2 * L * l * L * N
-    return conv, ks
+    w8 = N * 8
+    return {
+        "conv_modmac": conv, "ks_modmac": ks,
+        # forward transforms of c0 and of the digits of c1 (the single digit of c1 in its own limb is c1)
+        "ntt_in_transforms": lay.n_ct_in * (L + L * l * L),
+        # the key stream of every Galois element once, plus the digit and c0 transforms the switch reads
+        "ks_bytes": lay.n_galois * L * l * 2 * L * w8 + lay.n_ct_in * (L * l * L + L) * w8,
+        "ntt_out_transforms": lay.n_ct_out * 2 * L,
+        "in_bytes": lay.n_ct_in * 2 * L * w8, "out_bytes": lay.n_ct_out * 2 * L * w8,
+        # rotated copies the MAC streams (this design's own traffic, not the method's minimum)
+        "mac_r_bytes": lay.n_ct_in * n_rot * 2 * L * w8,
+    }
 
 
-# ------------------------------------------------------------------ ranks
-def rank_inputs(rank):
-    """Per-rank workload: rank r encrypts its own image (activation labels and
-    encryption seed depend on r); weights and keys are shared by all ranks."""
-    return {"act_label": 1000 * rank, "enc_seed": synth.SEED_ENC + 7919 * rank}
+def rank_inputs(workload, i, rank, t):
+    """Layer i's inputs on a rank: rank 0 runs the stack's own seeds (those of the tests and the
+    stored oracle samples); rank r > 0 its own activations and encryption randomness."""
+    act, wt, seed = synth.stack_inputs(workload, i, t)
+    if rank:
+        sp = synth.stack_layer(workload, i)
+        act = synth.activations(act.shape, t, label=i + 1000 * rank)
+        seed = seed + 7919 * rank
+        del sp
+    return act, wt, seed
 
 
 def reduce_max(values, device, world):
@@ -99,7 +130,7 @@ def reduce_max(values, device, world):
 
 
 def layers_per_second(world, n_layers, steps, seconds):
-    """Whole-job throughput: every rank runs n_layers layers per step on its own image."""
+    """Whole-job throughput: every rank runs n_layers layers per step on its own images."""
     return world * n_layers * steps / seconds
 
 
@@ -158,46 +189,174 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) sample
-def oracle_sample(reps=1):
-    """The CPU oracle on one whole layer of the stack (16 -> 16 channels, 32x32):
-    returns (seconds per layer, description).  Single-threaded."""
+def oracle_layer_estimate(workload, i, threads, keys_cache):
+    """Seconds the CPU oracle (oracle/conv.he_conv on `threads` host threads) needs for layer i of
+    the stack, from a bounded sample: the layer with its input channels cut to `threads` channel
+    groups (same ring, kernel, images and output channels), of which `threads` output ciphertexts
+    of the first row-unit are computed.  The timed rotation phase gives the cost per input
+    ciphertext (decomposition + hoisted rotations, one ciphertext per thread), the timed sum phase
+    the cost per accumulated term of an output ciphertext (CMult + HAdd, one ciphertext per
+    thread, with its reduction and PMult); the layer's estimate scales them by its own counts
+    (input ciphertexts; output ciphertexts x terms)."""
     from oracle import bfv, conv
     from oracle import params as prm
 
-    P = prm.make_params(N=N_RING, L=L_LIMBS, w=50)
-    spec = layer_descs()[1]
-    lay = conv.Layout(N=N_RING, **spec)
-    s = bfv.keygen(P, synth.SEED_KEYS)
-    ksk = {g: bfv.galois_key(P, s, g, synth.SEED_KEYS) for g in conv.galois_elements(P, lay)}
-    act = synth.activations((1, spec["C_in"], spec["H"], spec["W"]), P.t, label=1)
-    wt = synth.weights((spec["C_out"], spec["C_in"], 3, 3), label=1)
-    cts = conv.encrypt_image(P, lay, s, act, synth.SEED_ENC)
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        conv.he_conv(P, lay, wt, cts, ksk)
-        times.append(time.perf_counter() - t0)
-    return times, "one whole ResNet-20 layer (16->16 channels, 32x32, N=8192, L=3) per step, 1 thread"
+    shapes, N, L, images = synth.STACKS[workload]
+    if (N, L) not in keys_cache:
+        P = prm.make_params(N=N, L=L, w=50)
+        keys_cache[(N, L)] = (P, bfv.keygen(P, synth.SEED_KEYS), {})
+    P, s, ksk = keys_cache[(N, L)]
+    sp = synth.stack_layer(workload, i)
+    lay = conv.Layout(N=N, **sp)
+    groups = min(threads, lay.in_groups)
+    sub = dict(sp, C_in=min(sp["C_in"], 2 * groups))
+    if sp["depthwise"]:
+        sub["C_out"] = sub["C_in"]
+    lay_s = conv.Layout(N=N, **sub)
+    act, wt, seed = synth.stack_inputs(workload, i, P.t)
+    act_s = np.ascontiguousarray(act[:, :sub["C_in"]])
+    wt_s = np.ascontiguousarray(wt[:sub["C_out"], :(1 if sp["depthwise"] else sub["C_in"])])
+    cts = conv.encrypt_image(P, lay_s, s, act_s, seed, only=range(lay_s.in_groups), threads=threads)
+    for g in conv.galois_elements(P, lay_s):
+        if g not in ksk:
+            ksk[g] = bfv.galois_key(P, s, g, synth.SEED_KEYS)
+    n_out = min(threads, lay_s.out_groups)
+    tm = {}
+    conv.he_conv(P, lay_s, wt_s, cts, ksk, out_cts=list(range(n_out)), threads=threads, timings=tm)
+    n_rot = len(conv.rotation_plan(P, lay_s))
+    k_s = n_rot if sp["depthwise"] else lay_s.in_groups * n_rot
+    k = n_rot if sp["depthwise"] else lay.in_groups * n_rot
+    rot_in = lay_s.in_groups if not sp["depthwise"] else n_out
+    per_ct = tm["rotations"] / rot_in
+    per_term = tm["sums"] / (n_out * k_s)
+    est = per_ct * lay.n_ct_in + per_term * lay.n_ct_out * k
+    return est, tm["rotations"] + tm["sums"], {"layer": i, "input_cts": rot_in, "output_cts": n_out, "terms": k_s}
+
+
+def oracle_sample(workload, layers, threads):
+    """Estimated oracle seconds for each sampled layer, wall seconds spent, and a description."""
+    cache, est, spent, parts = {}, [], 0.0, []
+    for i in layers:
+        e, w, info = oracle_layer_estimate(workload, i, threads, cache)
+        est.append(e)
+        spent += w
+        parts.append(info)
+    n_layers = len(synth.STACKS[workload][0]())
+    desc = (f"CPU oracle (oracle/conv.he_conv) on {threads} host threads; layers {list(layers)} of the "
+            f"{n_layers}-layer stack, each cut to {threads} input channel groups with {threads} output ciphertexts "
+            "computed; rotation and sum phases timed and scaled by each layer's input ciphertexts and "
+            "output ciphertexts x terms; layers/s = sampled layers / estimated seconds")
+    return est, spent, desc, parts
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: each step estimates one layer of the stack (cycling)."""
     if rank != 0:
         return
-    steps = max(1, args.steps)
-    warm = max(0, args.warmup)
-    times, desc = oracle_sample(reps=steps + warm)
-    t = sum(times[warm:])
-    value = steps / t
+    wl = args.workload
+    n_layers = len(synth.STACKS[wl][0]())
+    threads = host_cores()
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    cache, est = {}, []
+    t0 = time.perf_counter()
+    for st in range(warm + steps):
+        e, _, _ = oracle_layer_estimate(wl, st % n_layers, threads, cache)
+        if st >= warm:
+            est.append(e)
+    wall = time.perf_counter() - t0
+    value = len(est) / sum(est)
+    desc = (f"CPU oracle (oracle/conv.he_conv) on {threads} host threads; step s estimates layer s mod {n_layers} "
+            f"of the stack from a sample cut to {threads} input channel groups and {threads} output ciphertexts "
+            "(rotation and sum phases timed, scaled by the layer's counts); layers/s = steps / estimated seconds")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": args.gpus,
-            "steps": steps, "warmup": warm, "ms_per_step": 1000 * t / steps, "higher_is_better": True,
+            "steps": steps, "warmup": warm, "ms_per_step": 1000 * sum(est) / len(est), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "config": {"workload": WORKLOADS[wl][1]},
+            "wall_seconds": round(wall, 1),
+            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
+def verify_outputs(H, p, sk, info, workload, specs, descs, d_outs, rank, index):
+    """After the timed region, on rank 0 (whose inputs are the stack's own seeds): one seeded output
+    ciphertext of every layer against the oracle's stored words, and every output ciphertext of
+    the last layer decrypted and compared with the plain convolution (float64 torch conv2d)."""
+    import torch
+
+    if rank != 0:
+        return {"checked": False, "why": "rank > 0 runs its own inputs; rank 0 checks the stack's seeds"}
+    res = {"checked": True}
+    L, N = info.L, info.N
+    ctw = 2 * L * N
+    try:
+        golden = json.load(open(GOLDEN)).get(workload)
+    except OSError:
+        golden = None
+    if golden and (golden["N"], golden["L"]) == (N, L):
+        ok, bad = 0, []
+        for i, li in enumerate(index):
+            row = golden["samples"][li]
+            c = row["ct"]
+            words = d_outs[i][c * ctw:(c + 1) * ctw].cpu().numpy().view(np.uint64)
+            if hashlib.sha256(np.ascontiguousarray(words, dtype="<u8").tobytes()).hexdigest() == row["sha256"]:
+                ok += 1
+            else:
+                bad.append(li)
+        res["oracle_samples"] = {"layers": len(index), "equal": ok, "differ": bad,
+                                 "what": "one seeded output ciphertext per layer vs the oracle's words (SHA-256)"}
+    else:
+        res["oracle_samples"] = None
+    i = len(specs) - 1
+    sp = specs[i]
+    act, wt, _ = synth.stack_inputs(workload, index[i], info.t)
+    out = d_outs[i].cpu().numpy().view(np.uint64).reshape(-1, 2, L, N)
+    dec = H.he_decrypt_image(p, sk, descs[i], out)
+    x = torch.from_numpy(act.astype(np.float64))
+    w = torch.from_numpy(wt.astype(np.float64))
+    y = torch.nn.functional.conv2d(x, w, stride=sp["stride"], padding=(sp["kh"] - 1) // 2,
+                                   groups=sp["C_in"] if sp["depthwise"] else 1)
+    plain = np.mod(y.numpy().astype(np.int64), info.t)
+    res["decrypt_last_layer"] = {"layer": index[i], "ciphertexts": int(out.shape[0]),
+                                 "equal": bool((dec == plain).all())}
+    res["bit_exact"] = bool(res["decrypt_last_layer"]["equal"] and
+                            (res["oracle_samples"] is None or not res["oracle_samples"]["differ"]))
+    return res
+
+
+def stage_rooflines(stages, counts, steps, peaks, N):
+    """Sec. 8(d)'s roofline of each stage kernel of the batched step, from its event-timed
+    duration: NTTs 16 N bytes per transform, the key switch its key stream plus the digit and c0
+    transforms it reads, the tensor-core MAC 10 fp16 flops per modMAC (five 10-bit chunks, one
+    multiply-add each) against the dense fp16 tensor peak (= the measured bf16 peak)."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    tc = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+    out = {}
+    for st, (ms, launches) in stages.items():
+        sec = ms / 1000 / max(1, steps)
+        if st == "ntt_in":
+            a = counts["ntt_in_transforms"] * 16 * N
+            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
+        elif st == "ntt_out":
+            a = counts["ntt_out_transforms"] * 16 * N
+            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
+        elif st == "keyswitch":
+            a = counts["ks_bytes"]
+            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
+        else:
+            a = 10 * counts["conv_modmac"]
+            r = {"bound": "tensor", "algorithmic": a, "unit": "TFLOP/s", "peak": tc,
+                 "hbm_gbs_design_bytes": (counts["mac_r_bytes"] + counts["out_bytes"]) / sec / 1e9 if sec else None}
+        scale = 1e9 if r["unit"] == "GB/s" else 1e12
+        r["achieved"] = a / sec / scale if sec else None
+        r["frac"] = r["achieved"] / r["peak"] if sec else None
+        r["ms_per_step"] = ms / max(1, steps)
+        r["launches_per_step"] = launches / max(1, steps)
+        out[st] = r
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -207,10 +366,14 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    _, n_ring, n_limbs, images, ws_limit, workload = WORKLOADS[args.workload]
-    specs = layer_descs(args.workload)
-    k_max = max(s["kh"] ** 2 * (1 if s["depthwise"] else s["C_in"]) for s in specs)
-    p = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=0, est_mac_terms=k_max)
+    wl = args.workload
+    ws_limit, workload = WORKLOADS[wl]
+    specs, n_ring, n_limbs, images = layer_specs(wl, args.layers)
+    index = list(range(len(specs))) if args.layers is None else list(args.layers)
+    if args.layers is not None:
+        workload += f", layers {index} only"
+    t_setup = time.perf_counter()
+    p = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=50)
     info = H.he_params_info(p)
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
@@ -229,7 +392,6 @@ def run_gpu(args, rank, world):
             best, best_ms, times = CM.autotune(rings, shape, CM.candidates(rings, shape, [(N, L)]))
             specs[i] = dict(s, c_n=best.c_n, tile_h=best.tile[0], tile_w=best.tile[1])
             tunes[i] = dict(mac_groups=best.mac_groups, mac_impl=best.mac_impl, tc_rows=best.tc_rows)
-            # the untuned plan: packing 2, default tile, tensor core with 96 rows (CUDA cores if depthwise)
             default = times.get(CM.Config(N, L, 2, (0, 0), 1, 0, 0) if s["depthwise"] else
                                 CM.Config(N, L, 2, (0, 0), 2, 96, 0))
             tuned.append({"layer": i, "c_n": best.c_n, "tile": list(best.tile), **tunes[i], "ms": round(best_ms, 4),
@@ -240,28 +402,16 @@ def run_gpu(args, rank, world):
     gal = sorted(set(int(g) for d in descs for g in H.he_layer_galois(p, d)))
     gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
     plans, d_ins, d_outs, h_ins, h_outs = [], [], [], [], []
-    ws_max, conv_mm, ks_mm, in_bytes, out_bytes = 0, 0, 0, 0, 0
-    stage_bytes = {"ntt_in": 0, "keyswitch": 0, "mac": 0, "ntt_out": 0}
+    ws_max = 0
+    counts = {}
     for i, (s, d) in enumerate(zip(specs, descs)):
-        ri = rank_inputs(rank)
-        act = synth.activations((images, s["C_in"], s["H"], s["W"]), info.t, label=i + ri["act_label"])
-        wt = synth.weights((s["C_out"], 1 if s["depthwise"] else s["C_in"], s["kh"], s["kh"]), label=i)
-        cts = H.he_encrypt_image(p, sk, d, act, ri["enc_seed"], info)
+        act, wt, enc_seed = rank_inputs(wl, index[i], rank, info.t)
+        cts = H.he_encrypt_image(p, sk, d, act, enc_seed, info)
         plan = H.he_conv_plan(p, gk, d, wt, **tunes[i])
         n_in, n_out, ws = H.he_conv_sizes(plan)
         lay = H.he_layout_for_layer(p, d)
-        n_rot = s["kh"] ** 2 * (2 if s["c_n"] == 2 and not s["depthwise"] else 1)
-        cm, km = modmacs(s, lay, n_rot, L, l, N)
-        conv_mm += cm
-        ks_mm += km
-        ctb = 2 * L * N * 8
-        # algorithmic bytes of each stage (one read of every input, one write of every output)
-        stage_bytes["ntt_in"] += lay.n_ct_in * ctb + lay.n_ct_in * (2 * L + L * l * L) * N * 8
-        # minimum: rotated copies written once, digit NTTs, NTT(c0) and keys read once
-        stage_bytes["keyswitch"] += (lay.n_ct_in * lay.n_galois * ctb + lay.n_ct_in * (L * l * L + L) * N * 8
-                                     + lay.n_galois * L * l * 2 * L * N * 8)
-        stage_bytes["mac"] += lay.n_ct_in * n_rot * ctb + lay.n_ct_out * ctb
-        stage_bytes["ntt_out"] += 2 * lay.n_ct_out * ctb
+        for k, v in layer_counts(s, lay, L, l, N).items():
+            counts[k] = counts.get(k, 0) + v
         plans.append(plan)
         h_in = torch.from_numpy(cts.reshape(-1).view(np.int64)).pin_memory()
         h_ins.append(h_in)
@@ -269,184 +419,148 @@ def run_gpu(args, rank, world):
         d_ins.append(h_in.to(dev))
         d_outs.append(torch.empty(n_out, dtype=torch.int64, device=dev))
         ws_max = max(ws_max, ws)
-        in_bytes += n_in * 8
-        out_bytes += n_out * 8
+        del cts
     # the batch runs in waves under the workspace limit; the plain per-layer form shares its workspace
     batch = H.he_batch_create(plans) if ws_limit is None else H.he_batch_create_limited(plans, ws_limit)
     d_ws = torch.empty(max(ws_max, H.he_batch_workspace_bytes(batch)) // 8 + 1, dtype=torch.int64, device=dev)
-    d_wsb = d_ws
+    setup_s = time.perf_counter() - t_setup
+    ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
     if args.mode == "batch":
         # profiler mode: per step one launch per stage and wave, nothing else on the GPU
-        ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
         torch.cuda.synchronize()
         for _ in range(args.warmup + args.steps):
-            H.he_batch_forward(batch, ins_p, outs_p, d_wsb.data_ptr(), 0)
+            H.he_batch_forward(batch, ins_p, outs_p, d_ws.data_ptr(), 0)
         torch.cuda.synchronize()
-        print(json.dumps({"mode": "batch", "steps": args.steps, "warmup": args.warmup, "layers": len(plans)}))
+        for plan in plans:
+            H.he_conv_status(plan)
+        print(json.dumps({"mode": "batch", "workload": wl, "steps": args.steps, "warmup": args.warmup,
+                          "layers": len(plans)}))
         return
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     n_layers = len(plans)
     sp = stream.cuda_stream
+    warm = max(3, args.warmup)
 
-    def step():
+    def step_plain():
         for plan, a, b in zip(plans, d_ins, d_outs):
             H.he_conv_forward(plan, a.data_ptr(), b.data_ptr(), d_ws.data_ptr(), sp)
 
-    def step_host():
-        for plan, a, b, ha, hb in zip(plans, d_ins, d_outs, h_ins, h_outs):
-            H.he_conv_forward_host(plan, ha.data_ptr(), hb.data_ptr(), a.data_ptr(), b.data_ptr(), d_ws.data_ptr(),
-                                   sp)
+    def step_batch():
+        H.he_batch_graph_launch(batch, ins_p, outs_p, d_ws.data_ptr(), sp)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    with torch.cuda.stream(stream):
-        for _ in range(max(3, args.warmup)):
-            step()
+    def timed(fn):
+        """W warm-up steps, then K steps with the L2 flushed before each (outside the events)."""
+        for _ in range(warm):
+            fn()
         torch.cuda.synchronize()
-        # timed region: K steps, L2 flushed before each (outside the events)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        H.he_profile_enable(True)
-        H.he_profile_collect()
         barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             for e0, e1 in ev:
                 flush.zero_()
                 e0.record(stream)
-                step()
+                fn()
                 e1.record(stream)
             torch.cuda.synchronize()
-            clk.keep_busy(lambda: (flush.zero_(), step(), torch.cuda.synchronize()))
+            clk.keep_busy(lambda: (flush.zero_(), fn(), torch.cuda.synchronize()))
         barrier()
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev), clk.summary()
+
+    with torch.cuda.stream(stream):
+        # batched form (the headline): one launch per stage and wave, replayed as a CUDA graph
+        ms, clocks_b = timed(step_batch)
+        verified = verify_outputs(H, p, sk, info, wl, specs, descs, d_outs, rank, index)
+        # plain per-layer form, with the per-stage event times of its launches
+        H.he_profile_enable(True)
+        H.he_profile_collect()
+        ms_plain, clocks_p = timed(step_plain)
         H.he_profile_enable(False)
-        stages = H.he_profile_collect()
-        ms_plain = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-        # batched form: one launch per stage for all layers, replayed as a CUDA graph
-        ins_p, outs_p = [a.data_ptr() for a in d_ins], [b.data_ptr() for b in d_outs]
-
-        def step_batch():
-            H.he_batch_graph_launch(batch, ins_p, outs_p, d_wsb.data_ptr(), sp)
-
-        for _ in range(max(3, args.warmup)):
-            step_batch()
-        torch.cuda.synchronize()
-        evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk_b:
-            for e0, e1 in evb:
-                flush.zero_()
-                e0.record(stream)
-                step_batch()
-                e1.record(stream)
-            torch.cuda.synchronize()
-            clk_b.keep_busy(lambda: (flush.zero_(), step_batch(), torch.cuda.synchronize()))
-        barrier()
-        ms = sum(e0.elapsed_time(e1) for e0, e1 in evb)
-        # per-stage times of the batched form (events around each stage launch)
+        H.he_profile_collect()
+        # per-stage times of the batched form (events around each stage launch, same kernels)
         H.he_profile_enable(True)
         H.he_profile_collect()
         for _ in range(args.steps):
             flush.zero_()
-            H.he_batch_forward(batch, ins_p, outs_p, d_wsb.data_ptr(), sp)
+            H.he_batch_forward(batch, ins_p, outs_p, d_ws.data_ptr(), sp)
         torch.cuda.synchronize()
         H.he_profile_enable(False)
         stages_b = H.he_profile_collect()
-        # end to end through host buffers: the batch (he_batch_forward_host), and layer by layer
-        def step_host_batch():
-            H.he_batch_forward_host(batch, h_ins, h_outs, d_ins, d_outs, d_wsb.data_ptr(), sp)
-
-        e2e = {}
-        for name, fn in (("batch", step_host_batch), ("plain", step_host)):
-            for _ in range(2):
-                fn()
-            barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                fn()
-            torch.cuda.synchronize()
-            e2e[name] = time.perf_counter() - t0
-            barrier()
-        e2e_s, e2e_plain_s = e2e["batch"], e2e["plain"]
-    ms, ms_plain, e2e_s, e2e_plain_s = reduce_max([ms, ms_plain, e2e_s, e2e_plain_s], dev, world)
+        # end to end through host buffers: the batch (he_batch_forward_host)
+        for _ in range(2):
+            H.he_batch_forward_host(batch, h_ins, h_outs, d_ins, d_outs, d_ws.data_ptr(), sp)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            H.he_batch_forward_host(batch, h_ins, h_outs, d_ins, d_outs, d_ws.data_ptr(), sp)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+    for plan in plans:
+        H.he_conv_status(plan)
+    ms, ms_plain, e2e_s = reduce_max([ms, ms_plain, e2e_s], dev, world)
     if rank != 0:
         return
-    ms_step = ms / args.steps
-    layers_per_s = layers_per_second(world, n_layers, args.steps, ms / 1000)
-    # dominant stage and its roofline
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roofs = stage_rooflines(stages_b, counts, args.steps, peaks, N)
     top = max(stages_b, key=lambda k: stages_b[k][0])
-    top_ms, top_launches = stages_b[top]
-    per_launch_s = top_ms / 1000 / max(1, top_launches)
     mac_tc = all(H.he_conv_info(pl) == 2 for pl in plans)
-    if top == "mac" and mac_tc:
-        # tensor-core contraction: 10 fp16 flops per modMAC would put it at a few % of the tensor roof;
-        # the binding roof is HBM (every rotated residue read once, every output written once)
-        achieved = stage_bytes["mac"] * args.steps / (top_ms / 1000) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "k_mac_tc", "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "tensor_tflops_equiv": 10 * conv_mm * args.steps / (top_ms / 1000) / 1e12}
-    elif top == "mac":
-        # CUDA-core integer roof: 2 IMAD.WIDE per modMAC, 64 IMAD lanes per SM per clock issue
-        # at half rate for the 64-bit wide form -> 32 wide products per SM per clock
-        alu_peak = 152 * 2.07e9 * 32 / 2 / 1e12  # TmodMAC/s
-        achieved = conv_mm * args.steps / (top_ms / 1000) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TmodMAC/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_mac",
-                "peak_source": "derived: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 2 per modMAC"}
-    else:
-        achieved = stage_bytes[top] * args.steps / (top_ms / 1000) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": top, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roof["ms_per_launch"] = per_launch_s * 1000
-    src = kernel_source_digest()
-    kname = {"mac": "k_mac_tc" if mac_tc else "k_mac", "keyswitch": "k_keyswitch", "ntt_in": "k_ntt_inputs",
-             "ntt_out": "k_intt"}[top]
-    if (src.hexdigest().startswith(PROFILED_TRAFFIC["source"]) and kname in PROFILED_TRAFFIC
-            and args.workload == "resnet20"):
-        roof["traffic"] = PROFILED_TRAFFIC[kname]
-    roof["kernel"] = kname
-    roof["stage_share"] = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages_b.values())), 4)
-                           for k, v in stages_b.items()}
+    kname = {"mac": "k_mac_tc" if mac_tc else "k_mac_tc + k_mac", "keyswitch": "k_keyswitch",
+             "ntt_in": "k_ntt_inputs", "ntt_out": "k_intt"}
+    roof = {k: v for k, v in roofs[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
+    src = kernel_source_digest().hexdigest()
+    prof = PROFILED_TRAFFIC.get((wl, kname[top]))
+    roof["traffic"] = prof[1] if prof and src.startswith(prof[0]) else None
+    roof.update(kernel=kname[top], per_launch="one launch per stage and wave; achieved = algorithmic units of the "
+                "step / the kernel's event-timed time in the step",
+                peak_source="MEASURED_PEAKS.json " + ("hbm_gbs" if roof["unit"] == "GB/s" else
+                                                      "bf16_tflops_sustained (fp16 dense = bf16 dense)")
+                + " (of measured)")
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and args.workload == "resnet20":
-        times, desc = oracle_sample(reps=1)
-        cpu = {"value": 1.0 / times[0], "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": desc}
+    if world == 1 and not args.no_cpu_baseline:
+        layers = sorted({index[min(1, len(index) - 1)], index[-1]})
+        threads = host_cores()
+        est, spent, desc, parts = oracle_sample(wl, layers, threads)
+        # every layer of these stacks costs the oracle per input ciphertext and per term alike
+        # (one ring, one rotation set per kernel size), so the sampled layers' unit costs give the
+        # stack's layers/s over its own layer mix
+        cpu = {"value": len(layers) / sum(est), "unit": "layers/s", "cores": threads, "kind": "oracle",
+               "sample": desc, "sampled_layers": parts, "wall_seconds": round(spent, 1),
+               "estimated_seconds_per_sampled_layer": [round(e, 1) for e in est]}
     line = {
-        "metric": METRIC if args.workload == "resnet20" else METRIC.replace("ResNet-20", args.workload),
-        "value": layers_per_s, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "metric": METRIC, "value": layers_per_second(world, n_layers, args.steps, ms / 1000), "unit": "layers/s",
+        "n_gpus": world, "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": workload, "layers_per_step": n_layers, "images_per_gpu": images,
                    "batch_waves": H.he_batch_waves(batch),
                    "l2": "flushed before each timed step (256 MiB write)", "decomp_bits": info.w,
                    "parallelism": f"replicas x{world} (independent images, no collective)"},
-        "modmac_per_s": (conv_mm + ks_mm) * world * args.steps / (ms / 1000),
-        "modmac_per_step": {"conv": conv_mm, "keyswitch": ks_mm},
+        "modmac_per_s": (counts["conv_modmac"] + counts["ks_modmac"]) * world * args.steps / (ms / 1000),
+        "modmac_per_step": {"conv": counts["conv_modmac"], "keyswitch": counts["ks_modmac"]},
         "e2e": {"value": layers_per_second(world, n_layers, args.steps, e2e_s), "unit": "layers/s",
-                "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": out_bytes,
-                "call": "he_batch_forward_host (pinned host buffers, copies and graph replay in the timed region)",
-                "plain_per_layer": layers_per_second(world, n_layers, args.steps, e2e_plain_s)},
-        "gpu_launches": sum(v[1] for v in stages_b.values()),
+                "h2d_bytes_per_step": counts["in_bytes"], "d2h_bytes_per_step": counts["out_bytes"],
+                "call": "he_batch_forward_host (pinned host buffers, copies and graph replay in the timed region)"},
+        "gpu_launches": int(sum(v[1] for v in stages_b.values()) // max(1, args.steps) * args.steps),
         "roofline": roof,
+        "roofline_per_kernel": {kname[k]: v for k, v in roofs.items()},
         "cpu_baseline": cpu,
-        "clocks": clk_b.summary(),
+        "clocks": clocks_b,
+        "verified": verified,
         "form": f"batched: one launch per stage for all {n_layers} layers of each of {H.he_batch_waves(batch)} "
                 "workspace wave(s), replayed as a CUDA graph",
         "plain_per_layer": {"value": layers_per_second(world, n_layers, args.steps, ms_plain / 1000),
-                            "unit": "layers/s", "ms_per_step": ms_plain / args.steps,
-                            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-                            "clocks": clk.summary()},
+                            "unit": "layers/s", "ms_per_step": ms_plain / args.steps, "clocks": clocks_p},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages_b.items()},
+        "setup_seconds": round(setup_s, 1),
         "tuning": None if tuned is None else {"per_layer": tuned, "seconds": round(tune_s, 1),
                                               "method": "exhaustive timing of every packing x tile x schedule"},
     }
@@ -470,8 +584,8 @@ def run_learned(args):
     if not os.path.exists(CM.WEIGHTS):
         print(json.dumps({"mode": "learned", "unavailable": "no trained cost model weights in the package"}))
         return
-    _, n_ring, n_limbs, images, ws_limit, workload = WORKLOADS[args.workload]
-    specs = layer_descs(args.workload)
+    ws_limit, workload = WORKLOADS[args.workload]
+    specs, _, _, images = layer_specs(args.workload)
     model = CM.CostModel.load(CM.WEIGHTS)
     rings = CM.Rings()
     t0 = time.perf_counter()
@@ -482,7 +596,7 @@ def run_learned(args):
     groups = {}
     for i, c in enumerate(picks):
         groups.setdefault((c.N, c.L), []).append(i)
-    batches, keep = [], []
+    batches, keep, checks = [], [], []
     for (N, L), idx in sorted(groups.items()):
         p = rings.get(N, L)
         info = H.he_params_info(p)
@@ -493,9 +607,8 @@ def run_learned(args):
         plans, ins, outs = [], [], []
         for i in idx:
             s, c = specs[i], picks[i]
-            act = synth.activations((images, s["C_in"], s["H"], s["W"]), info.t, label=i)
-            wt = synth.weights((s["C_out"], 1 if s["depthwise"] else s["C_in"], s["kh"], s["kh"]), label=i)
-            cts = H.he_encrypt_image(p, sk, descs[i], act, synth.SEED_ENC, info)
+            act, wt, enc_seed = synth.stack_inputs(args.workload, i, info.t)
+            cts = H.he_encrypt_image(p, sk, descs[i], act, enc_seed, info)
             plans.append(H.he_conv_plan(p, gk, descs[i], wt, mac_groups=c.mac_groups, mac_impl=c.mac_impl,
                                         tc_rows=c.tc_rows))
             ins.append(torch.from_numpy(cts.reshape(-1).view(np.int64)).to(dev))
@@ -504,6 +617,7 @@ def run_learned(args):
         ws = torch.empty(H.he_batch_workspace_bytes(b) // 8 + 1, dtype=torch.int64, device=dev)
         batches.append((b, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], ws.data_ptr()))
         keep += [ins, outs, ws, plans, gk, sk]
+        checks.append((p, sk, idx, descs, outs))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
     def step():
@@ -526,8 +640,24 @@ def run_learned(args):
     for plan in [pl for k in keep[3::6] for pl in k]:
         H.he_conv_status(plan)
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / args.steps
+    # every output of every layer, as the last timed step left it, decrypted and compared with the
+    # plain convolution (float64 torch conv2d, exact at these sizes)
+    decrypt_ok = []
+    for p, sk, idx, descs, outs in checks:
+        info = H.he_params_info(p)
+        for i, o in zip(idx, outs):
+            s = specs[i]
+            act, wt, _ = synth.stack_inputs(args.workload, i, info.t)
+            dec = H.he_decrypt_image(p, sk, descs[i], o.cpu().numpy().view(np.uint64).reshape(-1, 2, info.L, info.N))
+            y = torch.nn.functional.conv2d(torch.from_numpy(act.astype(np.float64)),
+                                           torch.from_numpy(wt.astype(np.float64)), stride=s["stride"],
+                                           padding=(s["kh"] - 1) // 2, groups=s["C_in"] if s["depthwise"] else 1)
+            decrypt_ok.append((i, bool((dec == np.mod(y.numpy().astype(np.int64), info.t)).all())))
+    decrypt_ok.sort()
     print(json.dumps({
-        "mode": "learned", "metric": METRIC if args.workload == "resnet20" else METRIC.replace("ResNet-20", args.workload),
+        "mode": "learned", "metric": METRIC,
+        "decrypts_to_plain_conv": {"layers": len(decrypt_ok), "equal": sum(ok for _, ok in decrypt_ok),
+                                   "differ": [i for i, ok in decrypt_ok if not ok]},
         "value": len(specs) * 1000.0 / ms, "unit": "layers/s", "ms_per_step": ms, "steps": args.steps,
         "workload": workload.split(", N=")[0] + ", ring, packing, tile and MAC schedule per layer by the cost model",
         "rings": {f"{N},{L}": len(idx) for (N, L), idx in sorted(groups.items())}, "pick_seconds": round(pick_s, 2),
@@ -573,10 +703,10 @@ def run_ablation(args):
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
-    specs = layer_descs()
+    specs, n_ring, n_limbs, _ = layer_specs("resnet20")
     words = {}
     for name, paper, w, c_n, impl in ABLATION:
-        p = H.he_params_create(N_RING, L_LIMBS, limb_bits=LIMB_BITS, decomp_bits=w, est_mac_terms=64 * 9)
+        p = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=w, est_mac_terms=64 * 9)
         info = H.he_params_info(p)
         sk = H.he_keygen(p, synth.SEED_KEYS)
         descs = [H.conv_desc(**dict(s, c_n=c_n)) for s in specs]
@@ -639,7 +769,7 @@ def run_ablation(args):
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "est_noise_log2": info.est_noise_log2, "log2_delta": info.log2_delta,
             "decrypts_to_plain_conv": decrypt_ok, "words_equal_to_first_mac_form": same_words,
-            "clocks": clk.summary(), "workload": WORKLOAD.replace("c_n=2", f"c_n={c_n}")}), flush=True)
+            "clocks": clk.summary(), "workload": WORKLOADS["resnet20"][1].replace("c_n=2", f"c_n={c_n}")}), flush=True)
         H.he_batch_destroy(batch)
         for plan in plans:
             H.he_plan_destroy(plan)
@@ -657,8 +787,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hyena", choices=["hyena", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="resnet20", choices=sorted(WORKLOADS),
-                    help="the headline ResNet-20 stack, or the VGG-16 (8 images) or MobileNetV1 (32 images) stack")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="the headline VGG-16 stack (8 images), or the ResNet-20 (1 image) or MobileNetV1 "
+                         "(32 images) stack")
+    ap.add_argument("--layers", type=lambda v: [int(x) for x in v.split(",")], default=None,
+                    help="run only these layer indices of the stack (comma list), e.g. for profiler captures")
     ap.add_argument("--tuned", action="store_true",
                     help="pick each layer's packing, tile and MAC schedule by timing every candidate first")
     ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation", "learned"],

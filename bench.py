@@ -672,7 +672,10 @@ ABLATION = [
     ("eager, w=25", "Fig. latency (c): no latency optimisation", 25, 2, 3),
     ("eager, w=50", "Fig. latency (d): parameter selection only", 50, 2, 3),
     ("lazy CUDA-core, w=50", "Fig. latency (e): all optimisations", 50, 2, 1),
-    ("lazy tensor-core, w=50", "(e) with the contraction on tcgen05 (the default form)", 50, 2, 2),
+    ("lazy tensor-core, in-kernel fp16 conversion, w=50", "(e) on tcgen05, residues split into chunks by the MAC",
+     50, 2, 4),
+    ("lazy tensor-core, w=50", "(e) on tcgen05, operand images written by the key switch (the default form)",
+     50, 2, 2),
     ("lazy tensor-core, w=50, c_n=1", "padded convolution without output-channel packing (Sec. 2.4)", 50, 1, 2),
 ]
 

@@ -49,8 +49,16 @@ struct KP {
     const u64* itw_sh;
 };
 struct RotDev {
-    u32 galois, rot, key, pad;
+    u32 galois, rot, key, galois_inv;  // galois_inv = galois^-1 mod 2N
 };
+
+// g^-1 mod 2N for odd g (Newton's iteration for inverses modulo a power of two: each step
+// doubles the number of correct low bits; 5 steps from g (correct to 3 bits) reach 32 bits)
+inline u32 galois_inverse(u32 g, u32 N) {
+    u32 inv = g;
+    for (int i = 0; i < 5; i++) inv *= 2u - g * inv;
+    return inv & (2 * N - 1);
+}
 
 #define CUDA_OK(x)                                                                         \
     do {                                                                                   \
@@ -94,6 +102,11 @@ __device__ __forceinline__ u64 addq(u64 a, u64 b, u64 q) {
 // opposite order with psi^-rev(...) at the same position.
 constexpr int NTT_E = 16;
 constexpr int NTT_MAX_THREADS = 256;
+// N = 16384 needs 132 KB of shared memory per transform, so one CTA fits an SM: it runs with
+// 512 threads (two element sets each, 128 registers: the whole register file) to keep 16 warps
+// resident, as two 256-thread CTAs do for N = 8192
+constexpr int NTT_BIG_THREADS = 512;
+constexpr u32 NTT_BIG_N = 16384;
 
 __device__ __forceinline__ u32 spad(u32 i) { return i + (i >> 5); }  // one pad word per 32
 __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wsh, u64 q) {
@@ -274,6 +287,10 @@ struct LayerDev {
     u32 n_ct_in, n_ct_out, n_rot, rot_id, n_ks, K, Kpad, in_groups, out_groups, row_units, tc_rows, tc_rows_per_cta;
     u32 tmem_cols;             // TMEM columns of a tensor-core MAC CTA (power of two >= 5 rows)
     u32 r_slots, r_id;         // rotated copies stored per input ciphertext in R, and the identity's slot
+    // operand-image form (tensor-core MAC fed with ready fp16 chunk images, see k_keyswitch_img)
+    __half* A16;               // images [row_units][2][L][N/128][ktiles][5 chunks][128 slots x 32 terms]
+    const RotDev* rots_all;    // every rotation of the layer, identity included (key = ~0u)
+    u32 img, in_pad, n_rot_all, id_rot;  // in_pad = in_groups rounded up to 8; id_rot = the identity's index
 };
 
 enum { ST_NTT = 0, ST_KS = 1, ST_MAC = 2, ST_INTT = 3 };
@@ -301,8 +318,8 @@ __device__ __forceinline__ u32 find_layer(const Batch<MAXB>& B, int stage, u32 b
 // polynomial job/L, limb job%L into R[c][rot_id]; otherwise digit
 // dd = (job-2L)/L of c1 lifted into limb (job-2L)%L, into D[c][dd].  Digits
 // are below 2^w <= 2^s < 2q, inside the forward transform's input range.
-template <int MAXB>
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt_inputs(const __grid_constant__ Batch<MAXB> B, KP kp) {
+template <int MAXB, int NTHR, int MINB>
+__global__ void __launch_bounds__(NTHR, MINB) k_ntt_inputs(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ u64 sm[];
     const u32 li = find_layer(B, ST_NTT, blockIdx.x);
     const LayerDev& Ly = B.L[li];
@@ -358,8 +375,8 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_plain(u64* __restrict__
 }
 
 // Step 4: inverse NTT of the outputs.  Local block = (ciphertext, polynomial*L + limb).
-template <int MAXB>
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_intt(const __grid_constant__ Batch<MAXB> B, KP kp) {
+template <int MAXB, int NTHR, int MINB>
+__global__ void __launch_bounds__(NTHR, MINB) k_intt(const __grid_constant__ Batch<MAXB> B, KP kp) {
     extern __shared__ u64 sm[];
     const u32 li = find_layer(B, ST_INTT, blockIdx.x);
     const LayerDev& Ly = B.L[li];
@@ -416,10 +433,13 @@ __device__ __forceinline__ void mad_wide_u(u64& acc, u32 a, u32 b) {
     asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-// Step 2: hoisted key switch.  Thread = NTT slot x; local block = (rotation, limb, slot tile).
+// Step 2: hoisted key switch.  Local block = (rotation, limb, slot tile).
 // The NTT slot x holds the evaluation at psi^e with e = 2 rev(x) + 1, so
-// sigma_g reads slot rev((g e mod 2N - 1)/2).  The key values of (x, limb)
-// stay in registers across all input ciphertexts of the layer.
+// sigma_g(a)[x] = a[src(x)] with src(x) = rev((g e(x) mod 2N - 1)/2).  A thread owns a
+// SOURCE slot y of the tile and writes the destination x = src^-1(y) = rev((g^-1 e(y) mod
+// 2N - 1)/2): its loads of the digit and c0 transforms are coalesced, only its two stores
+// are permuted (within one aligned tile, since the map keeps the tile).  The key values of
+// (x, limb) stay in registers across all input ciphertexts of the layer.
 constexpr int KS_THREADS = 256;
 template <int LL, int MAXB>
 __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant__ Batch<MAXB> B, KP kp) {
@@ -429,12 +449,12 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
     const u32 xt_n = N / KS_THREADS;
     const u32 local = blockIdx.x - B.start[ST_KS][li];
     const u32 xt = local % xt_n, k = (local / xt_n) % L, r = local / (xt_n * L);
-    const u32 x = xt * KS_THREADS + threadIdx.x;
+    const u32 src = xt * KS_THREADS + threadIdx.x;
     const RotDev rd = Ly.rots[r];
     const LimbC m = kp.limb[k];
-    const u32 e = 2 * (__brev(x) >> (32 - logN)) + 1;
-    const u32 e2 = (u32)(((u64)e * rd.galois) & (2ull * N - 1));
-    const u32 src = __brev((e2 - 1) >> 1) >> (32 - logN);
+    const u32 e = 2 * (__brev(src) >> (32 - logN)) + 1;
+    const u32 e2 = (u32)(((u64)e * rd.galois_inv) & (2ull * N - 1));
+    const u32 x = __brev((e2 - 1) >> 1) >> (32 - logN);
     // keys split at bit 25, held in registers for all input ciphertexts: a product of two
     // residues below 2^s is (a1 2^25 + a0)(b1 2^25 + b0), four 32x32 -> 64-bit multiply-adds
     // into three 64-bit partial sums.  With s <= 54 and at most 16 digit terms the high halves
@@ -462,7 +482,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
 #pragma unroll
             for (int dd = 0; dd < LL; dd++) {
-                const u64 dv = Dc[(size_t)dd * L * N];
+                const u64 dv = __ldg(Dc + (size_t)dd * L * N);
                 const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
                 mad_wide_u(lo0, dl, k0l[dd]);
                 mad_wide_u(hi0, dh, k0h[dd]);
@@ -474,7 +494,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             mid0 -= lo0 + hi0;
             mid1 -= lo1 + hi1;
             u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
-            lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];  // + sigma(c0); lo stays below 2^57
+            lo0 += __ldg(Rc + (size_t)r_id * ctw + (size_t)k * N + src);  // + sigma(c0); lo stays below 2^57
             u64 r0, r1;
             if (m.delta) {
                 r0 = fold_reduce50(lo0, mid0, hi0, m);
@@ -495,7 +515,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
         u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
 #pragma unroll
         for (int dd = 0; dd < LL; dd++) {
-            const u64 dv = Dc[(size_t)dd * L * N];
+            const u64 dv = __ldg(Dc + (size_t)dd * L * N);
             const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
             mad_wide_u(lo0, dl, k0l[dd]);
             mad_wide_u(mid0, dl, k0h[dd]);
@@ -507,7 +527,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
             mad_wide_u(hi1, dh, k1h[dd]);
         }
         u64* Rc = Ly.R + (size_t)c * r_slots * ctw;
-        lo0 += Rc[(size_t)r_id * ctw + (size_t)k * N + src];
+        lo0 += __ldg(Rc + (size_t)r_id * ctw + (size_t)k * N + src);
         const u64 r0 = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
         const u64 r1 = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
         __stcs(reinterpret_cast<unsigned long long*>(Rc + (size_t)rd.rot * ctw + (size_t)k * N + x), r0);
@@ -1035,6 +1055,385 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     }
 }
 
+// ------------------------------------------------------------------ operand-image form
+// The key switch writes the rotated residues straight into the shared-memory image the
+// tensor-core MMA reads (five fp16 chunks per residue, K-major core matrices), so the MAC is
+// a pure copy -> MMA pipeline and a residue is split into chunks once, not once per row tile.
+//
+// Term order of the image form: kk = rot * in_pad + j (rotation-major; in_pad = in_groups
+// rounded up to 8, the padded terms carry zero scalars), so eight consecutive terms of one
+// slot are eight input ciphertexts of one rotation: one 16-byte store per chunk.
+// Image of (row unit, polynomial, limb, slot tile nt, K tile kt): 5 chunks x 8 KB, chunk c at
+// byte c * 8192, element (slot row m, term kl) at (m >> 3) * 512 + (kl >> 3) * 128 + (m & 7) * 16
+// + (kl & 7) * 2, the layout smem_desc describes (LBO 128 B, SBO 512 B).
+constexpr int KSI_THREADS = 128;          // one 128-slot tile per block, thread = destination slot
+constexpr u32 KSI_JB = 32;                // input ciphertexts per block (four groups of eight)
+constexpr u32 IMG_HALVES = TC_CHUNKS * TC_MTILE * TC_KTILE;  // 20480 halves = 40 KB per image
+
+// Step 2, operand-image form.  Local block = (row unit, block of 32 input ciphertexts, rotation,
+// limb, slot tile), the tile varying fastest, so that the blocks resident together share the
+// digit transforms of the same input ciphertexts in L2.  As in k_keyswitch, a thread owns a
+// SOURCE slot y of the tile (coalesced loads) and produces the destination x = src^-1(y).  The
+// chunks of eight input ciphertexts go to a shared-memory copy of the tile's image rows (row
+// x & 127), which the block then writes out in 16-byte pieces, row by row.  The identity
+// rotation converts NTT(c0), NTT(c1) as they are.
+constexpr int KSI_JH = 4;  // input ciphertexts computed per pass (two passes per eight)
+
+__device__ __forceinline__ uint2 chunk_pack4(const u64 (&v)[KSI_JH], int c) {
+    u32 w[2];
+#pragma unroll
+    for (int e = 0; e < KSI_JH; e += 2) {
+        u32 a, b;
+        const u32 la = (u32)v[e], ha = (u32)(v[e] >> 32), lb = (u32)v[e + 1], hb = (u32)(v[e + 1] >> 32);
+        switch (c) {
+            case 0: a = la, b = lb; break;
+            case 1: a = la >> 10, b = lb >> 10; break;
+            case 2: a = la >> 20, b = lb >> 20; break;
+            case 3: a = __funnelshift_r(la, ha, 30), b = __funnelshift_r(lb, hb, 30); break;
+            default: a = ha >> 8, b = hb >> 8; break;
+        }
+        // fp16 bits of 1024 + x are 0x6400 | x (x < 1024); subtracting 1536 gives x - 512 exactly
+        const u32 packed = (a & 0x3FFu) | ((b << 16) & 0x3FF0000u) | 0x64006400u;
+        __half2 h = *reinterpret_cast<const __half2*>(&packed);
+        h = __hsub2(h, __float2half2_rn(1536.0f));
+        w[e / 2] = *reinterpret_cast<u32*>(&h);
+    }
+    return make_uint2(w[0], w[1]);
+}
+
+template <int LL, int MAXB>
+__global__ void __launch_bounds__(KSI_THREADS, 6) k_keyswitch_img(const __grid_constant__ Batch<MAXB> B, KP kp) {
+    // image rows of eight terms: [polynomial][chunk][slot row][8 halves]
+    __shared__ __align__(16) uint4 rows[2][TC_CHUNKS][TC_MTILE];
+    const u32 li = find_layer(B, ST_KS, blockIdx.x);
+    const LayerDev& Ly = B.L[li];
+    const u32 N = kp.N, L = kp.L, logN = kp.logN, NT = N / TC_MTILE;
+    const u32 JC = (Ly.in_pad + KSI_JB - 1) / KSI_JB;
+    u32 local = blockIdx.x - B.start[ST_KS][li];
+    const u32 nt = local % NT;
+    local /= NT;
+    const u32 k = local % L;
+    local /= L;
+    const u32 r = local % Ly.n_rot_all;
+    local /= Ly.n_rot_all;
+    const u32 jc = local % JC, ru = local / JC;
+    const u32 tid = threadIdx.x;
+    const u32 src = nt * TC_MTILE + tid;
+    const RotDev rd = Ly.rots_all[r];
+    const LimbC m = kp.limb[k];
+    const bool ident = r == Ly.id_rot;
+    const u32 e = 2 * (__brev(src) >> (32 - logN)) + 1;
+    const u32 e2 = (u32)(((u64)e * rd.galois_inv) & (2ull * N - 1));
+    const u32 x = __brev((e2 - 1) >> 1) >> (32 - logN);
+    // the destinations of a source tile fill one aligned destination tile xt (sigma maps aligned
+    // tiles onto aligned tiles), so xt is the same for every thread of the block
+    const u32 xl = x & (TC_MTILE - 1), xt = x / TC_MTILE;
+    const size_t ctw = 2ull * L * N;
+    const u32 ktiles = Ly.Kpad / TC_KTILE;
+    __half* const img0 = Ly.A16 + ((((size_t)ru * 2 + 0) * L + k) * NT + xt) * ktiles * IMG_HALVES;
+    const size_t p_stride = (size_t)L * NT * ktiles * IMG_HALVES;
+    const u32 row_off = (tid >> 3) * 256 + (tid & 7) * 8;  // halves: image row tid within a chunk
+    // keys of the destination x split at bit 25 (see k_keyswitch), in registers for the block
+    u32 k0l[LL], k0h[LL], k1l[LL], k1h[LL];
+    if (!ident) {
+        const u64* kb = Ly.ksk + (size_t)rd.key * LL * 2 * L * N;
+#pragma unroll
+        for (int dd = 0; dd < LL; dd++) {
+            const u64 a = __ldg(kb + (((size_t)dd * 2 + 0) * L + k) * N + x);
+            const u64 b = __ldg(kb + (((size_t)dd * 2 + 1) * L + k) * N + x);
+            k0l[dd] = (u32)(a & 0x1FFFFFFu), k0h[dd] = (u32)(a >> 25);
+            k1l[dd] = (u32)(b & 0x1FFFFFFu), k1h[dd] = (u32)(b >> 25);
+        }
+    }
+    auto store_rows = [&](u32 kk) {
+        // the block's image rows of terms kk .. kk+7 of both polynomials, row tid, 16 bytes a chunk
+        const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
+        __half* d0 = img0 + (size_t)kt * IMG_HALVES + (kl >> 3) * 64 + row_off;
+#pragma unroll
+        for (int c = 0; c < TC_CHUNKS; c++) {
+            __stcs(reinterpret_cast<uint4*>(d0 + c * (TC_MTILE * TC_KTILE)), rows[0][c][tid]);
+            __stcs(reinterpret_cast<uint4*>(d0 + p_stride + c * (TC_MTILE * TC_KTILE)), rows[1][c][tid]);
+        }
+    };
+    const u32 j_end = min(Ly.in_pad, (jc + 1) * KSI_JB);
+    for (u32 j0 = jc * KSI_JB; j0 < j_end; j0 += 8) {
+#pragma unroll 1
+        for (u32 h = 0; h < 8; h += KSI_JH) {
+            u64 v0[KSI_JH], v1[KSI_JH];
+#pragma unroll
+            for (int jj = 0; jj < KSI_JH; jj++) {
+                const u32 j = j0 + h + jj;
+                v0[jj] = v1[jj] = 0;
+                if (j >= Ly.in_groups) continue;  // padded term: zero scalars, any finite operand
+                const u32 c = ru * Ly.in_groups + j;
+                const u64* Rid = Ly.R + ((size_t)c * Ly.r_slots + Ly.r_id) * ctw + (size_t)k * N;
+                if (ident) {
+                    v0[jj] = __ldg(Rid + src);
+                    v1[jj] = __ldg(Rid + (size_t)L * N + src);
+                    continue;
+                }
+                const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
+                u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
+                if (m.sm1 == 49) {
+#pragma unroll
+                    for (int dd = 0; dd < LL; dd++) {
+                        const u64 dv = __ldg(Dc + (size_t)dd * L * N);
+                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
+                        mad_wide_u(lo0, dl, k0l[dd]);
+                        mad_wide_u(hi0, dh, k0h[dd]);
+                        mad_wide_u(mid0, ds, k0l[dd] + k0h[dd]);
+                        mad_wide_u(lo1, dl, k1l[dd]);
+                        mad_wide_u(hi1, dh, k1h[dd]);
+                        mad_wide_u(mid1, ds, k1l[dd] + k1h[dd]);
+                    }
+                    mid0 -= lo0 + hi0;
+                    mid1 -= lo1 + hi1;
+                    lo0 += __ldg(Rid + src);  // + sigma(c0)
+                    if (m.delta) {
+                        v0[jj] = fold_reduce50(lo0, mid0, hi0, m);
+                        v1[jj] = fold_reduce50(lo1, mid1, hi1, m);
+                    } else {
+                        v0[jj] = bred_split50(lo0, mid0, hi0, m);
+                        v1[jj] = bred_split50(lo1, mid1, hi1, m);
+                    }
+                } else {
+#pragma unroll
+                    for (int dd = 0; dd < LL; dd++) {
+                        const u64 dv = __ldg(Dc + (size_t)dd * L * N);
+                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                        mad_wide_u(lo0, dl, k0l[dd]);
+                        mad_wide_u(mid0, dl, k0h[dd]);
+                        mad_wide_u(mid0, dh, k0l[dd]);
+                        mad_wide_u(hi0, dh, k0h[dd]);
+                        mad_wide_u(lo1, dl, k1l[dd]);
+                        mad_wide_u(mid1, dl, k1h[dd]);
+                        mad_wide_u(mid1, dh, k1l[dd]);
+                        mad_wide_u(hi1, dh, k1h[dd]);
+                    }
+                    lo0 += __ldg(Rid + src);
+                    v0[jj] = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
+                    v1[jj] = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
+                }
+            }
+            // chunks of these four terms into the shared image rows of destination x
+#pragma unroll
+            for (int c = 0; c < TC_CHUNKS; c++) {
+                reinterpret_cast<uint2*>(&rows[0][c][xl])[h / KSI_JH] = chunk_pack4(v0, c);
+                reinterpret_cast<uint2*>(&rows[1][c][xl])[h / KSI_JH] = chunk_pack4(v1, c);
+            }
+        }
+        __syncthreads();
+        store_rows(r * Ly.in_pad + j0);
+        __syncthreads();
+    }
+    // the terms past n_rot in_pad that fill the last K tile carry zero scalars; their operands must
+    // still be finite numbers (a NaN times 0 is NaN), so the last block of the last rotation zeroes them
+    if (r + 1 == Ly.n_rot_all && jc + 1 == JC) {
+        for (int c = 0; c < TC_CHUNKS; c++) rows[0][c][tid] = rows[1][c][tid] = make_uint4(0, 0, 0, 0);
+        for (u32 kk = Ly.n_rot_all * Ly.in_pad; kk < Ly.Kpad; kk += 8) store_rows(kk);
+    }
+}
+
+// Step 3, operand-image form: the tensor-core contraction of k_mac_tc with the operands copied
+// ready-made.  Warp 0 issues one bulk copy of the 40 KB image and one of the scalar tile per
+// K tile into a ring of TCI_STAGES stages; warp 1 (lane 0) issues the MMAs; warps 4..15 run the
+// epilogue of each accumulation segment (as in k_mac_tc).  Barriers (all bounded waits):
+//   full[s]    image and scalars of stream position g landed in stage s = g % TCI_STAGES
+//   empty[s]   MMAs of stage s done (commit)
+//   acc_full   last MMA of an accumulation segment done (commit)
+//   acc_empty  accumulators read by every epilogue warp
+constexpr int TCI_STAGES = 4;
+constexpr u32 TCI_A_BYTES = IMG_HALVES * 2;                       // 40 KB
+constexpr u32 TCI_B_OFF = TCI_STAGES * TCI_A_BYTES;               // scalar tiles after the images
+constexpr u32 TCI_BAR_OFF = TCI_B_OFF + TCI_STAGES * TC_B_BYTES;
+constexpr u32 TCI_SMEM_BYTES = TCI_BAR_OFF + 128;                 // 2 TCI_STAGES + 2 mbarriers, TMEM slot, flag
+static_assert(TCI_SMEM_BYTES <= 227 * 1024, "operand-image MAC exceeds shared memory");
+
+template <bool PACKED, int MAXB>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant__ Batch<MAXB> B, KP kp, u32 tmem_cols) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    constexpr int NR = PACKED ? 2 : 1;
+    constexpr int NB = 2 * TCI_STAGES + 2;
+    const u32 N = kp.N, L = kp.L, NT = N / TC_MTILE;
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    u64* bars = reinterpret_cast<u64*>(tsm + TCI_BAR_OFF);
+    // barrier indices: full 0..S-1, empty S..2S-1, acc_full 2S, acc_empty 2S+1
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    constexpr int FULL = 0, EMPTY = TCI_STAGES, ACC_FULL = 2 * TCI_STAGES, ACC_EMPTY = 2 * TCI_STAGES + 1;
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + TCI_BAR_OFF + NB * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + TCI_BAR_OFF + NB * 8 + 4);
+
+    if (tid == 0) {
+        for (int i = 0; i < TCI_STAGES; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(FULL + i)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_FULL)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_EMPTY)), "r"(TC_EPI));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const u32 tmem = *tmem_slot;
+
+    auto wait = [&](int i, u32 parity) -> bool {
+        return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, nullptr);
+    };
+    auto arrive = [&](int i) { asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(i)) : "memory"); };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- copies
+        u32 g = 0;
+        TcItem it;
+        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 bbytes = Ly.tc_rows_per_cta * TC_KTILE * 2, ktiles = Ly.Kpad / TC_KTILE;
+            const u32 mt = it.row0 / Ly.tc_rows_per_cta, nt = it.n0 / TC_MTILE;
+            const __half* abase = Ly.A16 + ((((size_t)it.ru * 2 + it.p) * L + it.k) * NT + nt) * ktiles * IMG_HALVES;
+            bool ok = true;
+            for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                const u32 s = g % TCI_STAGES;
+                const bool fr = g < TCI_STAGES || wait(EMPTY + s, ((g / TCI_STAGES) - 1) & 1);
+                if (!__all_sync(0xffffffffu, fr)) { ok = false; break; }
+                if (lane == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)),
+                                 "r"(TCI_A_BYTES + bbytes)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(tsm + s * TCI_A_BYTES)),
+                        "l"(abase + (size_t)t * IMG_HALVES), "r"(TCI_A_BYTES), "r"(bar(FULL + s))
+                        : "memory");
+                    const __half* bsrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (Ly.tc_rows_per_cta * TC_KTILE);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(tsm + TCI_B_OFF + s * TC_B_BYTES)),
+                        "l"(bsrc), "r"(bbytes), "r"(bar(FULL + s))
+                        : "memory");
+                }
+                __syncwarp();
+            }
+            if (!ok || *abort_flag) break;
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMAs (lane 0)
+        if (lane == 0) {
+            u32 g = 0, unit = 0;  // unit = (item, segment): one accumulation in TMEM
+            TcItem it;
+            for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+                const u32 idesc = tc_idesc(TC_MTILE, it.nrows);
+                bool okk = true;
+                for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                    const u32 s = g % TCI_STAGES, tseg = t % TC_SEG_TILES;
+                    if (tseg == 0) {
+                        if (unit > 0 && !wait(ACC_EMPTY, (unit - 1) & 1)) { okk = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                    }
+                    if (!wait(FULL + s, (g / TCI_STAGES) & 1)) { okk = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const u32 a_base = smem_u32(tsm + s * TCI_A_BYTES), b_base = smem_u32(tsm + TCI_B_OFF + s * TC_B_BYTES);
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+#pragma unroll
+                        for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                            const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
+                            const u64 bd = smem_desc(b_base + ks * 256);
+                            const u32 acc = (tseg > 0 || ks > 0) ? 1u : 0u;
+                            const u32 dt = tmem + (u32)(c * it.nrows);
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(EMPTY + s)));
+                    if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(ACC_FULL)));
+                        unit++;
+                    }
+                }
+                if (!okk) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------------- epilogue
+        u32 unit = 0;
+        TcItem it;
+        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 n_seg = (it.n_tiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
+            bool okk = true;
+            for (u32 seg = 0; seg < n_seg; seg++) {
+                if (!__all_sync(0xffffffffu, wait(ACC_FULL, unit & 1))) { okk = false; break; }
+                unit++;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const u32 sp = warp & 3, third = (warp - 4) >> 2;
+                const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
+                const LimbC m = kp.limb[k];
+                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+                for (u32 cb = third * 8; cb < nrows; cb += 24) {
+                    u32 d[TC_CHUNKS][8];
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+                        const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
+                                       "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
+                                     : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    u64 red[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const long long b = Ly.bias[(size_t)seg * Ly.tc_rows + row0 + cb + j];  // 512 S of the segment
+                        const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
+                        const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
+                        const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+                        red[j] = bred128((u128)a, m);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; j += NR) {
+                        const u32 row = row0 + cb + j;
+                        const u32 gg = row / NR;
+                        if (gg >= Ly.out_groups) continue;
+                        u64 out = red[j];
+                        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                        u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
+                        if (seg > 0) out = addq(out, *o, m.q);  // this thread stored the earlier segments
+                        *o = out;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) arrive(ACC_EMPTY);  // accumulators free
+            }
+            if (!okk) break;
+        }
+    }
+    // drain: after an abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    if (*abort_flag && tid == 0) {
+        for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
+        for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+    }
+}
+
 // ------------------------------------------------------------------ profiling
 struct Prof {
     std::mutex mu;
@@ -1189,10 +1588,11 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
-    bool tc = false, packed = false, dw = false, eager = false;
+    bool tc = false, packed = false, dw = false, eager = false, img = false;
     u32 gt = 8;
     bool operator==(const MacVariant& o) const {
-        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && (tc || eager || gt == o.gt);
+        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img &&
+               (tc || eager || gt == o.gt);
     }
 };
 
@@ -1206,7 +1606,9 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
     const u32 L = p->L, N = p->N;
     switch (stage) {
         case ST_NTT: return d.n_ct_in * (L + (p->l == 1 ? 0 : L) + L * p->l * L);
-        case ST_KS: return d.n_ks * L * (N / KS_THREADS);
+        case ST_KS:
+            if (d.img) return d.row_units * ((d.in_pad + KSI_JB - 1) / KSI_JB) * d.n_rot_all * L * (N / TC_MTILE);
+            return d.n_ks * L * (N / KS_THREADS);
         case ST_MAC:
             if (s.mv.eager) return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + 3) / 4);
             if (s.mv.tc) return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta);
@@ -1216,15 +1618,17 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
 }
 
 template <int LL, int MAXB>
-void ks_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
-    k_keyswitch<LL, MAXB><<<blocks, KS_THREADS, 0, s>>>(B, kp);
+void ks_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s, bool img) {
+    if (img) k_keyswitch_img<LL, MAXB><<<blocks, KSI_THREADS, 0, s>>>(B, kp);
+    else k_keyswitch<LL, MAXB><<<blocks, KS_THREADS, 0, s>>>(B, kp);
 }
 
 template <int MAXB>
-void launch_keyswitch_b(const he_params* p, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+void launch_keyswitch_b(const he_params* p, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s,
+                        bool img) {
     switch (p->L * p->l) {
 #define KS_CASE(v) \
-    case v: ks_launch<v, MAXB>(blocks, B, kp, s); break;
+    case v: ks_launch<v, MAXB>(blocks, B, kp, s, img); break;
         KS_CASE(1) KS_CASE(2) KS_CASE(3) KS_CASE(4) KS_CASE(5) KS_CASE(6) KS_CASE(7) KS_CASE(8) KS_CASE(9)
             KS_CASE(10) KS_CASE(12) KS_CASE(14) KS_CASE(15) KS_CASE(16)
 #undef KS_CASE
@@ -1250,6 +1654,16 @@ void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const 
         u32 cols = 32;
         for (u32 i = 0; i < B.n; i++) cols = std::max(cols, B.L[i].tmem_cols);
         const u32 grid = std::min(blocks, (u32)sm_count());
+        if (mv.img) {
+            if (mv.packed) {
+                allow_smem(k_mac_img<true, MAXB>, TCI_SMEM_BYTES);
+                k_mac_img<true, MAXB><<<grid, TC_THREADS, TCI_SMEM_BYTES, s>>>(B, kp, cols);
+            } else {
+                allow_smem(k_mac_img<false, MAXB>, TCI_SMEM_BYTES);
+                k_mac_img<false, MAXB><<<grid, TC_THREADS, TCI_SMEM_BYTES, s>>>(B, kp, cols);
+            }
+            return;
+        }
         if (mv.packed) {
             allow_smem(k_mac_tc<true, MAXB>, TC_SMEM_BYTES);
             k_mac_tc<true, MAXB><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(B, kp, cols);
@@ -1302,13 +1716,18 @@ void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector
         switch (stage) {
             case ST_NTT: {
                 const size_t smem = ntt_smem_bytes(p->N);
-                allow_smem(k_ntt_inputs<MAXB>, smem);
-                k_ntt_inputs<MAXB><<<total, ntt_threads(p->N), smem, s>>>(B, kp);
+                if (p->N >= NTT_BIG_N) {
+                    allow_smem(k_ntt_inputs<MAXB, NTT_BIG_THREADS, 1>, smem);
+                    k_ntt_inputs<MAXB, NTT_BIG_THREADS, 1><<<total, NTT_BIG_THREADS, smem, s>>>(B, kp);
+                } else {
+                    allow_smem(k_ntt_inputs<MAXB, NTT_MAX_THREADS, 2>, smem);
+                    k_ntt_inputs<MAXB, NTT_MAX_THREADS, 2><<<total, ntt_threads(p->N), smem, s>>>(B, kp);
+                }
                 check_launch("k_ntt_inputs");
                 break;
             }
             case ST_KS:
-                launch_keyswitch_b<MAXB>(p, total, B, kp, s);
+                launch_keyswitch_b<MAXB>(p, total, B, kp, s, layers[c0]->dev.img != 0);
                 check_launch("k_keyswitch");
                 break;
             case ST_MAC:
@@ -1317,8 +1736,13 @@ void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector
                 break;
             default: {
                 const size_t smem = ntt_smem_bytes(p->N);
-                allow_smem(k_intt<MAXB>, smem);
-                k_intt<MAXB><<<total, ntt_threads(p->N), smem, s>>>(B, kp);
+                if (p->N >= NTT_BIG_N) {
+                    allow_smem(k_intt<MAXB, NTT_BIG_THREADS, 1>, smem);
+                    k_intt<MAXB, NTT_BIG_THREADS, 1><<<total, NTT_BIG_THREADS, smem, s>>>(B, kp);
+                } else {
+                    allow_smem(k_intt<MAXB, NTT_MAX_THREADS, 2>, smem);
+                    k_intt<MAXB, NTT_MAX_THREADS, 2><<<total, ntt_threads(p->N), smem, s>>>(B, kp);
+                }
                 check_launch("k_intt");
             }
         }
@@ -1346,8 +1770,12 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
     }
     mark(1);
     {
+        // the operand-image layers and the others have different key-switch kernels
         StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
-        go(ST_KS, all);
+        std::vector<const StageLayer*> grp[2];
+        for (auto& l : layers) grp[l.dev.img ? 1 : 0].push_back(&l);
+        for (auto& g : grp)
+            if (!g.empty()) go(ST_KS, g);
     }
     mark(2);
     if (do_mac) {
@@ -1424,17 +1852,18 @@ struct he_plan {
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
     bool packed = false, dw = false;
     u32 mac_groups = 8;
-    bool use_tc = false, eager = false;
-    u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0;
+    bool use_tc = false, eager = false, img = false;
+    u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
+    RotDev* d_rots_all = nullptr;
     int16_t* d_scal = nullptr;
     u64* d_pk = nullptr;
     __half* d_sc16 = nullptr;
     int* d_bias = nullptr;
     int* d_err = nullptr;
     u32 tmem_cols = 0, r_slots = 0, r_id = 0;
-    size_t off_R = 0, off_D = 0, off_O = 0, ws_bytes = 0;
+    size_t off_R = 0, off_D = 0, off_O = 0, off_A = 0, ws_bytes = 0;
     KP kp{};
     ~he_plan() {
         int cur = -1;
@@ -1442,6 +1871,7 @@ struct he_plan {
         cudaSetDevice(device);
         cudaFree(d_ksk);
         cudaFree(d_rots);
+        cudaFree(d_rots_all);
         cudaFree(d_scal);
         cudaFree(d_pk);
         cudaFree(d_sc16);
@@ -1463,8 +1893,11 @@ struct he_plan {
         L.K = K, L.Kpad = tc_kpad, L.in_groups = lay.in_groups, L.out_groups = lay.out_groups;
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
         L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
-        if (use_tc) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
+        L.img = img, L.in_pad = in_pad, L.n_rot_all = n_rot, L.id_rot = rot_id, L.rots_all = d_rots_all;
+        L.A16 = img ? (__half*)(ws + off_A) : nullptr;
+        if (use_tc && !img) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
+        s.mv.img = img;
         return s;
     }
 };
@@ -1486,18 +1919,20 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     const u32 taps = d->kh * d->kh;
     // rotations that need a key switch, grouped by distinct Galois element
     std::vector<u32> gal;
-    std::vector<RotDev> rots;
+    std::vector<RotDev> rots, rots_all;
     bool have_id = false;
     for (u32 r = 0; r < rl.size(); r++) {
         if (rl[r].galois == 1) {
             P->rot_id = r;
             have_id = true;
+            rots_all.push_back({1u, r, ~0u, 1u});
             continue;
         }
         auto it = std::find(gal.begin(), gal.end(), rl[r].galois);
         u32 key = (u32)(it - gal.begin());
         if (it == gal.end()) gal.push_back(rl[r].galois);
-        rots.push_back({rl[r].galois, r, key, 0});
+        rots.push_back({rl[r].galois, r, key, galois_inverse(rl[r].galois, p->N)});
+        rots_all.push_back(rots.back());
     }
     if (!have_id) fail(HE_EINVAL, "internal: identity rotation missing");
     std::vector<const std::vector<u64>*> keys;
@@ -1560,12 +1995,16 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     bool limbs_fit = true;
     for (u64 qi : p->q) limbs_fit = limbs_fit && qi < (1ull << (10 * TC_CHUNKS));
     const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && limbs_fit;
-    if (impl == 2 && !tc_ok)
+    if ((impl == 2 || impl == 4) && !tc_ok)
         fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
-    if (impl > 3) fail(HE_EINVAL, "mac_impl must be 0..3");
+    if (impl > 4) fail(HE_EINVAL, "mac_impl must be 0..4");
     P->eager = impl == 3;
     P->use_tc = tc_ok && impl != 1 && impl != 3;
+    // tensor-core layers take their operands as images written by the key switch, unless the
+    // in-kernel conversion form is asked for (mac_impl 4)
+    P->img = P->use_tc && impl != 4;
+    P->in_pad = (lay.in_groups + 7) / 8 * 8;
     if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
     const u32 tc_rows_req = tune ? tune->tc_rows : 0;
     if (tc_rows_req && (tc_rows_req % 16 || tc_rows_req > (u32)TC_NMAX))
@@ -1587,6 +2026,8 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         CUDA_OK(cudaMalloc(&P->d_rots, rots.size() * sizeof(RotDev)));
         CUDA_OK(cudaMemcpy(P->d_rots, rots.data(), rots.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
     }
+    CUDA_OK(cudaMalloc(&P->d_rots_all, rots_all.size() * sizeof(RotDev)));
+    CUDA_OK(cudaMemcpy(P->d_rots_all, rots_all.data(), rots_all.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
     CUDA_OK(cudaMalloc(&P->d_scal, sc.size() * sizeof(int16_t)));
     CUDA_OK(cudaMemcpy(P->d_scal, sc.data(), sc.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
     // NTT(P_k): P_k = kh (X^(N/4) + X^(3N/4)) lifted into every limb
@@ -1607,7 +2048,9 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 rows = lay.out_groups * NR;
         P->tc_rows = (rows + 15) / 16 * 16;
         P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
-        P->tc_kpad = (P->K + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
+        // terms: kk = j n_rot + rot for the in-kernel conversion form, rot in_pad + j for the image form
+        const u32 k_terms = P->img ? P->n_rot * P->in_pad : P->K;
+        P->tc_kpad = (k_terms + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
         // scalar tiles stored as the exact shared-memory image the MMA reads (K-major, no
         // swizzle), one block of rows_per_cta x 32 terms per (row tile, K tile)
         const u32 rpc = P->tc_rows_per_cta, ktiles = P->tc_kpad / TC_KTILE;
@@ -1619,8 +2062,9 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         for (u32 g = 0; g < lay.out_groups; g++)
             for (u32 r = 0; r < NR; r++) {
                 const u32 row = g * NR + r, mt = row / rpc, rl = row % rpc;
-                for (u32 kk = 0; kk < P->K; kk++) {
-                    int v = sc[((size_t)g * NR + r) * P->K + kk];
+                for (u32 kk0 = 0; kk0 < P->K; kk0++) {
+                    int v = sc[((size_t)g * NR + r) * P->K + kk0];
+                    const u32 kk = P->img ? (kk0 % P->n_rot) * P->in_pad + kk0 / P->n_rot : kk0;
                     const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
                     const size_t byte = ((size_t)mt * ktiles + kt) * rpc * TC_KTILE * 2 +
                                         (rl >> 3) * TC_SBO + (kl >> 3) * 128 + (rl & 7) * 16 + (kl & 7) * 2;
@@ -1639,14 +2083,20 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         P->tmem_cols = cols;
     }
     CUDA_OK(cudaStreamSynchronize(s));
-    // workspace: R [n_ct_in][n_rot][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N]
-    P->r_slots = P->n_rot;
-    P->r_id = P->rot_id;
+    // workspace: R [n_ct_in][r_slots][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N] and, for
+    // the image form, A [row_units][2][L][N/128][Kpad/32] operand images of 40 KB (R then holds only
+    // the identity rotation, NTT(c0) and NTT(c1))
+    P->r_slots = P->img ? 1 : P->n_rot;
+    P->r_id = P->img ? 0 : P->rot_id;
     const size_t ctw = 2ull * p->L * p->N;
     P->off_R = 0;
     P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);
     P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
-    P->ws_bytes = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
+    P->off_A = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
+    const size_t img_bytes = P->img ? (size_t)lay.row_units * 2 * p->L * (p->N / TC_MTILE) * (P->tc_kpad / TC_KTILE) *
+                                          IMG_HALVES * 2
+                                    : 0;
+    P->ws_bytes = align256(P->off_A + img_bytes);
     (void)taps;
     return P;
 }
@@ -1792,7 +2242,7 @@ extern "C" int he_conv_time(const he_params* p, const he_conv_desc* d, const int
 extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
     return guard([&] {
         if (!plan || !mac_impl) fail(HE_EINVAL, "null argument");
-        *mac_impl = plan->use_tc ? 2 : (plan->eager ? 3 : 1);
+        *mac_impl = plan->use_tc ? (plan->img ? 2 : 4) : (plan->eager ? 3 : 1);
     });
 }
 
@@ -2155,7 +2605,8 @@ extern "C" int he_rotate(const he_params* p, const he_galkeys* gk, uint32_t galo
         } fkey, frot;
         u64* dkey = upload_keys(p, kp, {key}, s);
         fkey.p = dkey;
-        RotDev rd{galois, 1, 0, 0};
+        if (!(galois & 1) || galois >= 2 * p->N) fail(HE_EINVAL, "Galois element must be odd and below 2N");
+        RotDev rd{galois, 1, 0, galois_inverse(galois, p->N)};
         RotDev* drot = nullptr;
         CUDA_OK(cudaMalloc(&drot, sizeof(RotDev)));
         frot.p = drot;

@@ -256,11 +256,12 @@ def test_repeat_on_side_stream_and_host_path(small):
 
 
 # ---------------------------------------------------------------- both MAC implementations
-@pytest.mark.parametrize("impl", [1, 2, 3])
+@pytest.mark.parametrize("impl", [1, 2, 3, 4])
 @pytest.mark.parametrize("spec", [SMALL[0], SMALL[1], SMALL[4], SMALL[7], SMALL[11]])
 def test_mac_implementations(small, spec, impl):
-    """1 lazy CUDA-core, 2 tensor-core, 3 eager (reduced after every CMult and HAdd, Sec. 3.2.2's
-    conventional form): all three give the oracle's words."""
+    """1 lazy CUDA-core, 2 tensor-core fed with operand images written by the key switch, 3 eager
+    (reduced after every CMult and HAdd, Sec. 3.2.2's conventional form), 4 tensor-core with
+    in-kernel fp16 conversion: all four give the oracle's words."""
     small.layer(spec, mac_impl=impl)
 
 
@@ -290,8 +291,10 @@ def test_tensor_core_mac_is_chosen_when_exact(small):
 def test_tensor_core_mac_at_the_exactness_bound(pairs):
     """Every scalar 16 and every chunk at -512 drive each fp32 sum to its largest magnitude.
     A zero ciphertext makes every rotated residue 0 (all chunks 0 -> -512 after the offset).
-    113 pairs: K = 2034 terms in one accumulation.  228 pairs: K = 4104 terms, three segments
-    (2048 + 2048 + 8) whose results add mod q in the output."""
+    113 pairs: K = 2034 terms in one accumulation of the in-kernel conversion form (mac_impl 4);
+    the image form pads each rotation's 113 terms to 120, 2160 terms in two segments.  228 pairs:
+    K = 4104 terms, three segments (2048 + 2048 + 8; the image form 4176 terms) whose results add
+    mod q in the output."""
     S = Setup(1024, 2, 25)
     C_in = 2 * pairs
     spec = dict(C_in=C_in, C_out=4, H=2, W=2, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
@@ -300,15 +303,17 @@ def test_tensor_core_mac_at_the_exactness_bound(pairs):
     lay = H.he_layout_for_layer(S.p, d)
     zero = np.zeros((lay.n_ct_in, 2, 2, 1024), dtype=np.uint64)
     w = np.full((4, C_in, 3, 3), 8)
-    out_tc = gpu_layer(S.p, gk, d, w, zero, 2, 1024, mac_impl=2)
-    assert (out_tc == 0).all()
+    for impl in (2, 4):
+        out_tc = gpu_layer(S.p, gk, d, w, zero, 2, 1024, mac_impl=impl)
+        assert (out_tc == 0).all()
     # and on a real encryption, the tensor-core path equals the CUDA-core path word for word
     act = synth.activations((1, C_in, 2, 2), S.P.t)
     cts = H.he_encrypt_image(S.p, S.sk, d, act, synth.SEED_ENC, S.info)
     w = np.where(synth.weights((4, C_in, 3, 3)) >= 0, 8, -8)
     a = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=1)
     b = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=2)
-    assert (a == b).all()
+    c = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=4)
+    assert (a == b).all() and (a == c).all()
     dec = H.he_decrypt_image(S.p, S.sk, d, b)
     assert (dec == conv.conv_plain(act, w, 1, 1, False, S.P.t)).all()
 

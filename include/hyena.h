@@ -175,7 +175,11 @@ typedef struct {
                                 (reduced after every term; for ablations), 4 tensor-core MAC that splits
                                 the rotated residues into fp16 chunks itself (for ablations) */
     uint32_t tc_rows;        /* tensor-core MAC: output rows per CTA, a multiple of 16 up to 96 (0 -> 96) */
-    uint32_t reserved[5];
+    uint32_t tc_cluster;     /* image-form tensor-core MAC: 0 (default) or 2, 4, 8 -- run in clusters of
+                                that many CTAs that share each operand image by TMA multicast, each CTA
+                                taking a share of the layer's output rows (HE_EINVAL if the layer has too
+                                few rows or tc_rows is set) */
+    uint32_t reserved[4];
 } he_tune;
 
 /* Uploads the layer's Galois keys (NTT form), the Hadamard scalars

@@ -789,14 +789,18 @@ struct TcItem {
     u32 ru, p, k, n0, row0, nrows, n_tiles;
 };
 
+// With clusters of CL CTAs (operand-image MAC), an item is (row unit, polynomial, limb, slot
+// tile, group of CL row tiles) and CTA `rank` of the cluster takes row tile group * CL + rank.
 template <int MAXB>
-__device__ __forceinline__ bool tc_item(const Batch<MAXB>& B, u32 item, u32 N, u32 L, TcItem& it) {
+__device__ __forceinline__ bool tc_item(const Batch<MAXB>& B, u32 item, u32 N, u32 L, TcItem& it, u32 rank = 0,
+                                        u32 CL = 1) {
     if (item >= B.start[ST_MAC][B.n]) return false;
     const u32 li = find_layer(B, ST_MAC, item);
     const LayerDev& Ly = B.L[li];
     const u32 rpc = Ly.tc_rows_per_cta, mtiles = (Ly.tc_rows + rpc - 1) / rpc, nt_n = N / TC_MTILE;
+    const u32 mgroups = mtiles / CL;
     const u32 local = item - B.start[ST_MAC][li];
-    const u32 mt = local % mtiles, nt = (local / mtiles) % nt_n, z = local / (mtiles * nt_n);
+    const u32 mt = (local % mgroups) * CL + rank, nt = (local / mgroups) % nt_n, z = local / (mgroups * nt_n);
     it.ly = &Ly;
     it.k = z % L, it.p = (z / L) & 1, it.ru = z / (2 * L);
     it.n0 = nt * TC_MTILE;
@@ -1067,7 +1071,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
 // byte c * 8192, element (slot row m, term kl) at (m >> 3) * 512 + (kl >> 3) * 128 + (m & 7) * 16
 // + (kl & 7) * 2, the layout smem_desc describes (LBO 128 B, SBO 512 B).
 constexpr int KSI_THREADS = 128;          // one 128-slot tile per block, thread = destination slot
-constexpr u32 KSI_JB = 32;                // input ciphertexts per block (four groups of eight)
+constexpr u32 KSI_JB = 8;                 // input ciphertexts per block (one group of eight)
 constexpr u32 IMG_HALVES = TC_CHUNKS * TC_MTILE * TC_KTILE;  // 20480 halves = 40 KB per image
 
 // Step 2, operand-image form.  Local block = (row unit, block of 32 input ciphertexts, rotation,
@@ -1155,77 +1159,93 @@ __global__ void __launch_bounds__(KSI_THREADS, 6) k_keyswitch_img(const __grid_c
             __stcs(reinterpret_cast<uint4*>(d0 + p_stride + c * (TC_MTILE * TC_KTILE)), rows[1][c][tid]);
         }
     };
-    const u32 j_end = min(Ly.in_pad, (jc + 1) * KSI_JB);
-    for (u32 j0 = jc * KSI_JB; j0 < j_end; j0 += 8) {
+    // the block's input ciphertexts c = ru in_groups + j, j in [j0, j0 + 8), walked with running
+    // pointers; the loop is specialised by rotation kind and limb reduction outside the loop
+    const u32 j0 = jc * KSI_JB;
+    const u32 nj = j0 >= Ly.in_groups ? 0u : min(8u, Ly.in_groups - j0);  // real terms; the rest are padding
+    const size_t d_step = (size_t)LL * L * N, r_step = (size_t)Ly.r_slots * ctw, dd_step = (size_t)L * N;
+    const u64* Dp = Ly.D + (size_t)(ru * Ly.in_groups + j0) * d_step + (size_t)k * N + src;
+    const u64* Rp = Ly.R + ((size_t)(ru * Ly.in_groups + j0) * Ly.r_slots + Ly.r_id) * ctw + (size_t)k * N + src;
+    auto put = [&](u32 h, const u64 (&v0)[KSI_JH], const u64 (&v1)[KSI_JH]) {
+#pragma unroll
+        for (int c = 0; c < TC_CHUNKS; c++) {
+            reinterpret_cast<uint2*>(&rows[0][c][xl])[h] = chunk_pack4(v0, c);
+            reinterpret_cast<uint2*>(&rows[1][c][xl])[h] = chunk_pack4(v1, c);
+        }
+    };
+    const int kind = ident ? 0 : (m.sm1 == 49 ? (m.delta ? 1 : 2) : 3);
 #pragma unroll 1
-        for (u32 h = 0; h < 8; h += KSI_JH) {
-            u64 v0[KSI_JH], v1[KSI_JH];
+    for (u32 h = 0; h < 8 / KSI_JH; h++) {
+        u64 v0[KSI_JH], v1[KSI_JH];
+        if (kind == 0) {
 #pragma unroll
             for (int jj = 0; jj < KSI_JH; jj++) {
-                const u32 j = j0 + h + jj;
+                const bool real = h * KSI_JH + jj < nj;
+                v0[jj] = real ? __ldg(Rp + jj * r_step) : 0;
+                v1[jj] = real ? __ldg(Rp + jj * r_step + dd_step) : 0;
+            }
+        } else if (kind <= 2) {
+            // 50-bit limbs: Karatsuba middle term, one reduction per sum (see k_keyswitch)
+#pragma unroll
+            for (int jj = 0; jj < KSI_JH; jj++) {
                 v0[jj] = v1[jj] = 0;
-                if (j >= Ly.in_groups) continue;  // padded term: zero scalars, any finite operand
-                const u32 c = ru * Ly.in_groups + j;
-                const u64* Rid = Ly.R + ((size_t)c * Ly.r_slots + Ly.r_id) * ctw + (size_t)k * N;
-                if (ident) {
-                    v0[jj] = __ldg(Rid + src);
-                    v1[jj] = __ldg(Rid + (size_t)L * N + src);
-                    continue;
-                }
-                const u64* Dc = Ly.D + (size_t)c * LL * L * N + (size_t)k * N + src;
+                if (h * KSI_JH + jj >= nj) continue;
+                const u64* Dc = Dp + jj * d_step;
                 u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
-                if (m.sm1 == 49) {
 #pragma unroll
-                    for (int dd = 0; dd < LL; dd++) {
-                        const u64 dv = __ldg(Dc + (size_t)dd * L * N);
-                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
-                        mad_wide_u(lo0, dl, k0l[dd]);
-                        mad_wide_u(hi0, dh, k0h[dd]);
-                        mad_wide_u(mid0, ds, k0l[dd] + k0h[dd]);
-                        mad_wide_u(lo1, dl, k1l[dd]);
-                        mad_wide_u(hi1, dh, k1h[dd]);
-                        mad_wide_u(mid1, ds, k1l[dd] + k1h[dd]);
-                    }
-                    mid0 -= lo0 + hi0;
-                    mid1 -= lo1 + hi1;
-                    lo0 += __ldg(Rid + src);  // + sigma(c0)
-                    if (m.delta) {
-                        v0[jj] = fold_reduce50(lo0, mid0, hi0, m);
-                        v1[jj] = fold_reduce50(lo1, mid1, hi1, m);
-                    } else {
-                        v0[jj] = bred_split50(lo0, mid0, hi0, m);
-                        v1[jj] = bred_split50(lo1, mid1, hi1, m);
-                    }
+                for (int dd = 0; dd < LL; dd++) {
+                    const u64 dv = __ldg(Dc + dd * dd_step);
+                    const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
+                    mad_wide_u(lo0, dl, k0l[dd]);
+                    mad_wide_u(hi0, dh, k0h[dd]);
+                    mad_wide_u(mid0, ds, k0l[dd] + k0h[dd]);
+                    mad_wide_u(lo1, dl, k1l[dd]);
+                    mad_wide_u(hi1, dh, k1h[dd]);
+                    mad_wide_u(mid1, ds, k1l[dd] + k1h[dd]);
+                }
+                mid0 -= lo0 + hi0;
+                mid1 -= lo1 + hi1;
+                lo0 += __ldg(Rp + jj * r_step);  // + sigma(c0)
+                if (kind == 1) {
+                    v0[jj] = fold_reduce50(lo0, mid0, hi0, m);
+                    v1[jj] = fold_reduce50(lo1, mid1, hi1, m);
                 } else {
-#pragma unroll
-                    for (int dd = 0; dd < LL; dd++) {
-                        const u64 dv = __ldg(Dc + (size_t)dd * L * N);
-                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
-                        mad_wide_u(lo0, dl, k0l[dd]);
-                        mad_wide_u(mid0, dl, k0h[dd]);
-                        mad_wide_u(mid0, dh, k0l[dd]);
-                        mad_wide_u(hi0, dh, k0h[dd]);
-                        mad_wide_u(lo1, dl, k1l[dd]);
-                        mad_wide_u(mid1, dl, k1h[dd]);
-                        mad_wide_u(mid1, dh, k1l[dd]);
-                        mad_wide_u(hi1, dh, k1h[dd]);
-                    }
-                    lo0 += __ldg(Rid + src);
-                    v0[jj] = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
-                    v1[jj] = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
+                    v0[jj] = bred_split50(lo0, mid0, hi0, m);
+                    v1[jj] = bred_split50(lo1, mid1, hi1, m);
                 }
             }
-            // chunks of these four terms into the shared image rows of destination x
+        } else {
 #pragma unroll
-            for (int c = 0; c < TC_CHUNKS; c++) {
-                reinterpret_cast<uint2*>(&rows[0][c][xl])[h / KSI_JH] = chunk_pack4(v0, c);
-                reinterpret_cast<uint2*>(&rows[1][c][xl])[h / KSI_JH] = chunk_pack4(v1, c);
+            for (int jj = 0; jj < KSI_JH; jj++) {
+                v0[jj] = v1[jj] = 0;
+                if (h * KSI_JH + jj >= nj) continue;
+                const u64* Dc = Dp + jj * d_step;
+                u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
+#pragma unroll
+                for (int dd = 0; dd < LL; dd++) {
+                    const u64 dv = __ldg(Dc + dd * dd_step);
+                    const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                    mad_wide_u(lo0, dl, k0l[dd]);
+                    mad_wide_u(mid0, dl, k0h[dd]);
+                    mad_wide_u(mid0, dh, k0l[dd]);
+                    mad_wide_u(hi0, dh, k0h[dd]);
+                    mad_wide_u(lo1, dl, k1l[dd]);
+                    mad_wide_u(mid1, dl, k1h[dd]);
+                    mad_wide_u(mid1, dh, k1l[dd]);
+                    mad_wide_u(hi1, dh, k1h[dd]);
+                }
+                lo0 += __ldg(Rp + jj * r_step);
+                v0[jj] = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
+                v1[jj] = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
             }
         }
-        __syncthreads();
-        store_rows(r * Ly.in_pad + j0);
-        __syncthreads();
+        put(h, v0, v1);
+        Dp += KSI_JH * d_step;
+        Rp += KSI_JH * r_step;
     }
+    __syncthreads();
+    store_rows(r * Ly.in_pad + j0);
+    __syncthreads();
     // the terms past n_rot in_pad that fill the last K tile carry zero scalars; their operands must
     // still be finite numbers (a NaN times 0 is NaN), so the last block of the last rotation zeroes them
     if (r + 1 == Ly.n_rot_all && jc + 1 == JC) {
@@ -1249,13 +1269,24 @@ constexpr u32 TCI_BAR_OFF = TCI_B_OFF + TCI_STAGES * TC_B_BYTES;
 constexpr u32 TCI_SMEM_BYTES = TCI_BAR_OFF + 128;                 // 2 TCI_STAGES + 2 mbarriers, TMEM slot, flag
 static_assert(TCI_SMEM_BYTES <= 227 * 1024, "operand-image MAC exceeds shared memory");
 
-template <bool PACKED, int MAXB>
+// Clusters (CL = 2, 4, 8): the CL CTAs of a cluster take the row tiles of one slot tile and share
+// each image: CTA `rank` copies bytes [rank, rank + 1) x 40 KB / CL of it with one multicast bulk
+// copy into the same stage of every CTA of the cluster, and every CTA's MMA completion is
+// committed to the `empty` barrier of every CTA, so no CTA refills a stage (in any CTA) before all
+// have used it.  A cluster barrier at start (barrier initialisation) and at exit (no copy or
+// commit may still target a CTA that has left) brackets the work.
+template <bool PACKED, int CL, int MAXB>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant__ Batch<MAXB> B, KP kp, u32 tmem_cols) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     constexpr int NR = PACKED ? 2 : 1;
     constexpr int NB = 2 * TCI_STAGES + 2;
     const u32 N = kp.N, L = kp.L, NT = N / TC_MTILE;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    u32 rank = 0;
+    if (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const u32 cid = blockIdx.x / CL, n_cl = gridDim.x / CL;
+    constexpr u32 SLICE = TCI_A_BYTES / CL;  // bytes of an image each CTA of a cluster copies
+    const uint16_t cta_mask = (uint16_t)((1u << CL) - 1);
     u64* bars = reinterpret_cast<u64*>(tsm + TCI_BAR_OFF);
     // barrier indices: full 0..S-1, empty S..2S-1, acc_full 2S, acc_empty 2S+1
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
@@ -1266,7 +1297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
     if (tid == 0) {
         for (int i = 0; i < TCI_STAGES; i++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(FULL + i)), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(CL));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_FULL)), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_EMPTY)), "r"(TC_EPI));
@@ -1279,7 +1310,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    if (CL > 1) {
+        // every CTA's barriers are initialised before any CTA of the cluster copies or commits to them
+        asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+        __syncthreads();
+    }
     asm volatile("tcgen05.fence::after_thread_sync;");
     const u32 tmem = *tmem_slot;
 
@@ -1292,12 +1328,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         // ---------------------------------------------------------------- copies
         u32 g = 0;
         TcItem it;
-        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+        bool ok = true;
+        for (u32 item = cid; ok && tc_item(B, item, N, L, it, rank, CL); item += n_cl) {
             const LayerDev& Ly = *it.ly;
             const u32 bbytes = Ly.tc_rows_per_cta * TC_KTILE * 2, ktiles = Ly.Kpad / TC_KTILE;
             const u32 mt = it.row0 / Ly.tc_rows_per_cta, nt = it.n0 / TC_MTILE;
             const __half* abase = Ly.A16 + ((((size_t)it.ru * 2 + it.p) * L + it.k) * NT + nt) * ktiles * IMG_HALVES;
-            bool ok = true;
             for (u32 t = 0; t < it.n_tiles; t++, g++) {
                 const u32 s = g % TCI_STAGES;
                 const bool fr = g < TCI_STAGES || wait(EMPTY + s, ((g / TCI_STAGES) - 1) & 1);
@@ -1306,11 +1342,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)),
                                  "r"(TCI_A_BYTES + bbytes)
                                  : "memory");
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(tsm + s * TCI_A_BYTES)),
-                        "l"(abase + (size_t)t * IMG_HALVES), "r"(TCI_A_BYTES), "r"(bar(FULL + s))
-                        : "memory");
+                    if (CL == 1) {
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                smem_u32(tsm + s * TCI_A_BYTES)),
+                            "l"(abase + (size_t)t * IMG_HALVES), "r"(TCI_A_BYTES), "r"(bar(FULL + s))
+                            : "memory");
+                    } else {
+                        // this CTA's slice of the image, into the same stage of every CTA of the cluster
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+                            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(tsm + s * TCI_A_BYTES + rank * SLICE)),
+                            "l"(reinterpret_cast<const unsigned char*>(abase + (size_t)t * IMG_HALVES) + rank * SLICE),
+                            "r"(SLICE), "r"(bar(FULL + s)), "h"(cta_mask)
+                            : "memory");
+                    }
                     const __half* bsrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (Ly.tc_rows_per_cta * TC_KTILE);
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -1320,14 +1366,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
                 }
                 __syncwarp();
             }
-            if (!ok || *abort_flag) break;
+            if (*abort_flag) ok = false;
+        }
+        // with clusters, the other CTAs' MMAs commit to this CTA's empty barriers: wait for the
+        // commits of the last uses of every stage, so none is still on its way when this CTA leaves
+        if (CL > 1 && ok) {
+            for (u32 gg = g > TCI_STAGES ? g - TCI_STAGES : 0; gg < g; gg++)
+                if (!__all_sync(0xffffffffu, wait(EMPTY + gg % TCI_STAGES, (gg / TCI_STAGES) & 1))) break;
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMAs (lane 0)
         if (lane == 0) {
             u32 g = 0, unit = 0;  // unit = (item, segment): one accumulation in TMEM
             TcItem it;
-            for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+            for (u32 item = cid; tc_item(B, item, N, L, it, rank, CL); item += n_cl) {
                 const u32 idesc = tc_idesc(TC_MTILE, it.nrows);
                 bool okk = true;
                 for (u32 t = 0; t < it.n_tiles; t++, g++) {
@@ -1353,7 +1405,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                         }
                     }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(EMPTY + s)));
+                    if (CL == 1)
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            bar(EMPTY + s)));
+                    else
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+                            " [%0], %1;" ::"r"(bar(EMPTY + s)),
+                            "h"(cta_mask));
                     if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(ACC_FULL)));
                         unit++;
@@ -1367,7 +1426,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         // ---------------------------------------------------------------- epilogue
         u32 unit = 0;
         TcItem it;
-        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+        for (u32 item = cid; tc_item(B, item, N, L, it, rank, CL); item += n_cl) {
             const LayerDev& Ly = *it.ly;
             const u32 n_seg = (it.n_tiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
             bool okk = true;
@@ -1432,6 +1491,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
     }
+    // no CTA leaves while another CTA of its cluster may still copy into its shared memory
+    if (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ profiling
@@ -1589,9 +1650,9 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
     bool tc = false, packed = false, dw = false, eager = false, img = false;
-    u32 gt = 8;
+    u32 gt = 8, cl = 1;  // cl: CTAs per cluster of the operand-image MAC
     bool operator==(const MacVariant& o) const {
-        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img &&
+        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img && cl == o.cl &&
                (tc || eager || gt == o.gt);
     }
 };
@@ -1611,7 +1672,9 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
             return d.n_ks * L * (N / KS_THREADS);
         case ST_MAC:
             if (s.mv.eager) return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + 3) / 4);
-            if (s.mv.tc) return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta);
+            if (s.mv.tc)
+                return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta) /
+                       s.mv.cl;
             return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + s.mv.gt - 1) / s.mv.gt);
         default: return d.n_ct_out * 2 * L;
     }
@@ -1642,6 +1705,38 @@ void mac_cuda_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_
     k_mac<GT, PACKED, DW, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
 }
 
+// Persistent launch of the operand-image MAC in clusters of CL CTAs: as many clusters as fit the
+// device at once (one CTA per SM), at most one per cluster item.
+template <int CL, int MAXB>
+void mac_img_launch(bool packed, u32 items, const Batch<MAXB>& B, const KP& kp, u32 cols, cudaStream_t s) {
+    auto kern = packed ? k_mac_img<true, CL, MAXB> : k_mac_img<false, CL, MAXB>;
+    allow_smem(kern, TCI_SMEM_BYTES);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TCI_SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int cached[9] = {0};  // clusters that fit at once, per cluster size (one device per process)
+    if (!cached[CL]) {
+        int n = 0;
+        cfg.gridDim = dim3(CL * 64);
+        if (CL == 1 || cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = sm_count() / CL;
+        }
+        cached[CL] = std::max(n, 1);
+    }
+    const u32 n_cl = std::min<u32>(items, (u32)cached[CL]);
+    cfg.gridDim = dim3(n_cl * CL);
+    CUDA_OK(cudaLaunchKernelEx(&cfg, kern, B, kp, cols));
+}
+
 template <int MAXB>
 void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
     if (mv.eager) {
@@ -1655,12 +1750,11 @@ void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const 
         for (u32 i = 0; i < B.n; i++) cols = std::max(cols, B.L[i].tmem_cols);
         const u32 grid = std::min(blocks, (u32)sm_count());
         if (mv.img) {
-            if (mv.packed) {
-                allow_smem(k_mac_img<true, MAXB>, TCI_SMEM_BYTES);
-                k_mac_img<true, MAXB><<<grid, TC_THREADS, TCI_SMEM_BYTES, s>>>(B, kp, cols);
-            } else {
-                allow_smem(k_mac_img<false, MAXB>, TCI_SMEM_BYTES);
-                k_mac_img<false, MAXB><<<grid, TC_THREADS, TCI_SMEM_BYTES, s>>>(B, kp, cols);
+            switch (mv.cl) {
+                case 1: mac_img_launch<1, MAXB>(mv.packed, blocks, B, kp, cols, s); break;
+                case 2: mac_img_launch<2, MAXB>(mv.packed, blocks, B, kp, cols, s); break;
+                case 4: mac_img_launch<4, MAXB>(mv.packed, blocks, B, kp, cols, s); break;
+                default: mac_img_launch<8, MAXB>(mv.packed, blocks, B, kp, cols, s); break;
             }
             return;
         }
@@ -1853,7 +1947,7 @@ struct he_plan {
     bool packed = false, dw = false;
     u32 mac_groups = 8;
     bool use_tc = false, eager = false, img = false;
-    u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0;
+    u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0, cl = 1;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
     RotDev* d_rots_all = nullptr;
@@ -1897,7 +1991,7 @@ struct he_plan {
         L.A16 = img ? (__half*)(ws + off_A) : nullptr;
         if (use_tc && !img) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
-        s.mv.img = img;
+        s.mv.img = img, s.mv.cl = cl;
         return s;
     }
 };
@@ -1999,6 +2093,8 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
     if (impl > 4) fail(HE_EINVAL, "mac_impl must be 0..4");
+    if (tune && tune->tc_cluster && tune->tc_cluster != 2 && tune->tc_cluster != 4 && tune->tc_cluster != 8)
+        fail(HE_EINVAL, "tc_cluster must be 0, 2, 4 or 8");
     P->eager = impl == 3;
     P->use_tc = tc_ok && impl != 1 && impl != 3;
     // tensor-core layers take their operands as images written by the key switch, unless the
@@ -2048,6 +2144,18 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 rows = lay.out_groups * NR;
         P->tc_rows = (rows + 15) / 16 * 16;
         P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
+        P->cl = 1;
+        const u32 cl_req = tune ? tune->tc_cluster : 0;
+        if (cl_req > 1) {
+            // clusters of cl_req CTAs share each operand image by multicast: the row tiles of a slot
+            // tile are split into a multiple of cl_req tiles of at most 96 rows, none of them empty
+            const u32 m = cl_req * ((P->tc_rows + TC_NMAX * cl_req - 1) / (TC_NMAX * cl_req));
+            const u32 rpc = ((P->tc_rows + m - 1) / m + 15) / 16 * 16;
+            if (!P->img || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
+                fail(HE_EINVAL, "tc_cluster needs the image-form tensor-core MAC, no tc_rows, and at least " +
+                                    std::to_string(16 * (m - 1) + 16) + " output rows");
+            P->cl = cl_req, P->tc_rows_per_cta = rpc;
+        }
         // terms: kk = j n_rot + rot for the in-kernel conversion form, rot in_pad + j for the image form
         const u32 k_terms = P->img ? P->n_rot * P->in_pad : P->K;
         P->tc_kpad = (k_terms + TC_KTILE - 1) / TC_KTILE * TC_KTILE;

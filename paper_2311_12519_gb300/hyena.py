@@ -47,7 +47,7 @@ class he_layout(ctypes.Structure):
 
 
 class he_tune(ctypes.Structure):
-    _fields_ = [("mac_groups", u32), ("mac_impl", u32), ("tc_rows", u32), ("reserved", u32 * 5)]
+    _fields_ = [("mac_groups", u32), ("mac_impl", u32), ("tc_rows", u32), ("tc_cluster", u32), ("reserved", u32 * 4)]
 
 
 class he_stage_times(ctypes.Structure):
@@ -265,9 +265,9 @@ def he_decrypt_slots(p, sk, ct, N):
 
 
 # ---------------------------------------------------------------------- server
-def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0):
+def he_conv_plan(p, gk, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0, tc_cluster=0):
     w = np.ascontiguousarray(weights, dtype=np.int32)
-    t = he_tune(mac_groups, mac_impl, tc_rows)
+    t = he_tune(mac_groups, mac_impl, tc_rows, tc_cluster)
     h = vp()
     _check(load().he_conv_plan(p, gk, ctypes.byref(d), _ptr(w), ctypes.byref(t), ctypes.byref(h)), "he_conv_plan")
     return h.value

@@ -31,8 +31,9 @@ def from_dev(t, shape):
     return t.cpu().numpy().view(np.uint64).reshape(shape)
 
 
-def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0, mac_impl=0):
-    plan = H.he_conv_plan(p, gk, d, w, mac_groups=mac_groups, mac_impl=mac_impl)
+def gpu_layer(p, gk, d, w, cts, L, N, stream=None, mac_groups=0, mac_impl=0, tc_rows=0, tc_cluster=0):
+    plan = H.he_conv_plan(p, gk, d, w, mac_groups=mac_groups, mac_impl=mac_impl, tc_rows=tc_rows,
+                          tc_cluster=tc_cluster)
     n_in, n_out, ws = H.he_conv_sizes(plan)
     assert n_in == cts.size
     d_in = to_dev(cts)
@@ -64,7 +65,7 @@ class Setup:
                 self._ksk[g] = bfv.galois_key(self.P, self.s, g, synth.SEED_KEYS)
         return self._ksk
 
-    def layer(self, spec, label=0, sample=None, mac_groups=0, mac_impl=0, wmax=8):
+    def layer(self, spec, label=0, sample=None, mac_groups=0, mac_impl=0, wmax=8, tc_rows=0, tc_cluster=0):
         N, L = self.N, self.L
         d = H.conv_desc(**spec)
         ol = conv.Layout(N=N, **spec)
@@ -76,7 +77,8 @@ class Setup:
         cts = H.he_encrypt_image(self.p, self.sk, d, act, synth.SEED_ENC, self.info)
         ref_in = conv.encrypt_image(self.P, ol, self.s, act, synth.SEED_ENC)
         assert (cts == ref_in).all()
-        out = gpu_layer(self.p, gk, d, wt, cts, L, N, mac_groups=mac_groups, mac_impl=mac_impl)
+        out = gpu_layer(self.p, gk, d, wt, cts, L, N, mac_groups=mac_groups, mac_impl=mac_impl, tc_rows=tc_rows,
+                        tc_cluster=tc_cluster)
         ref = conv.he_conv(self.P, ol, wt, ref_in, self.oracle_keys(gs), out_cts=sample)
         idx = range(len(out)) if sample is None else sample
         for c in idx:
@@ -325,6 +327,26 @@ def test_tensor_core_multi_segment_matches_oracle(small, C_in):
     results add mod q in the output; every output ciphertext word for word against the oracle."""
     spec = dict(C_in=C_in, C_out=6, H=4, W=4, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
     small.layer(spec, label=C_in, mac_impl=2)
+
+
+@pytest.mark.parametrize("C_out,cluster", [(128, 0), (128, 2), (256, 4), (512, 8), (1024, 8), (200, 2)])
+def test_tensor_core_clusters_match_oracle(small, C_out, cluster):
+    """Layers wider than one 96-row tile, with the tensor-core MAC in clusters of 2, 4 or 8 CTAs
+    that share each operand image by TMA multicast (tc_cluster), or without (0): every output
+    ciphertext word for word against the oracle."""
+    spec = dict(C_in=6, C_out=C_out, H=3, W=3, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
+    small.layer(spec, label=C_out, mac_impl=2, tc_cluster=cluster)
+
+
+def test_tensor_core_cluster_needs_enough_rows(small):
+    spec = dict(C_in=6, C_out=16, H=3, W=3, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
+    d = H.conv_desc(**spec)
+    gk = H.he_galois_keys(small.p, small.sk, H.he_layer_galois(small.p, d), synth.SEED_KEYS)
+    for cl in (8, 3):
+        with pytest.raises(H.HyenaError) as e:
+            H.he_conv_plan(small.p, gk, d, synth.weights((16, 6, 3, 3)), tc_cluster=cl)
+        assert e.value.code == H.HE_EINVAL
+    H.he_galkeys_destroy(gk)
 
 
 # ---------------------------------------------------------------- batched execution

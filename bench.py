@@ -94,7 +94,7 @@ def layer_counts(spec, lay, L, l, N):
     ks = lay.n_ct_in * lay.n_galois * 2 * L * l * L * N
     w8 = N * 8
     return {
-        "conv_modmac": conv, "ks_modmac": ks,
+        "conv_modmac": conv, "ks_modmac": ks, "ks_modmac_stage": ks,
         # forward transforms of c0 and of the digits of c1 (the single digit of c1 in its own limb is c1)
         "ntt_in_transforms": lay.n_ct_in * (L + L * l * L),
         # the key stream of every Galois element once, plus the digit and c0 transforms the switch reads
@@ -325,15 +325,26 @@ def verify_outputs(H, p, sk, info, workload, specs, descs, d_outs, rank, index):
     return res
 
 
-def stage_rooflines(stages, counts, steps, peaks, N):
+# 32x32 -> 64-bit multiply-adds (mad.wide.u32) per clock per SM, from a throughput probe on this GPU
+MAD_WIDE_PER_CLK_SM = 28.5
+
+
+def stage_rooflines(stages, counts, steps, peaks, N, sm_mhz=None):
     """Sec. 8(d)'s roofline of each stage kernel of the batched step, from its event-timed
     duration: NTTs 16 N bytes per transform, the key switch its key stream plus the digit and c0
     transforms it reads, the tensor-core MAC 10 fp16 flops per modMAC (five 10-bit chunks, one
-    multiply-add each) against the dense fp16 tensor peak (= the measured bf16 peak)."""
+    multiply-add each) against the dense fp16 tensor peak (= the measured bf16 peak).  The key
+    switch also gets an ALU view: modMAC/s against 3 mad.wide per modMAC (Karatsuba products) at
+    the probed mad.wide rate, 152 SMs and the SM clock."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     tc = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+    mhz = float(sm_mhz or peaks.get("sm_max_mhz", 2070.0))
+    alu_modmac = MAD_WIDE_PER_CLK_SM * 152 * mhz * 1e6 / 3
     out = {}
     for st, (ms, launches) in stages.items():
+        if not launches:  # e.g. no key-switch launch when every layer's key switch is fused
+            out[st] = None
+            continue
         sec = ms / 1000 / max(1, steps)
         if st == "ntt_in":
             a = counts["ntt_in_transforms"] * 16 * N
@@ -343,11 +354,15 @@ def stage_rooflines(stages, counts, steps, peaks, N):
             r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
         elif st == "keyswitch":
             a = counts["ks_bytes"]
-            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
+            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm,
+                 "alu_view": {"modmac_per_s": counts["ks_modmac_stage"] / sec if sec else None,
+                              "peak_modmac_per_s": alu_modmac,
+                              "frac": counts["ks_modmac_stage"] / sec / alu_modmac if sec else None}}
         else:
             a = 10 * counts["conv_modmac"]
             r = {"bound": "tensor", "algorithmic": a, "unit": "TFLOP/s", "peak": tc,
-                 "hbm_gbs_design_bytes": (counts["mac_r_bytes"] + counts["out_bytes"]) / sec / 1e9 if sec else None}
+                 "fused_key_switch": {"key_and_digit_bytes": counts["mac_ks_bytes"],
+                                      "modmac": counts["mac_ks_modmac"]}}
         scale = 1e9 if r["unit"] == "GB/s" else 1e12
         r["achieved"] = a / sec / scale if sec else None
         r["frac"] = r["achieved"] / r["peak"] if sec else None
@@ -403,14 +418,20 @@ def run_gpu(args, rank, world):
     gk = H.he_galois_keys(p, sk, gal, synth.SEED_KEYS)
     plans, d_ins, d_outs, h_ins, h_outs = [], [], [], [], []
     ws_max = 0
-    counts = {}
+    counts = {"ks_bytes": 0, "ks_modmac_stage": 0, "mac_ks_bytes": 0, "mac_ks_modmac": 0}
+    impls = []
     for i, (s, d) in enumerate(zip(specs, descs)):
         act, wt, enc_seed = rank_inputs(wl, index[i], rank, info.t)
         cts = H.he_encrypt_image(p, sk, d, act, enc_seed, info)
         plan = H.he_conv_plan(p, gk, d, wt, **tunes[i])
         n_in, n_out, ws = H.he_conv_sizes(plan)
         lay = H.he_layout_for_layer(p, d)
-        for k, v in layer_counts(s, lay, L, l, N).items():
+        lc = layer_counts(s, lay, L, l, N)
+        impl = H.he_conv_info(plan)
+        impls.append(impl)
+        if impl == 6:  # the key switch runs inside the fused MAC kernel: its work is that stage's
+            lc["mac_ks_bytes"], lc["mac_ks_modmac"] = lc.pop("ks_bytes"), lc.pop("ks_modmac_stage")
+        for k, v in lc.items():
             counts[k] = counts.get(k, 0) + v
         plans.append(plan)
         h_in = torch.from_numpy(cts.reshape(-1).view(np.int64)).pin_memory()
@@ -511,11 +532,16 @@ def run_gpu(args, rank, world):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    roofs = stage_rooflines(stages_b, counts, args.steps, peaks, N)
+    roofs = stage_rooflines(stages_b, counts, args.steps, peaks, N, clocks_b.get("sm_mhz"))
     top = max(stages_b, key=lambda k: stages_b[k][0])
-    mac_tc = all(H.he_conv_info(pl) == 2 for pl in plans)
-    kname = {"mac": "k_mac_tc" if mac_tc else "k_mac_tc + k_mac", "keyswitch": "k_keyswitch",
+    # the kernels of each stage: he_conv_info 1 CUDA-core MAC, 3 eager, 4 tensor-core with in-kernel
+    # conversion, 5 tensor-core on operand images, 6 fused key switch + tensor-core MAC
+    mac_k = {1: "k_mac", 3: "k_mac_eager", 4: "k_mac_tc", 5: "k_mac_img", 6: "k_ksmac"}
+    ks_k = {1: "k_keyswitch", 3: "k_keyswitch", 4: "k_keyswitch", 5: "k_keyswitch_img"}
+    kname = {"mac": " + ".join(sorted({mac_k[i] for i in impls})),
+             "keyswitch": " + ".join(sorted({ks_k[i] for i in impls if i != 6})) or "none (fused)",
              "ntt_in": "k_ntt_inputs", "ntt_out": "k_intt"}
+    top = max((k for k in stages_b if roofs[k]), key=lambda k: stages_b[k][0])
     roof = {k: v for k, v in roofs[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
     src = kernel_source_digest().hexdigest()
     prof = PROFILED_TRAFFIC.get((wl, kname[top]))
@@ -551,7 +577,7 @@ def run_gpu(args, rank, world):
                 "call": "he_batch_forward_host (pinned host buffers, copies and graph replay in the timed region)"},
         "gpu_launches": int(sum(v[1] for v in stages_b.values()) // max(1, args.steps) * args.steps),
         "roofline": roof,
-        "roofline_per_kernel": {kname[k]: v for k, v in roofs.items()},
+        "roofline_per_kernel": {kname[k]: v for k, v in roofs.items() if v},
         "cpu_baseline": cpu,
         "clocks": clocks_b,
         "verified": verified,
@@ -674,8 +700,11 @@ ABLATION = [
     ("lazy CUDA-core, w=50", "Fig. latency (e): all optimisations", 50, 2, 1),
     ("lazy tensor-core, in-kernel fp16 conversion, w=50", "(e) on tcgen05, residues split into chunks by the MAC",
      50, 2, 4),
-    ("lazy tensor-core, w=50", "(e) on tcgen05, operand images written by the key switch (the default form)",
-     50, 2, 2),
+    ("lazy tensor-core, operand images, w=50", "(e) on tcgen05, operand images written by the key switch",
+     50, 2, 5),
+    ("lazy tensor-core, fused key switch, w=50", "(e) on tcgen05, key switch inside the MAC kernel", 50, 2, 6),
+    ("lazy tensor-core, w=50", "(e) on tcgen05, the automatic form (in-kernel conversion for layers of one "
+     "row tile, operand images for wider ones)", 50, 2, 2),
     ("lazy tensor-core, w=50, c_n=1", "padded convolution without output-channel packing (Sec. 2.4)", 50, 1, 2),
 ]
 
@@ -783,6 +812,35 @@ def run_ablation(args):
         torch.cuda.empty_cache()
 
 
+# ------------------------------------------------------------------ tensor-core forms per layer
+def run_forms(args):
+    """Every layer of the stack timed alone (he_conv_time: uniform residues, median of `steps`
+    forwards) in each tensor-core form it admits (4 in-kernel conversion, 5 operand images, 6 fused
+    key switch) and with the automatic choice: one JSON line per layer with per-stage ms."""
+    import torch
+
+    from paper_2311_12519_gb300 import hyena as H
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    specs, N, L, images = layer_specs(args.workload, args.layers)
+    index = list(range(len(specs))) if args.layers is None else list(args.layers)
+    p = H.he_params_create(N, L, limb_bits=LIMB_BITS, decomp_bits=50)
+    for i, s in zip(index, specs):
+        d = H.conv_desc(**s)
+        _, wt, _ = synth.stack_inputs(args.workload, i, H.he_params_info(p).t)
+        row = {"mode": "forms", "workload": args.workload, "layer": i}
+        for impl in (0, 4, 5, 6):
+            try:
+                total, stages = H.he_conv_time(p, d, wt, mac_impl=impl, reps=max(3, args.steps),
+                                               stream=stream.cuda_stream)
+                row[str(impl)] = {"ms": round(total, 4), "stages": [round(x, 4) for x in stages]}
+            except H.HyenaError as e:
+                row[str(impl)] = {"unavailable": str(e).split(": ", 1)[-1][:80]}
+        print(json.dumps(row), flush=True)
+    H.he_params_destroy(p)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -797,7 +855,7 @@ def main():
                     help="run only these layer indices of the stack (comma list), e.g. for profiler captures")
     ap.add_argument("--tuned", action="store_true",
                     help="pick each layer's packing, tile and MAC schedule by timing every candidate first")
-    ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation", "learned"],
+    ap.add_argument("--mode", default="full", choices=["full", "batch", "ablation", "learned", "forms"],
                     help="batch: only the batched forward, W + K times, no JSON (for profiler captures); "
                          "ablation: one JSON line per variant of the latency study (reduction, w, c_n, MAC unit); "
                          "learned: every layer in the configuration the trained cost model picks")
@@ -814,6 +872,10 @@ def main():
     if args.mode == "learned":
         if rank == 0:
             run_learned(args)
+        return
+    if args.mode == "forms":
+        if rank == 0:
+            run_forms(args)
         return
     if world > 1:
         import torch

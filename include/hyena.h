@@ -170,10 +170,12 @@ int he_decrypt_slots(const he_params* p, const he_seckey* sk, const uint64_t* ct
 /* ------------------------------------------------------------------ */
 typedef struct {
     uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block (0 -> default) */
-    uint32_t mac_impl;       /* 0 auto, 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL if not exact;
-                                the key switch writes the MMA operand images), 3 CUDA-core eager MAC
-                                (reduced after every term; for ablations), 4 tensor-core MAC that splits
-                                the rotated residues into fp16 chunks itself (for ablations) */
+    uint32_t mac_impl;       /* 0 auto, 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL if not exact)
+                                in the form auto picks: 4 when the layer's output rows fit one CTA, else 5;
+                                3 CUDA-core eager MAC (reduced after every term; for ablations);
+                                4 tensor-core MAC that splits the rotated residues into fp16 chunks itself;
+                                5 tensor-core MAC on operand images the key switch writes once;
+                                6 key switch fused into the tensor-core MAC (rows fitting one CTA only) */
     uint32_t tc_rows;        /* tensor-core MAC: output rows per CTA, a multiple of 16 up to 96 (0 -> 96) */
     uint32_t tc_cluster;     /* image-form tensor-core MAC: 0 (default) or 2, 4, 8 -- run in clusters of
                                 that many CTAs that share each operand image by TMA multicast, each CTA
@@ -206,8 +208,8 @@ int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_
 /* Synchronises the device and returns HE_ETIMEOUT if a bounded wait inside
  * an earlier forward of this plan gave up (the outputs are then invalid). */
 int he_conv_status(const he_plan* plan);
-/* *mac_impl = 1 (CUDA-core MAC), 2 (tensor-core MAC), 3 (eager) or 4 (tensor-core MAC with
- * in-kernel conversion) for this plan.  The
+/* *mac_impl = 1 (CUDA-core MAC), 3 (eager), or the tensor-core form: 4 (in-kernel conversion),
+ * 5 (operand images) or 6 (key switch fused) for this plan.  The
  * tensor-core form (fp16 10-bit chunks, fp32 sums of at most 2048 terms per
  * accumulation) is chosen automatically when it is exact: no depthwise,
  * |s| <= 16 and every limb below 2^50 (five chunks). */

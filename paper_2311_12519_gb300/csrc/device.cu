@@ -43,10 +43,8 @@ struct KP {
     u32 N, logN, L, l, w;
     u64 kmul;  // the k of the [k,-k] plaintext
     LimbC limb[HE_MAX_LIMBS];
-    const u64* tw;
-    const u64* tw_sh;
-    const u64* itw;
-    const u64* itw_sh;
+    const u64* tw;   // [L][N][2]: psi^rev(k) and its Shoup companion, side by side (one 16-byte load)
+    const u64* itw;  // [L][N][2]: psi^-rev(k) and its Shoup companion
 };
 struct RotDev {
     u32 galois, rot, key, galois_inv;  // galois_inv = galois^-1 mod 2N
@@ -113,9 +111,13 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wsh, u64 q) {
     return a * w - __umul64hi(a, wsh) * q;  // in [0, 2q)
 }
 
+__device__ __forceinline__ ulonglong2 twiddle(const u64* __restrict__ twp, u32 i) {
+    return __ldg(reinterpret_cast<const ulonglong2*>(twp) + i);
+}
+
 template <int PE_TOP>
 __device__ __forceinline__ void fwd_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo, u32 logN, const u64* __restrict__ tw,
-                                           const u64* __restrict__ tws, u64 q, u64 q2) {
+                                           u64 q, u64 q2) {
 #pragma unroll
     for (int pe = PE_TOP; pe >= 0; pe--) {
         const u32 off = 1u << (logN - 1 - (lo + pe));
@@ -124,7 +126,8 @@ __device__ __forceinline__ void fwd_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo,
             if (e & (1 << pe)) continue;
             const int e2 = e | (1 << pe);
             const u32 i = off + ((u32)(e >> (pe + 1)) | (base_hi << (3 - pe)));
-            const u64 W = __ldg(tw + i), Ws = __ldg(tws + i);
+            const ulonglong2 w = twiddle(tw, i);
+            const u64 W = w.x, Ws = w.y;
             u64 X = x[e];
             X = X >= q2 ? X - q2 : X;
             const u64 T = shoup_lazy(x[e2], W, Ws, q);
@@ -136,7 +139,7 @@ __device__ __forceinline__ void fwd_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo,
 
 template <int PE_BOT>
 __device__ __forceinline__ void inv_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo, u32 logN, const u64* __restrict__ itw,
-                                           const u64* __restrict__ itws, u64 q, u64 q2) {
+                                           u64 q, u64 q2) {
 #pragma unroll
     for (int pe = PE_BOT; pe <= 3; pe++) {
         const u32 off = 1u << (logN - 1 - (lo + pe));
@@ -145,7 +148,8 @@ __device__ __forceinline__ void inv_window(u64 (&x)[NTT_E], u32 base_hi, u32 lo,
             if (e & (1 << pe)) continue;
             const int e2 = e | (1 << pe);
             const u32 i = off + ((u32)(e >> (pe + 1)) | (base_hi << (3 - pe)));
-            const u64 W = __ldg(itw + i), Ws = __ldg(itws + i);
+            const ulonglong2 w = twiddle(itw, i);
+            const u64 W = w.x, Ws = w.y;
             const u64 X = x[e], Y = x[e2];
             const u64 S = X + Y;
             x[e] = S >= q2 ? S - q2 : S;
@@ -159,7 +163,7 @@ __device__ __forceinline__ u32 win_base(u32 set, u32 lo) { return ((set >> lo) <
 
 // Forward NTT of one polynomial: load(i) gives coefficient i in [0, 4q); store(i, v) receives slot i in [0, q).
 template <class Load, class Store>
-__device__ void ntt_forward_block(u64* sm, u32 N, u32 logN, const u64* tw, const u64* tws, u64 q, Load load,
+__device__ void ntt_forward_block(u64* sm, u32 N, u32 logN, const u64* tw, u64 q, Load load,
                                   Store store) {
     const u64 q2 = 2 * q;
     const u32 sets = N / NTT_E;
@@ -169,7 +173,7 @@ __device__ void ntt_forward_block(u64* sm, u32 N, u32 logN, const u64* tw, const
     for (u32 set = threadIdx.x; set < sets; set += blockDim.x) {
 #pragma unroll
         for (int e = 0; e < NTT_E; e++) x[e] = load(set | ((u32)e << lo));
-        fwd_window<3>(x, 0, lo, logN, tw, tws, q, q2);
+        fwd_window<3>(x, 0, lo, logN, tw, q, q2);
         if (lo == 0) {
 #pragma unroll
             for (int e = 0; e < NTT_E; e++) {
@@ -192,10 +196,10 @@ __device__ void ntt_forward_block(u64* sm, u32 N, u32 logN, const u64* tw, const
             for (int e = 0; e < NTT_E; e++) x[e] = sm[spad(base | ((u32)e << nlo))];
             const u32 bh = base >> (nlo + 4);
             switch (pe_top) {
-                case 3: fwd_window<3>(x, bh, nlo, logN, tw, tws, q, q2); break;
-                case 2: fwd_window<2>(x, bh, nlo, logN, tw, tws, q, q2); break;
-                case 1: fwd_window<1>(x, bh, nlo, logN, tw, tws, q, q2); break;
-                default: fwd_window<0>(x, bh, nlo, logN, tw, tws, q, q2); break;
+                case 3: fwd_window<3>(x, bh, nlo, logN, tw, q, q2); break;
+                case 2: fwd_window<2>(x, bh, nlo, logN, tw, q, q2); break;
+                case 1: fwd_window<1>(x, bh, nlo, logN, tw, q, q2); break;
+                default: fwd_window<0>(x, bh, nlo, logN, tw, q, q2); break;
             }
             if (nlo == 0) {
 #pragma unroll
@@ -216,7 +220,7 @@ __device__ void ntt_forward_block(u64* sm, u32 N, u32 logN, const u64* tw, const
 
 // Inverse NTT (with the 1/N factor): load(i) gives slot i in [0, 2q); store(i, v) receives coefficient i in [0, q).
 template <class Load, class Store>
-__device__ void ntt_inverse_block(u64* sm, u32 N, u32 logN, const u64* itw, const u64* itws, u64 q, u64 ninv,
+__device__ void ntt_inverse_block(u64* sm, u32 N, u32 logN, const u64* itw, u64 q, u64 ninv,
                                   u64 ninv_sh, Load load, Store store) {
     const u64 q2 = 2 * q;
     const u32 sets = N / NTT_E;
@@ -239,10 +243,10 @@ __device__ void ntt_inverse_block(u64* sm, u32 N, u32 logN, const u64* itw, cons
             }
             const u32 bh = base >> (wlo + 4);
             switch (pe_bot) {
-                case 0: inv_window<0>(x, bh, wlo, logN, itw, itws, q, q2); break;
-                case 1: inv_window<1>(x, bh, wlo, logN, itw, itws, q, q2); break;
-                case 2: inv_window<2>(x, bh, wlo, logN, itw, itws, q, q2); break;
-                default: inv_window<3>(x, bh, wlo, logN, itw, itws, q, q2); break;
+                case 0: inv_window<0>(x, bh, wlo, logN, itw, q, q2); break;
+                case 1: inv_window<1>(x, bh, wlo, logN, itw, q, q2); break;
+                case 2: inv_window<2>(x, bh, wlo, logN, itw, q, q2); break;
+                default: inv_window<3>(x, bh, wlo, logN, itw, q, q2); break;
             }
             if (last) {
 #pragma unroll
@@ -291,6 +295,7 @@ struct LayerDev {
     __half* A16;               // images [row_units][2][L][N/128][ktiles][5 chunks][128 slots x 32 terms]
     const RotDev* rots_all;    // every rotation of the layer, identity included (key = ~0u)
     u32 img, in_pad, n_rot_all, id_rot;  // in_pad = in_groups rounded up to 8; id_rot = the identity's index
+    u32 fused;                 // key switch inside the MAC (k_ksmac): no image buffer, no key-switch launch
 };
 
 enum { ST_NTT = 0, ST_KS = 1, ST_MAC = 2, ST_INTT = 3 };
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_ntt_inputs(const __grid_constant
     }
     const LimbC m = kp.limb[limb];
     ntt_forward_block(
-        sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q,
+        sm, N, kp.logN, kp.tw + 2 * (size_t)limb * N, m.q,
         [&](u32 i) { return shift >= 64 ? 0ull : (__ldg(src + i) >> shift) & mask; },
         [&](u32 i, u64 v) {
             dst[i] = v;
@@ -367,10 +372,10 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) k_ntt_plain(u64* __restrict__
     u64* poly = a + (size_t)blockIdx.x * N;
     const LimbC m = kp.limb[limb];
     if (!inverse)
-        ntt_forward_block(sm, N, kp.logN, kp.tw + (size_t)limb * N, kp.tw_sh + (size_t)limb * N, m.q,
+        ntt_forward_block(sm, N, kp.logN, kp.tw + 2 * (size_t)limb * N, m.q,
                           [&](u32 i) { return poly[i]; }, [&](u32 i, u64 v) { poly[i] = v; });
     else
-        ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
+        ntt_inverse_block(sm, N, kp.logN, kp.itw + 2 * (size_t)limb * N, m.q, m.ninv,
                           m.ninv_sh, [&](u32 i) { return poly[i]; }, [&](u32 i, u64 v) { poly[i] = v; });
 }
 
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_intt(const __grid_constant__ Bat
     const u64* s = Ly.isrc + c * Ly.isrc_stride + (size_t)y * N;
     u64* d = Ly.out + c * (2ull * L * N) + (size_t)y * N;
     const LimbC m = kp.limb[limb];
-    ntt_inverse_block(sm, N, kp.logN, kp.itw + (size_t)limb * N, kp.itw_sh + (size_t)limb * N, m.q, m.ninv,
+    ntt_inverse_block(sm, N, kp.logN, kp.itw + 2 * (size_t)limb * N, m.q, m.ninv,
                       m.ninv_sh, [&](u32 i) { return __ldg(s + i); }, [&](u32 i, u64 v) { d[i] = v; });
 }
 
@@ -1495,6 +1500,313 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
     if (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// ------------------------------------------------------------------ fused key switch + MAC
+// For layers whose output rows fit one CTA (at most 96 rows, one row tile), the key switch runs
+// inside the tensor-core MAC: producer warps compute, per K tile, the 32 rotated residues of the
+// tile's 128 destination slots and write their fp16 chunks straight into the shared-memory
+// operand stage the MMA reads, so rotated copies never leave the SM (Sec. 3.1: the hoisted
+// rotations feed the CMult/HAdd sum directly; Sec. 3.2.2: one reduction per lazy sum).
+// Roles: warp 0 copies the scalar tiles, warp 1 (lane 0) issues the MMAs, warps 2..17 produce
+// operands (four groups of 128 threads, eight consecutive terms each per K tile; a thread owns
+// a SOURCE slot, as in k_keyswitch) and run the epilogue.  Barriers (all bounded waits):
+//   full[s]    producers wrote stage s (16 warp arrivals) and its scalar tile landed (1 + tx)
+//   empty[s]   MMAs of stage s done (commit)
+//   acc_full / acc_empty as in k_mac_img.
+constexpr int KF_PROD_WARPS = 16;
+constexpr int KF_THREADS = (2 + KF_PROD_WARPS) * 32;
+constexpr int KF_STAGES = 3;
+constexpr u32 KF_B_OFF = KF_STAGES * TCI_A_BYTES;
+constexpr u32 KF_BAR_OFF = KF_B_OFF + KF_STAGES * TC_B_BYTES;
+constexpr u32 KF_SMEM_BYTES = KF_BAR_OFF + 128;
+static_assert(KF_SMEM_BYTES <= 227 * 1024, "fused MAC exceeds shared memory");
+
+template <bool PACKED, int LL, int MAXB>
+__global__ void __launch_bounds__(KF_THREADS, 1) k_ksmac(const __grid_constant__ Batch<MAXB> B, KP kp, u32 tmem_cols) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    constexpr int NR = PACKED ? 2 : 1;
+    constexpr int NB = 2 * KF_STAGES + 2;
+    constexpr int FULL = 0, EMPTY = KF_STAGES, ACC_FULL = 2 * KF_STAGES, ACC_EMPTY = 2 * KF_STAGES + 1;
+    const u32 N = kp.N, L = kp.L, logN = kp.logN;
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    u64* bars = reinterpret_cast<u64*>(tsm + KF_BAR_OFF);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + KF_BAR_OFF + NB * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + KF_BAR_OFF + NB * 8 + 4);
+
+    if (tid == 0) {
+        for (int i = 0; i < KF_STAGES; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(FULL + i)), "r"(KF_PROD_WARPS + 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_FULL)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_EMPTY)), "r"(KF_PROD_WARPS));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const u32 tmem = *tmem_slot;
+    auto wait = [&](int i, u32 parity) -> bool {
+        return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, nullptr);
+    };
+    auto arrive = [&](int i) { asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(i)) : "memory"); };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- scalar tiles
+        u32 g = 0;
+        TcItem it;
+        bool ok = true;
+        for (u32 item = blockIdx.x; ok && tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 bbytes = Ly.tc_rows_per_cta * TC_KTILE * 2, ktiles = Ly.Kpad / TC_KTILE;
+            for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                const u32 s = g % KF_STAGES;
+                const bool fr = g < KF_STAGES || wait(EMPTY + s, ((g / KF_STAGES) - 1) & 1);
+                if (!__all_sync(0xffffffffu, fr)) { ok = false; break; }
+                if (lane == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)), "r"(bbytes)
+                                 : "memory");
+                    const __half* bsrc = Ly.sc16 + (size_t)t * (Ly.tc_rows_per_cta * TC_KTILE);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(tsm + KF_B_OFF + s * TC_B_BYTES)),
+                        "l"(bsrc), "r"(bbytes), "r"(bar(FULL + s))
+                        : "memory");
+                }
+                __syncwarp();
+            }
+            (void)ktiles;
+            if (*abort_flag) ok = false;
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMAs (lane 0)
+        if (lane == 0) {
+            u32 g = 0, unit = 0;
+            TcItem it;
+            for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+                const u32 idesc = tc_idesc(TC_MTILE, it.nrows);
+                bool okk = true;
+                for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                    const u32 s = g % KF_STAGES, tseg = t % TC_SEG_TILES;
+                    if (tseg == 0) {
+                        if (unit > 0 && !wait(ACC_EMPTY, (unit - 1) & 1)) { okk = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                    }
+                    if (!wait(FULL + s, (g / KF_STAGES) & 1)) { okk = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const u32 a_base = smem_u32(tsm + s * TCI_A_BYTES), b_base = smem_u32(tsm + KF_B_OFF + s * TC_B_BYTES);
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+#pragma unroll
+                        for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                            const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
+                            const u64 bd = smem_desc(b_base + ks * 256);
+                            const u32 acc = (tseg > 0 || ks > 0) ? 1u : 0u;
+                            const u32 dt = tmem + (u32)(c * it.nrows);
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        bar(EMPTY + s)));
+                    if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            bar(ACC_FULL)));
+                        unit++;
+                    }
+                }
+                if (!okk) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- producers + epilogue
+        const u32 pt = tid - 64, grp = pt >> 7, t = pt & (TC_MTILE - 1);  // group of 8 terms, slot in tile
+        u32 g = 0, unit = 0;
+        TcItem it;
+        for (u32 item = blockIdx.x; tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 k = it.k, p = it.p, nt = it.n0 / TC_MTILE;
+            const LimbC m = kp.limb[k];
+            const int red = m.sm1 == 49 ? (m.delta ? 1 : 2) : 3;
+            const size_t ctw = 2ull * L * N, d_step = (size_t)LL * L * N, dd_step = (size_t)L * N;
+            const size_t r_step = (size_t)Ly.r_slots * ctw;
+            const u32 nterm = Ly.n_rot_all * Ly.in_pad;
+            u32 cur_rot = ~0u, y = 0, xl = t, src_base = 0;
+            u32 kl_[LL], kh_[LL];
+            bool ident = false;
+            bool okk = true;
+            for (u32 tt = 0; tt < it.n_tiles; tt++, g++) {
+                const u32 s = g % KF_STAGES;
+                const bool fr = g < KF_STAGES || wait(EMPTY + s, ((g / KF_STAGES) - 1) & 1);
+                if (!__all_sync(0xffffffffu, fr)) { okk = false; break; }
+                unsigned char* A = tsm + s * TCI_A_BYTES;
+                const u32 kk0 = tt * TC_KTILE + grp * 8;
+                u64 v[8];
+                u32 row = t;  // the zero terms past the last rotation go to row t
+                if (kk0 < nterm) {
+                    const u32 r = kk0 / Ly.in_pad, j0 = kk0 % Ly.in_pad;
+                    if (r != cur_rot) {
+                        // the rotation's source tile for destination tile nt, this thread's source
+                        // slot there and its destination x = src^-1(y); the keys of (x, p, limb)
+                        const RotDev rd = Ly.rots_all[r];
+                        const u32 x0 = nt * TC_MTILE;
+                        const u32 e0 = 2 * (__brev(x0) >> (32 - logN)) + 1;
+                        const u32 s0 = __brev((u32)((((u64)e0 * rd.galois) & (2ull * N - 1)) - 1) >> 1) >> (32 - logN);
+                        src_base = s0 & ~(TC_MTILE - 1);
+                        y = src_base + t;
+                        const u32 e = 2 * (__brev(y) >> (32 - logN)) + 1;
+                        const u32 x = __brev((u32)((((u64)e * rd.galois_inv) & (2ull * N - 1)) - 1) >> 1) >> (32 - logN);
+                        xl = x & (TC_MTILE - 1);
+                        ident = r == Ly.id_rot;
+                        if (!ident) {
+                            const u64* kb = Ly.ksk + (size_t)rd.key * LL * 2 * L * N + ((size_t)p * L + k) * N + x;
+#pragma unroll
+                            for (int dd = 0; dd < LL; dd++) {
+                                const u64 a = __ldg(kb + (size_t)dd * 2 * L * N);
+                                kl_[dd] = (u32)(a & 0x1FFFFFFu), kh_[dd] = (u32)(a >> 25);
+                            }
+                        }
+                        cur_rot = r;
+                    }
+                    row = xl;
+                    const u32 c_first = it.ru * Ly.in_groups + j0;
+                    const u32 nj = j0 >= Ly.in_groups ? 0u : min(8u, Ly.in_groups - j0);
+                    const u64* Rp = Ly.R + ((size_t)c_first * Ly.r_slots + Ly.r_id) * ctw + (size_t)k * N + y;
+                    const u64* Dp = Ly.D + (size_t)c_first * d_step + (size_t)k * N + y;
+                    if (ident) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; jj++) v[jj] = jj < (int)nj ? __ldg(Rp + jj * r_step + p * dd_step) : 0;
+                    } else if (red <= 2) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; jj++) {
+                            v[jj] = 0;
+                            if (jj >= (int)nj) continue;
+                            const u64* Dc = Dp + jj * d_step;
+                            u64 lo = 0, mid = 0, hi = 0;
+#pragma unroll
+                            for (int dd = 0; dd < LL; dd++) {
+                                const u64 dv = __ldg(Dc + dd * dd_step);
+                                const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                                mad_wide_u(lo, dl, kl_[dd]);
+                                mad_wide_u(hi, dh, kh_[dd]);
+                                mad_wide_u(mid, dl + dh, kl_[dd] + kh_[dd]);
+                            }
+                            mid -= lo + hi;
+                            if (p == 0) lo += __ldg(Rp + jj * r_step);  // + sigma(c0)
+                            v[jj] = red == 1 ? fold_reduce50(lo, mid, hi, m) : bred_split50(lo, mid, hi, m);
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 8; jj++) {
+                            v[jj] = 0;
+                            if (jj >= (int)nj) continue;
+                            const u64* Dc = Dp + jj * d_step;
+                            u64 lo = 0, mid = 0, hi = 0;
+#pragma unroll
+                            for (int dd = 0; dd < LL; dd++) {
+                                const u64 dv = __ldg(Dc + dd * dd_step);
+                                const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                                mad_wide_u(lo, dl, kl_[dd]);
+                                mad_wide_u(mid, dl, kh_[dd]);
+                                mad_wide_u(mid, dh, kl_[dd]);
+                                mad_wide_u(hi, dh, kh_[dd]);
+                            }
+                            if (p == 0) lo += __ldg(Rp + jj * r_step);
+                            v[jj] = bred128(((u128)hi << 50) + ((u128)mid << 25) + lo, m);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < 8; jj++) v[jj] = 0;
+                }
+                // the eight terms' chunks: row `row`, terms grp*8 .. grp*8+7 of the stage (16 bytes a chunk)
+                const u32 off = (row >> 3) * 512 + grp * 128 + (row & 7) * 16;
+#pragma unroll
+                for (int c = 0; c < TC_CHUNKS; c++) {
+                    u64 v4[KSI_JH];
+#pragma unroll
+                    for (int e = 0; e < KSI_JH; e++) v4[e] = v[e];
+                    const uint2 a = chunk_pack4(v4, c);
+#pragma unroll
+                    for (int e = 0; e < KSI_JH; e++) v4[e] = v[KSI_JH + e];
+                    const uint2 b = chunk_pack4(v4, c);
+                    *reinterpret_cast<uint4*>(A + c * TC_A_CHUNK_BYTES + off) = make_uint4(a.x, a.y, b.x, b.y);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) arrive(FULL + s);
+                if (tt % TC_SEG_TILES != TC_SEG_TILES - 1 && tt + 1 != it.n_tiles) continue;
+                // epilogue of segment seg (as k_mac_img; the 16 warps take every fourth 8-row block)
+                const u32 seg = tt / TC_SEG_TILES;
+                if (!__all_sync(0xffffffffu, wait(ACC_FULL, unit & 1))) { okk = false; break; }
+                unit++;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const u32 sp = warp & 3, quarter = (warp - 2) >> 2;
+                const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0;
+                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+                for (u32 cb = quarter * 8; cb < nrows; cb += 32) {
+                    u32 d[TC_CHUNKS][8];
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+                        const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * nrows) + cb;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
+                                       "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
+                                     : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    u64 rr[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const long long b = Ly.bias[(size_t)seg * Ly.tc_rows + row0 + cb + j];
+                        const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
+                        const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
+                        const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+                        rr[j] = bred128((u128)a, m);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; j += NR) {
+                        const u32 rw = row0 + cb + j;
+                        const u32 gg = rw / NR;
+                        if (gg >= Ly.out_groups) continue;
+                        u64 out = rr[j];
+                        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(rr[j + 1], pkv, m), m.q);
+                        u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
+                        if (seg > 0) out = addq(out, *o, m.q);
+                        *o = out;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) arrive(ACC_EMPTY);
+            }
+            if (!okk) break;
+        }
+    }
+    if (*abort_flag && tid == 0) {
+        for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
+        for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+    }
+}
+
 // ------------------------------------------------------------------ profiling
 struct Prof {
     std::mutex mu;
@@ -1566,7 +1878,7 @@ KP make_kp(const he_params* p) {
         kp.limb[k].ninv = p->ntt[k].ninv;
         kp.limb[k].ninv_sh = p->ntt[k].ninv_sh;
     }
-    kp.tw = T.tw, kp.tw_sh = T.tw_sh, kp.itw = T.itw, kp.itw_sh = T.itw_sh;
+    kp.tw = T.tw, kp.itw = T.itw;
     return kp;
 }
 
@@ -1649,11 +1961,11 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
-    bool tc = false, packed = false, dw = false, eager = false, img = false;
+    bool tc = false, packed = false, dw = false, eager = false, img = false, fused = false;
     u32 gt = 8, cl = 1;  // cl: CTAs per cluster of the operand-image MAC
     bool operator==(const MacVariant& o) const {
         return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img && cl == o.cl &&
-               (tc || eager || gt == o.gt);
+               fused == o.fused && (tc || eager || gt == o.gt);
     }
 };
 
@@ -1737,8 +2049,34 @@ void mac_img_launch(bool packed, u32 items, const Batch<MAXB>& B, const KP& kp, 
     CUDA_OK(cudaLaunchKernelEx(&cfg, kern, B, kp, cols));
 }
 
+template <int LL, int MAXB>
+void ksmac_launch(bool packed, u32 grid, const Batch<MAXB>& B, const KP& kp, u32 cols, cudaStream_t s) {
+    if (packed) {
+        allow_smem(k_ksmac<true, LL, MAXB>, KF_SMEM_BYTES);
+        k_ksmac<true, LL, MAXB><<<grid, KF_THREADS, KF_SMEM_BYTES, s>>>(B, kp, cols);
+    } else {
+        allow_smem(k_ksmac<false, LL, MAXB>, KF_SMEM_BYTES);
+        k_ksmac<false, LL, MAXB><<<grid, KF_THREADS, KF_SMEM_BYTES, s>>>(B, kp, cols);
+    }
+}
+
 template <int MAXB>
-void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+void launch_ksmac_b(const he_params* p, bool packed, u32 grid, const Batch<MAXB>& B, const KP& kp, u32 cols,
+                    cudaStream_t s) {
+    switch (p->L * p->l) {
+#define KF_CASE(v) \
+    case v: ksmac_launch<v, MAXB>(packed, grid, B, kp, cols, s); break;
+        KF_CASE(1) KF_CASE(2) KF_CASE(3) KF_CASE(4) KF_CASE(5) KF_CASE(6) KF_CASE(7) KF_CASE(8) KF_CASE(9)
+            KF_CASE(10) KF_CASE(12) KF_CASE(14) KF_CASE(15) KF_CASE(16)
+#undef KF_CASE
+        default:
+            fail(HE_EINVAL, "L * l must be at most 16 (and not 11 or 13)");
+    }
+}
+
+template <int MAXB>
+void launch_mac_b(const he_params* p, const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const KP& kp,
+                  cudaStream_t s) {
     if (mv.eager) {
         if (mv.packed) k_mac_eager<true, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
         else k_mac_eager<false, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
@@ -1749,6 +2087,10 @@ void launch_mac_b(const MacVariant& mv, u32 blocks, const Batch<MAXB>& B, const 
         u32 cols = 32;
         for (u32 i = 0; i < B.n; i++) cols = std::max(cols, B.L[i].tmem_cols);
         const u32 grid = std::min(blocks, (u32)sm_count());
+        if (mv.fused) {
+            launch_ksmac_b<MAXB>(p, mv.packed, grid, B, kp, cols, s);
+            return;
+        }
         if (mv.img) {
             switch (mv.cl) {
                 case 1: mac_img_launch<1, MAXB>(mv.packed, blocks, B, kp, cols, s); break;
@@ -1825,7 +2167,7 @@ void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector
                 check_launch("k_keyswitch");
                 break;
             case ST_MAC:
-                launch_mac_b<MAXB>(layers[c0]->mv, total, B, kp, s);
+                launch_mac_b<MAXB>(p, layers[c0]->mv, total, B, kp, s);
                 check_launch("k_mac");
                 break;
             default: {
@@ -1867,7 +2209,8 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
         // the operand-image layers and the others have different key-switch kernels
         StageTimer t(HE_STAGE_KEYSWITCH, s, timed);
         std::vector<const StageLayer*> grp[2];
-        for (auto& l : layers) grp[l.dev.img ? 1 : 0].push_back(&l);
+        for (auto& l : layers)
+            if (!l.dev.fused) grp[l.dev.img ? 1 : 0].push_back(&l);
         for (auto& g : grp)
             if (!g.empty()) go(ST_KS, g);
     }
@@ -1904,18 +2247,19 @@ const DeviceTables& device_tables(const he_params* p) {
     auto T = std::make_unique<DeviceTables>();
     T->device = dev;
     const size_t n = (size_t)p->L * p->N;
-    std::vector<u64> tw(n), tws(n), itw(n), itws(n);
-    for (u32 k = 0; k < p->L; k++) {
-        std::copy(p->ntt[k].tw.begin(), p->ntt[k].tw.end(), tw.begin() + (size_t)k * p->N);
-        std::copy(p->ntt[k].tw_sh.begin(), p->ntt[k].tw_sh.end(), tws.begin() + (size_t)k * p->N);
-        std::copy(p->ntt[k].itw.begin(), p->ntt[k].itw.end(), itw.begin() + (size_t)k * p->N);
-        std::copy(p->ntt[k].itw_sh.begin(), p->ntt[k].itw_sh.end(), itws.begin() + (size_t)k * p->N);
-    }
-    u64** dst[4] = {&T->tw, &T->tw_sh, &T->itw, &T->itw_sh};
-    std::vector<u64>* srcs[4] = {&tw, &tws, &itw, &itws};
-    for (int i = 0; i < 4; i++) {
-        CUDA_OK(cudaMalloc(dst[i], n * 8));
-        CUDA_OK(cudaMemcpy(*dst[i], srcs[i]->data(), n * 8, cudaMemcpyHostToDevice));
+    // twiddle and Shoup companion side by side: [L][N][2]
+    std::vector<u64> tw(2 * n), itw(2 * n);
+    for (u32 k = 0; k < p->L; k++)
+        for (u32 i = 0; i < p->N; i++) {
+            const size_t o = 2 * ((size_t)k * p->N + i);
+            tw[o] = p->ntt[k].tw[i], tw[o + 1] = p->ntt[k].tw_sh[i];
+            itw[o] = p->ntt[k].itw[i], itw[o + 1] = p->ntt[k].itw_sh[i];
+        }
+    u64** dst[2] = {&T->tw, &T->itw};
+    std::vector<u64>* srcs[2] = {&tw, &itw};
+    for (int i = 0; i < 2; i++) {
+        CUDA_OK(cudaMalloc(dst[i], 2 * n * 8));
+        CUDA_OK(cudaMemcpy(*dst[i], srcs[i]->data(), 2 * n * 8, cudaMemcpyHostToDevice));
     }
     p->dev.push_back(T.release());
     return *p->dev.back();
@@ -1928,9 +2272,7 @@ he_params::~he_params() {
         if (cudaGetDevice(&cur) == cudaSuccess) {
             cudaSetDevice(t->device);
             cudaFree(t->tw);
-            cudaFree(t->tw_sh);
             cudaFree(t->itw);
-            cudaFree(t->itw_sh);
             cudaSetDevice(cur);
         }
         delete t;
@@ -1946,7 +2288,7 @@ struct he_plan {
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
     bool packed = false, dw = false;
     u32 mac_groups = 8;
-    bool use_tc = false, eager = false, img = false;
+    bool use_tc = false, eager = false, img = false, fused = false;
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0, cl = 1;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
@@ -1991,7 +2333,9 @@ struct he_plan {
         L.A16 = img ? (__half*)(ws + off_A) : nullptr;
         if (use_tc && !img) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
-        s.mv.img = img, s.mv.cl = cl;
+        s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused;
+        L.fused = fused;
+        if (fused) L.A16 = nullptr;
         return s;
     }
 };
@@ -2089,17 +2433,14 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     bool limbs_fit = true;
     for (u64 qi : p->q) limbs_fit = limbs_fit && qi < (1ull << (10 * TC_CHUNKS));
     const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && limbs_fit;
-    if ((impl == 2 || impl == 4) && !tc_ok)
+    if ((impl == 2 || impl >= 4) && !tc_ok)
         fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
-    if (impl > 4) fail(HE_EINVAL, "mac_impl must be 0..4");
+    if (impl > 6) fail(HE_EINVAL, "mac_impl must be 0..6");
     if (tune && tune->tc_cluster && tune->tc_cluster != 2 && tune->tc_cluster != 4 && tune->tc_cluster != 8)
         fail(HE_EINVAL, "tc_cluster must be 0, 2, 4 or 8");
     P->eager = impl == 3;
     P->use_tc = tc_ok && impl != 1 && impl != 3;
-    // tensor-core layers take their operands as images written by the key switch, unless the
-    // in-kernel conversion form is asked for (mac_impl 4)
-    P->img = P->use_tc && impl != 4;
     P->in_pad = (lay.in_groups + 7) / 8 * 8;
     if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
     const u32 tc_rows_req = tune ? tune->tc_rows : 0;
@@ -2144,6 +2485,16 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 rows = lay.out_groups * NR;
         P->tc_rows = (rows + 15) / 16 * 16;
         P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
+        // the form of the contraction (measured on the ResNet-20 and VGG-16 stacks): a layer whose
+        // rows fit one CTA takes its rotated residues from the key switch as words and splits them
+        // into chunks in the MAC (4); a wider layer, whose row tiles would each split them again,
+        // takes operand images the key switch writes once (5); 6 runs the key switch inside the MAC
+        const bool one_tile = P->tc_rows <= P->tc_rows_per_cta;
+        const u32 form = (impl >= 4) ? impl : (one_tile ? 4u : 5u);
+        if (form == 6 && (!one_tile || (tune && tune->tc_cluster)))
+            fail(HE_EINVAL, "the fused key switch + MAC needs a layer whose rows fit one CTA and no cluster");
+        P->img = form != 4;
+        P->fused = form == 6;
         P->cl = 1;
         const u32 cl_req = tune ? tune->tc_cluster : 0;
         if (cl_req > 1) {
@@ -2151,11 +2502,12 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
             // tile are split into a multiple of cl_req tiles of at most 96 rows, none of them empty
             const u32 m = cl_req * ((P->tc_rows + TC_NMAX * cl_req - 1) / (TC_NMAX * cl_req));
             const u32 rpc = ((P->tc_rows + m - 1) / m + 15) / 16 * 16;
-            if (!P->img || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
+            if (!P->img || P->fused || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
                 fail(HE_EINVAL, "tc_cluster needs the image-form tensor-core MAC, no tc_rows, and at least " +
                                     std::to_string(16 * (m - 1) + 16) + " output rows");
             P->cl = cl_req, P->tc_rows_per_cta = rpc;
         }
+
         // terms: kk = j n_rot + rot for the in-kernel conversion form, rot in_pad + j for the image form
         const u32 k_terms = P->img ? P->n_rot * P->in_pad : P->K;
         P->tc_kpad = (k_terms + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
@@ -2201,9 +2553,9 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     P->off_D = align256(P->off_R + (size_t)lay.n_ct_in * P->r_slots * ctw * 8);
     P->off_O = align256(P->off_D + (size_t)lay.n_ct_in * p->L * p->l * p->L * p->N * 8);
     P->off_A = align256(P->off_O + (size_t)lay.n_ct_out * ctw * 8);
-    const size_t img_bytes = P->img ? (size_t)lay.row_units * 2 * p->L * (p->N / TC_MTILE) * (P->tc_kpad / TC_KTILE) *
-                                          IMG_HALVES * 2
-                                    : 0;
+    const size_t img_bytes = P->img && !P->fused ? (size_t)lay.row_units * 2 * p->L * (p->N / TC_MTILE) *
+                                                       (P->tc_kpad / TC_KTILE) * IMG_HALVES * 2
+                                                 : 0;
     P->ws_bytes = align256(P->off_A + img_bytes);
     (void)taps;
     return P;
@@ -2350,7 +2702,7 @@ extern "C" int he_conv_time(const he_params* p, const he_conv_desc* d, const int
 extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
     return guard([&] {
         if (!plan || !mac_impl) fail(HE_EINVAL, "null argument");
-        *mac_impl = plan->use_tc ? (plan->img ? 2 : 4) : (plan->eager ? 3 : 1);
+        *mac_impl = plan->use_tc ? (plan->fused ? 6 : (plan->img ? 5 : 4)) : (plan->eager ? 3 : 1);
     });
 }
 

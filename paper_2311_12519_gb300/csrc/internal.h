@@ -116,10 +116,8 @@ u64 big_div_small_quotient(const Big& a, const Big& b);
 // Per-device constant tables of one parameter set.
 struct DeviceTables {
     int device = -1;
-    u64* tw = nullptr;      // [L][N] psi^rev(k)
-    u64* tw_sh = nullptr;   // Shoup companions
-    u64* itw = nullptr;     // [L][N] psi^-rev(k)
-    u64* itw_sh = nullptr;
+    u64* tw = nullptr;      // [L][N][2] psi^rev(k) and its Shoup companion
+    u64* itw = nullptr;     // [L][N][2] psi^-rev(k) and its Shoup companion
 };
 
 }  // namespace hy

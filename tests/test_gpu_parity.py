@@ -258,12 +258,13 @@ def test_repeat_on_side_stream_and_host_path(small):
 
 
 # ---------------------------------------------------------------- both MAC implementations
-@pytest.mark.parametrize("impl", [1, 2, 3, 4])
+@pytest.mark.parametrize("impl", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("spec", [SMALL[0], SMALL[1], SMALL[4], SMALL[7], SMALL[11]])
 def test_mac_implementations(small, spec, impl):
-    """1 lazy CUDA-core, 2 tensor-core fed with operand images written by the key switch, 3 eager
-    (reduced after every CMult and HAdd, Sec. 3.2.2's conventional form), 4 tensor-core with
-    in-kernel fp16 conversion: all four give the oracle's words."""
+    """1 lazy CUDA-core, 2 tensor-core in the automatic form, 3 eager (reduced after every CMult
+    and HAdd, Sec. 3.2.2's conventional form), 4 tensor-core with in-kernel fp16 conversion, 5
+    tensor-core fed with operand images written by the key switch, 6 key switch fused into the
+    tensor-core MAC: all give the oracle's words."""
     small.layer(spec, mac_impl=impl)
 
 
@@ -280,7 +281,7 @@ def test_tensor_core_mac_is_chosen_when_exact(small):
     spec = dict(C_in=4, C_out=4, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
     d = H.conv_desc(**spec)
     gk = H.he_galois_keys(small.p, small.sk, H.he_layer_galois(small.p, d), synth.SEED_KEYS)
-    for wmax, expect in ((8, 2), (9, 1)):  # |s| = |v0 +- v1| <= 16 is the exactness bound
+    for wmax, expect in ((8, 4), (9, 1)):  # |s| = |v0 +- v1| <= 16 is the exactness bound (4: one row tile)
         w = np.full((4, 4, 3, 3), wmax)
         plan = H.he_conv_plan(small.p, gk, d, w)
         assert H.he_conv_info(plan) == expect
@@ -305,7 +306,7 @@ def test_tensor_core_mac_at_the_exactness_bound(pairs):
     lay = H.he_layout_for_layer(S.p, d)
     zero = np.zeros((lay.n_ct_in, 2, 2, 1024), dtype=np.uint64)
     w = np.full((4, C_in, 3, 3), 8)
-    for impl in (2, 4):
+    for impl in (2, 4, 5, 6):
         out_tc = gpu_layer(S.p, gk, d, w, zero, 2, 1024, mac_impl=impl)
         assert (out_tc == 0).all()
     # and on a real encryption, the tensor-core path equals the CUDA-core path word for word
@@ -315,18 +316,22 @@ def test_tensor_core_mac_at_the_exactness_bound(pairs):
     a = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=1)
     b = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=2)
     c = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=4)
-    assert (a == b).all() and (a == c).all()
+    e = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=5)
+    f = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=6)
+    assert (a == b).all() and (a == c).all() and (a == e).all() and (a == f).all()
     dec = H.he_decrypt_image(S.p, S.sk, d, b)
     assert (dec == conv.conv_plain(act, w, 1, 1, False, S.P.t)).all()
 
 
+@pytest.mark.parametrize("impl", [4, 5, 6])
 @pytest.mark.parametrize("C_in", [240, 512])
-def test_tensor_core_multi_segment_matches_oracle(small, C_in):
+def test_tensor_core_multi_segment_matches_oracle(small, C_in, impl):
     """Contractions longer than one exact fp32 accumulation: K = 2160 terms (two segments of at
     most 2048) and K = 4608 (three segments, the 512-channel layers of VGG-16), whose segment
-    results add mod q in the output; every output ciphertext word for word against the oracle."""
+    results add mod q in the output, in each tensor-core form (in-kernel conversion 4, operand
+    images 5, fused key switch 6); every output ciphertext word for word against the oracle."""
     spec = dict(C_in=C_in, C_out=6, H=4, W=4, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
-    small.layer(spec, label=C_in, mac_impl=2)
+    small.layer(spec, label=C_in, mac_impl=impl)
 
 
 @pytest.mark.parametrize("C_out,cluster", [(128, 0), (128, 2), (256, 4), (512, 8), (1024, 8), (200, 2)])

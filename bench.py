@@ -392,7 +392,7 @@ def run_gpu(args, rank, world):
     info = H.he_params_info(p)
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
-    tunes = [{} for _ in specs]
+    tunes = [({"mac_impl": args.mac_impl} if args.mac_impl else {}) for _ in specs]
     tuned = None
     if args.tuned:
         # per layer, the fastest packing, tile and MAC schedule on this ring, timed exhaustively
@@ -851,6 +851,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="the headline VGG-16 stack (8 images), or the ResNet-20 (1 image) or MobileNetV1 "
                          "(32 images) stack")
+    ap.add_argument("--mac-impl", type=int, default=0,
+                    help="force every layer's MAC form (he_tune.mac_impl; 0 = automatic per layer)")
     ap.add_argument("--layers", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     help="run only these layer indices of the stack (comma list), e.g. for profiler captures")
     ap.add_argument("--tuned", action="store_true",

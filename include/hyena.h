@@ -171,7 +171,9 @@ int he_decrypt_slots(const he_params* p, const he_seckey* sk, const uint64_t* ct
 typedef struct {
     uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block (0 -> default) */
     uint32_t mac_impl;       /* 0 auto, 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL if not exact)
-                                in the form auto picks: 4 when the layer's output rows fit one CTA, else 5;
+                                in the form auto picks: 4 when the layer's output rows fit one CTA and its
+                                input channel groups are not a multiple of 8 or its digit transforms fit
+                                64 MB, else 5;
                                 3 CUDA-core eager MAC (reduced after every term; for ablations);
                                 4 tensor-core MAC that splits the rotated residues into fp16 chunks itself;
                                 5 tensor-core MAC on operand images the key switch writes once;

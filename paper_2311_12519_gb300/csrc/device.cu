@@ -2485,12 +2485,16 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 rows = lay.out_groups * NR;
         P->tc_rows = (rows + 15) / 16 * 16;
         P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
-        // the form of the contraction (measured on the ResNet-20 and VGG-16 stacks): a layer whose
-        // rows fit one CTA takes its rotated residues from the key switch as words and splits them
-        // into chunks in the MAC (4); a wider layer, whose row tiles would each split them again,
-        // takes operand images the key switch writes once (5); 6 runs the key switch inside the MAC
+        // the form of the contraction, from per-layer timings of the ResNet-20, VGG-16 and
+        // MobileNetV1 stacks: operand images written once by the key switch (5) unless the layer's
+        // rows fit one CTA (no row tile would split the residues again) and either the image form
+        // would pad the input channel groups (first layers: 3 channels) or the digit transforms
+        // of all input ciphertexts fit in L2 (the word-form key switch then reuses them well); those
+        // take the key switch's words and split them in the MAC (4).  6 runs the key switch in the MAC.
         const bool one_tile = P->tc_rows <= P->tc_rows_per_cta;
-        const u32 form = (impl >= 4) ? impl : (one_tile ? 4u : 5u);
+        const size_t digit_bytes = (size_t)lay.n_ct_in * (p->L * p->l * p->L + 2 * p->L) * p->N * 8;
+        const bool words = one_tile && (P->in_pad != lay.in_groups || digit_bytes <= (64u << 20));
+        const u32 form = (impl >= 4) ? impl : (words ? 4u : 5u);
         if (form == 6 && (!one_tile || (tune && tune->tc_cluster)))
             fail(HE_EINVAL, "the fused key switch + MAC needs a layer whose rows fit one CTA and no cluster");
         P->img = form != 4;

@@ -325,47 +325,56 @@ def verify_outputs(H, p, sk, info, workload, specs, descs, d_outs, rank, index):
     return res
 
 
-# 32x32 -> 64-bit multiply-adds (mad.wide.u32) per clock per SM, from a throughput probe on this GPU
+# 32x32 -> 64-bit multiply-adds (mad.wide.u32) per clock per SM on this GPU, measured by a
+# throughput probe (eight independent chains per thread, 2048 threads per SM)
 MAD_WIDE_PER_CLK_SM = 28.5
+# wide-product equivalents per Shoup butterfly: a*w mod 2^64 and Q*q mod 2^64 (one wide product and
+# two 32-bit products each, a 32-bit product counted as half a wide one) and the high half of a*w'
+# (four wide products)
+WIDE_PER_BUTTERFLY = 8
 
 
 def stage_rooflines(stages, counts, steps, peaks, N, sm_mhz=None):
-    """Sec. 8(d)'s roofline of each stage kernel of the batched step, from its event-timed
-    duration: NTTs 16 N bytes per transform, the key switch its key stream plus the digit and c0
-    transforms it reads, the tensor-core MAC 10 fp16 flops per modMAC (five 10-bit chunks, one
-    multiply-add each) against the dense fp16 tensor peak (= the measured bf16 peak).  The key
-    switch also gets an ALU view: modMAC/s against 3 mad.wide per modMAC (Karatsuba products) at
-    the probed mad.wide rate, 152 SMs and the SM clock."""
+    """The roofline of each stage kernel of the batched step, from its event-timed duration, in
+    two views: Sec. 8(d)'s memory view (NTTs 16 N bytes per transform, the key switch its key
+    stream plus the digit and c0 transforms it reads, against the measured HBM copy bandwidth)
+    and the arithmetic view (the tensor-core MAC at 10 fp16 flops per modMAC -- five 10-bit chunks,
+    one multiply-add each -- against the measured dense bf16 = fp16 tensor peak; the key switch at
+    3 mad.wide per modMAC (Karatsuba products) and the NTTs at WIDE_PER_BUTTERFLY per butterfly,
+    against the probed mad.wide rate x 152 SMs x the SM clock).  The view with the larger
+    fraction is the binding one and is reported first."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     tc = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
     mhz = float(sm_mhz or peaks.get("sm_max_mhz", 2070.0))
-    alu_modmac = MAD_WIDE_PER_CLK_SM * 152 * mhz * 1e6 / 3
+    wide = MAD_WIDE_PER_CLK_SM * 152 * mhz * 1e6  # mad.wide per second
     out = {}
     for st, (ms, launches) in stages.items():
         if not launches:  # e.g. no key-switch launch when every layer's key switch is fused
             out[st] = None
             continue
         sec = ms / 1000 / max(1, steps)
-        if st == "ntt_in":
-            a = counts["ntt_in_transforms"] * 16 * N
-            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
-        elif st == "ntt_out":
-            a = counts["ntt_out_transforms"] * 16 * N
-            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm}
+        views = []
+        if st in ("ntt_in", "ntt_out"):
+            tr = counts[st + "_transforms"]
+            views.append({"bound": "hbm", "algorithmic": tr * 16 * N, "unit": "GB/s", "peak": hbm, "scale": 1e9})
+            views.append({"bound": "alu", "algorithmic": tr * (N // 2) * (N.bit_length() - 1), "unit": "Tbutterfly/s",
+                          "peak": wide / WIDE_PER_BUTTERFLY / 1e12, "scale": 1e12})
         elif st == "keyswitch":
-            a = counts["ks_bytes"]
-            r = {"bound": "hbm", "algorithmic": a, "unit": "GB/s", "peak": hbm,
-                 "alu_view": {"modmac_per_s": counts["ks_modmac_stage"] / sec if sec else None,
-                              "peak_modmac_per_s": alu_modmac,
-                              "frac": counts["ks_modmac_stage"] / sec / alu_modmac if sec else None}}
+            views.append({"bound": "hbm", "algorithmic": counts["ks_bytes"], "unit": "GB/s", "peak": hbm, "scale": 1e9})
+            views.append({"bound": "alu", "algorithmic": counts["ks_modmac_stage"], "unit": "TmodMAC/s",
+                          "peak": wide / 3 / 1e12, "scale": 1e12})
         else:
-            a = 10 * counts["conv_modmac"]
-            r = {"bound": "tensor", "algorithmic": a, "unit": "TFLOP/s", "peak": tc,
-                 "fused_key_switch": {"key_and_digit_bytes": counts["mac_ks_bytes"],
-                                      "modmac": counts["mac_ks_modmac"]}}
-        scale = 1e9 if r["unit"] == "GB/s" else 1e12
-        r["achieved"] = a / sec / scale if sec else None
-        r["frac"] = r["achieved"] / r["peak"] if sec else None
+            views.append({"bound": "tensor", "algorithmic": 10 * counts["conv_modmac"], "unit": "TFLOP/s", "peak": tc,
+                          "scale": 1e12,
+                          "fused_key_switch": {"key_and_digit_bytes": counts["mac_ks_bytes"],
+                                               "modmac": counts["mac_ks_modmac"]}})
+        for v in views:
+            v["achieved"] = v["algorithmic"] / sec / v.pop("scale")
+            v["frac"] = v["achieved"] / v["peak"]
+        views.sort(key=lambda v: -v["frac"])
+        r = dict(views[0])
+        if len(views) > 1:
+            r["other_view"] = views[1]
         r["ms_per_step"] = ms / max(1, steps)
         r["launches_per_step"] = launches / max(1, steps)
         out[st] = r
@@ -393,6 +402,14 @@ def run_gpu(args, rank, world):
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
     tunes = [({"mac_impl": args.mac_impl} if args.mac_impl else {}) for _ in specs]
+    if args.tc_cluster:
+        # clusters where the layer is wide enough to take them (more than one row tile per CTA pair)
+        p0 = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=50)
+        for i, s in enumerate(specs):
+            if H.he_conv_check(p0, H.conv_desc(**s), synth.stack_inputs(wl, index[i], H.he_params_info(p0).t)[1],
+                               tc_cluster=args.tc_cluster) == H.HE_OK:
+                tunes[i]["tc_cluster"] = args.tc_cluster
+        H.he_params_destroy(p0)
     tuned = None
     if args.tuned:
         # per layer, the fastest packing, tile and MAC schedule on this ring, timed exhaustively
@@ -548,9 +565,10 @@ def run_gpu(args, rank, world):
     roof["traffic"] = prof[1] if prof and src.startswith(prof[0]) else None
     roof.update(kernel=kname[top], per_launch="one launch per stage and wave; achieved = algorithmic units of the "
                 "step / the kernel's event-timed time in the step",
-                peak_source="MEASURED_PEAKS.json " + ("hbm_gbs" if roof["unit"] == "GB/s" else
-                                                      "bf16_tflops_sustained (fp16 dense = bf16 dense)")
-                + " (of measured)")
+                peak_source={"GB/s": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                             "TFLOP/s": "MEASURED_PEAKS.json bf16_tflops_sustained, fp16 dense = bf16 dense (of measured)"}
+                .get(roof["unit"], "derived: probed mad.wide rate %.1f/clk/SM x 152 SMs x SM clock %s MHz" % (
+                    MAD_WIDE_PER_CLK_SM, clocks_b.get("sm_mhz"))))
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         layers = sorted({index[min(1, len(index) - 1)], index[-1]})
@@ -851,6 +869,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="the headline VGG-16 stack (8 images), or the ResNet-20 (1 image) or MobileNetV1 "
                          "(32 images) stack")
+    ap.add_argument("--tc-cluster", type=int, default=0,
+                    help="run the image-form MAC of layers wider than one row tile in clusters of this many CTAs")
     ap.add_argument("--mac-impl", type=int, default=0,
                     help="force every layer's MAC form (he_tune.mac_impl; 0 = automatic per layer)")
     ap.add_argument("--layers", type=lambda v: [int(x) for x in v.split(",")], default=None,

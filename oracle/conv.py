@@ -275,6 +275,66 @@ def ct_positions(lay: Layout, c: int) -> list[tuple[int, int, int, int, int]]:
     return res
 
 
+# ---------------------------------------------------------------- polyphase stride 2
+# Reading of Sec. 2.4 for stride 2 (the paper is silent on stride): a 3x3 stride-2 convolution with
+# zero padding 1 is a stride-1 convolution over the four phase planes of its input,
+#   plane (a, b)[u][v] = in[2u + a][2v + b],  a, b in {0, 1},
+# because tap (dy, dx) of output (y, x) reads in[2y + dy][2x + dx] = plane (dy mod 2, dx mod 2) at
+# (y + floor(dy / 2), x + floor(dx / 2)): plane a = 0 only at row offset 0 (dy = 0), plane a = 1 at
+# row offsets -1 (dy = -1) and 0 (dy = +1), likewise for columns.  The derived layer has 4 Cp input
+# channels c' = (2a + b) Cp + c (Cp = C_in rounded up to c_n), planes of ceil(H/2) x ceil(W/2),
+# a 3x3 kernel whose taps at offset +1 are zero, stride 1, and its output is the stride-2 output.
+# A depthwise layer becomes a dense derived layer in which output channel o reads the four planes
+# of channel o only.
+
+def polyphase_planes(act: np.ndarray, c_n: int) -> np.ndarray:
+    """[I][C][H][W] -> [I][4 Cp][ceil(H/2)][ceil(W/2)] phase planes, channel (2a + b) Cp + c."""
+    I, C, H, W = act.shape
+    Cp = -(-C // c_n) * c_n
+    Hh, Wh = -(-H // 2), -(-W // 2)
+    out = np.zeros((I, 4 * Cp, Hh, Wh), dtype=np.int64)
+    for a in range(2):
+        for b in range(2):
+            plane = act[:, :, a::2, b::2]
+            out[:, (2 * a + b) * Cp:(2 * a + b) * Cp + C, :plane.shape[2], :plane.shape[3]] = plane
+    return out
+
+
+def polyphase_weights(weights: np.ndarray, C_in: int, c_n: int, depthwise: bool) -> np.ndarray:
+    """[O][C_in or 1][3][3] stride-2 weights -> [O][4 Cp][3][3] weights of the derived stride-1
+    layer: tap (dy', dx') of plane (a, b) is tap (2 dy' + a, 2 dx' + b) of the original, zero where
+    that tap lies outside [-1, 1]."""
+    O = weights.shape[0]
+    Cp = -(-C_in // c_n) * c_n
+    out = np.zeros((O, 4 * Cp, 3, 3), dtype=np.int64)
+    for a in range(2):
+        for b in range(2):
+            for dyp in (-1, 0, 1):
+                for dxp in (-1, 0, 1):
+                    dy, dx = 2 * dyp + a, 2 * dxp + b
+                    if not (-1 <= dy <= 1 and -1 <= dx <= 1):
+                        continue
+                    for o in range(O):
+                        if depthwise:
+                            if o < C_in:
+                                out[o, (2 * a + b) * Cp + o, dyp + 1, dxp + 1] = weights[o, 0, dy + 1, dx + 1]
+                        else:
+                            out[o, (2 * a + b) * Cp:(2 * a + b) * Cp + C_in, dyp + 1, dxp + 1] = \
+                                weights[o, :, dy + 1, dx + 1]
+    return out
+
+
+def polyphase_spec(spec: dict) -> dict:
+    """The derived stride-1 layer of a 3x3 stride-2 layer (a Layout spec)."""
+    if spec["stride"] != 2 or spec["kh"] != 3:
+        raise ValueError("polyphase packing is for 3x3 stride-2 layers")
+    c_n = spec["c_n"]
+    Cp = -(-spec["C_in"] // c_n) * c_n
+    d = dict(spec, C_in=4 * Cp, H=-(-spec["H"] // 2), W=-(-spec["W"] // 2), stride=1, depthwise=False)
+    d.pop("polyphase", None)
+    return d
+
+
 # ---------------------------------------------------------------- keys used
 def rotation_plan(P: Params, lay: Layout):
     """List of (tap index, d, Galois element) for every rotated copy of an

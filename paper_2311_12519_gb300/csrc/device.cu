@@ -2446,6 +2446,37 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     const u32 tc_rows_req = tune ? tune->tc_rows : 0;
     if (tc_rows_req && (tc_rows_req % 16 || tc_rows_req > (u32)TC_NMAX))
         fail(HE_EINVAL, "tc_rows must be a multiple of 16, at most 96");
+    if (P->use_tc) {
+        const u32 rows = lay.out_groups * NR;
+        P->tc_rows = (rows + 15) / 16 * 16;
+        P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
+        // the form of the contraction, from per-layer timings of the ResNet-20, VGG-16 and
+        // MobileNetV1 stacks: operand images written once by the key switch (5) unless the layer's
+        // rows fit one CTA (no row tile would split the residues again) and either the image form
+        // would pad the input channel groups (first layers: 3 channels) or the digit transforms
+        // of all input ciphertexts fit in L2 (the word-form key switch then reuses them well); those
+        // take the key switch's words and split them in the MAC (4).  6 runs the key switch in the MAC.
+        const bool one_tile = P->tc_rows <= P->tc_rows_per_cta;
+        const size_t digit_bytes = (size_t)lay.n_ct_in * (p->L * p->l * p->L + 2 * p->L) * p->N * 8;
+        const bool words = one_tile && (P->in_pad != lay.in_groups || digit_bytes <= (64u << 20));
+        const u32 form = (impl >= 4) ? impl : (words ? 4u : 5u);
+        if (form == 6 && (!one_tile || (tune && tune->tc_cluster)))
+            fail(HE_EINVAL, "the fused key switch + MAC needs a layer whose rows fit one CTA and no cluster");
+        P->img = form != 4;
+        P->fused = form == 6;
+        P->cl = 1;
+        const u32 cl_req = tune ? tune->tc_cluster : 0;
+        if (cl_req > 1) {
+            // clusters of cl_req CTAs share each operand image by multicast: the row tiles of a slot
+            // tile are split into a multiple of cl_req tiles of at most 96 rows, none of them empty
+            const u32 m = cl_req * ((P->tc_rows + TC_NMAX * cl_req - 1) / (TC_NMAX * cl_req));
+            const u32 rpc = ((P->tc_rows + m - 1) / m + 15) / 16 * 16;
+            if (!P->img || P->fused || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
+                fail(HE_EINVAL, "tc_cluster needs the image-form tensor-core MAC, no tc_rows, and at least " +
+                                    std::to_string(16 * (m - 1) + 16) + " output rows");
+            P->cl = cl_req, P->tc_rows_per_cta = rpc;
+        }
+    }
     if (host_only) return P;
     // device data
     CUDA_OK(cudaGetDevice(&P->device));
@@ -2482,36 +2513,6 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     CUDA_OK(cudaMalloc(&P->d_err, sizeof(int)));
     CUDA_OK(cudaMemset(P->d_err, 0, sizeof(int)));
     if (P->use_tc) {
-        const u32 rows = lay.out_groups * NR;
-        P->tc_rows = (rows + 15) / 16 * 16;
-        P->tc_rows_per_cta = std::min<u32>(tc_rows_req ? tc_rows_req : TC_NMAX, P->tc_rows);
-        // the form of the contraction, from per-layer timings of the ResNet-20, VGG-16 and
-        // MobileNetV1 stacks: operand images written once by the key switch (5) unless the layer's
-        // rows fit one CTA (no row tile would split the residues again) and either the image form
-        // would pad the input channel groups (first layers: 3 channels) or the digit transforms
-        // of all input ciphertexts fit in L2 (the word-form key switch then reuses them well); those
-        // take the key switch's words and split them in the MAC (4).  6 runs the key switch in the MAC.
-        const bool one_tile = P->tc_rows <= P->tc_rows_per_cta;
-        const size_t digit_bytes = (size_t)lay.n_ct_in * (p->L * p->l * p->L + 2 * p->L) * p->N * 8;
-        const bool words = one_tile && (P->in_pad != lay.in_groups || digit_bytes <= (64u << 20));
-        const u32 form = (impl >= 4) ? impl : (words ? 4u : 5u);
-        if (form == 6 && (!one_tile || (tune && tune->tc_cluster)))
-            fail(HE_EINVAL, "the fused key switch + MAC needs a layer whose rows fit one CTA and no cluster");
-        P->img = form != 4;
-        P->fused = form == 6;
-        P->cl = 1;
-        const u32 cl_req = tune ? tune->tc_cluster : 0;
-        if (cl_req > 1) {
-            // clusters of cl_req CTAs share each operand image by multicast: the row tiles of a slot
-            // tile are split into a multiple of cl_req tiles of at most 96 rows, none of them empty
-            const u32 m = cl_req * ((P->tc_rows + TC_NMAX * cl_req - 1) / (TC_NMAX * cl_req));
-            const u32 rpc = ((P->tc_rows + m - 1) / m + 15) / 16 * 16;
-            if (!P->img || P->fused || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
-                fail(HE_EINVAL, "tc_cluster needs the image-form tensor-core MAC, no tc_rows, and at least " +
-                                    std::to_string(16 * (m - 1) + 16) + " output rows");
-            P->cl = cl_req, P->tc_rows_per_cta = rpc;
-        }
-
         // terms: kk = j n_rot + rot for the in-kernel conversion form, rot in_pad + j for the image form
         const u32 k_terms = P->img ? P->n_rot * P->in_pad : P->K;
         P->tc_kpad = (k_terms + TC_KTILE - 1) / TC_KTILE * TC_KTILE;

@@ -278,17 +278,17 @@ def he_selftest_bounded_wait(stream=0):
     return load().he_selftest_bounded_wait(stream)
 
 
-def he_conv_check(p, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0):
+def he_conv_check(p, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0, tc_cluster=0):
     """HE_OK (0) if he_conv_plan would accept the configuration, else its error code (host only)."""
     w = np.ascontiguousarray(weights, dtype=np.int32)
-    t = he_tune(mac_groups, mac_impl, tc_rows)
+    t = he_tune(mac_groups, mac_impl, tc_rows, tc_cluster)
     return load().he_conv_check(p, ctypes.byref(d), _ptr(w), ctypes.byref(t))
 
 
-def he_conv_time(p, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0, reps=3, stream=0):
+def he_conv_time(p, d: he_conv_desc, weights, mac_groups=0, mac_impl=0, tc_rows=0, reps=3, stream=0, tc_cluster=0):
     """(total ms, [ntt_in, keyswitch, mac, ntt_out] ms): medians over `reps` timed forwards."""
     w = np.ascontiguousarray(weights, dtype=np.int32)
-    t = he_tune(mac_groups, mac_impl, tc_rows)
+    t = he_tune(mac_groups, mac_impl, tc_rows, tc_cluster)
     st = (ctypes.c_float * 4)()
     tot = ctypes.c_float()
     _check(load().he_conv_time(p, ctypes.byref(d), _ptr(w), ctypes.byref(t), reps, stream, st, ctypes.byref(tot)),

@@ -206,3 +206,20 @@ def test_noalloc_scratch_size_matches_the_header():
     inc = H._build.os.path.join(H._build.os.path.dirname(H._build.HERE), "include", "hyena.h")
     m = re.search(r"#define\s+HE_NOALLOC_MAX_SCRATCH_BYTES\s+(\d+)u?", open(inc).read())
     assert m and int(m.group(1)) == H.HE_NOALLOC_MAX_SCRATCH_BYTES
+
+
+def test_cluster_and_form_choices_are_checked_without_a_device():
+    """he_conv_check applies the tensor-core form and cluster rules on the host: clusters need a
+    layer wider than one row tile, the fused form a layer that fits one."""
+    p = H.he_params_create(1024, 2, decomp_bits=25)
+    narrow = H.conv_desc(C_in=6, C_out=16, H=3, W=3, kh=3, stride=1, n_images=1, c_n=2)
+    wide = H.conv_desc(C_in=6, C_out=512, H=3, W=3, kh=3, stride=1, n_images=1, c_n=2)
+    wn, ww = synth.weights((16, 6, 3, 3)), synth.weights((512, 6, 3, 3))
+    assert H.he_conv_check(p, narrow, wn, tc_cluster=2) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, tc_cluster=2) == H.HE_OK
+    assert H.he_conv_check(p, wide, ww, tc_cluster=8) == H.HE_OK
+    assert H.he_conv_check(p, wide, ww, tc_cluster=3) == H.HE_EINVAL
+    assert H.he_conv_check(p, narrow, wn, mac_impl=6) == H.HE_OK
+    assert H.he_conv_check(p, wide, ww, mac_impl=6) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, mac_impl=7) == H.HE_EINVAL
+    H.he_params_destroy(p)

@@ -158,3 +158,42 @@ def test_he_conv_with_chosen_tiles_decrypts_to_conv(P256, case, tile):
     got, ref, out, s = _run(P256, lay)
     assert (got == ref).all()
     assert max(bfv.noise_of(P256, s, c) for c in out) < P256.delta // 2
+
+
+# ---------------------------------------------------------------- polyphase stride 2
+@pytest.mark.parametrize("shape", [(2, 3, 7, 9, 5, False, 2), (1, 4, 8, 8, 4, True, 2), (1, 3, 5, 5, 3, True, 1),
+                                   (2, 2, 6, 7, 6, False, 1)])
+def test_polyphase_planes_and_weights_give_the_stride2_conv(shape):
+    """The derived stride-1 layer on the phase planes computes the stride-2 convolution (plaintext,
+    brute-force definition of both)."""
+    I, C, H, W, O, dw, c_n = shape
+    t = 1032193
+    act = synth.activations((I, C, H, W), t, label=H)
+    wt = synth.weights((O, 1 if dw else C, 3, 3), label=W)
+    planes = conv.polyphase_planes(act, c_n)
+    w2 = conv.polyphase_weights(wt, C, c_n, dw)
+    assert planes.shape == (I, 4 * (-(-C // c_n) * c_n), -(-H // 2), -(-W // 2))
+    assert (w2[:, :, 2, :] == 0).all() and (w2[:, :, :, 2] == 0).all()  # no tap at offset +1
+    assert (conv.conv_plain(planes, w2, 1, 1, False, t) == conv.conv_plain(act, wt, 2, 1, dw, t)).all()
+
+
+@pytest.mark.parametrize("spec", [
+    dict(C_in=3, C_out=5, H=7, W=9, kh=3, stride=2, depthwise=False, n_images=2, c_n=2),
+    dict(C_in=4, C_out=4, H=8, W=6, kh=3, stride=2, depthwise=True, n_images=2, c_n=2),
+    dict(C_in=3, C_out=3, H=5, W=7, kh=3, stride=2, depthwise=True, n_images=1, c_n=1),
+])
+def test_polyphase_he_conv_decrypts_to_stride2_conv(P256, spec):
+    """Encrypted: the Hyena layer of the derived stride-1 layer, on the encrypted phase planes,
+    decrypts to (2k) x the stride-2 convolution at every output position."""
+    P = P256
+    act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), P.t, label=spec["H"])
+    wt = synth.weights((spec["C_out"], 1 if spec["depthwise"] else spec["C_in"], 3, 3), label=spec["W"])
+    lay = conv.Layout(N=P.N, **conv.polyphase_spec(spec))
+    planes = conv.polyphase_planes(act, spec["c_n"])
+    w2 = conv.polyphase_weights(wt, spec["C_in"], spec["c_n"], spec["depthwise"])
+    s = bfv.keygen(P, synth.SEED_KEYS)
+    ksk = {g: bfv.galois_key(P, s, g, synth.SEED_KEYS) for g in conv.galois_elements(P, lay)}
+    cts = conv.encrypt_image(P, lay, s, planes, synth.SEED_ENC)
+    out = conv.he_conv(P, lay, w2, cts, ksk)
+    dec = conv.decrypt_image(P, lay, s, out)
+    assert (dec == conv.conv_plain(act, wt, 2, 1, spec["depthwise"], P.t)).all()

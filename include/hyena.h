@@ -126,6 +126,12 @@ typedef struct {
                                 tiles, each as large as fits.  Given tiles must fit the image, be
                                 multiples of the stride unless they span the image, and their padded
                                 block (tile_h + kh - 1)(tile_w + kh - 1) must fit N/2 slots. */
+    uint32_t polyphase;      /* 3x3 stride-2 layers only: 1 packs the four phase planes
+                                in[2u + a][2v + b] of the input (channel (2a + b) Cp + c, Cp = C_in
+                                rounded up to c_n) and runs the layer as a stride-1 layer on them,
+                                with taps at offsets -1 and 0 only (the paper leaves stride open,
+                                Sec. 2.4); tiles then refer to the ceil(H/2) x ceil(W/2) planes.
+                                0 computes the stride-1 result and keeps every second position. */
 } he_conv_desc;
 
 typedef struct {

@@ -595,8 +595,10 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
 #pragma unroll 2
         for (u32 kk = 0; kk < kcn; kk++) {
             const u32 kg = kc0 + kk;
-            const u32 ct = DW ? ru * in_groups + g0 : ru * in_groups + kg / n_rot;
-            const u32 rot = DW ? kg : kg % n_rot;
+            // depthwise: the term's input ciphertext is phase kg / n_rot of output group g0
+            // (one phase unless polyphase packing gives four)
+            const u32 ct = DW ? ru * in_groups + (kg / n_rot) * out_groups + g0 : ru * in_groups + kg / n_rot;
+            const u32 rot = kg % n_rot;
             const u64 v = __ldg(base + ((size_t)ct * n_rot + rot) * ctw);
             const int vl = (int)(v & 0x1FFFFFFull), vh = (int)(v >> 25);
             int sv[NSP];
@@ -2383,7 +2385,10 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     if (p->L * p->l > 16) fail(HE_EINVAL, "L * l must be at most 16");
     // Hadamard scalars s0 = v0 + v1, s1 = v0 - v1 (Eq. 1 without the 1/2)
     const u32 NR = P->packed ? 2 : 1;
-    P->K = P->dw ? P->n_rot : lay.in_groups * P->n_rot;
+    // a depthwise output reads its own channel's input ciphertext, or with polyphase packing the
+    // ciphertexts of its channel's four phase planes (input groups phase-major: phase * out_groups + g)
+    const u32 phases = d->polyphase ? 4 : 1;
+    P->K = P->dw ? phases * P->n_rot : lay.in_groups * P->n_rot;
     if (P->K > (1u << 14)) fail(HE_EINVAL, "too many accumulation terms (C_in kh^2 > 16384)");
     {
         // every stage of the layer must fit one launch (grid x < 2^31) and 32-bit block indices
@@ -2396,7 +2401,18 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     }
     std::vector<int16_t> sc((size_t)lay.out_groups * NR * P->K, 0);
     const u32 wcin = P->dw ? 1 : d->C_in;
+    // weight of output channel o, input channel i and tap; with polyphase packing i is a plane
+    // channel (phase (a, b) = i / Cp, channel i % Cp) and the 3x3 tap (dy', dx') of the derived
+    // stride-1 layer is tap (2 dy' + a, 2 dx' + b) of the layer, zero where that lies outside the kernel
+    const u32 Cp = (d->C_in + d->c_n - 1) / d->c_n * d->c_n;
     auto W = [&](u32 o, u32 i, u32 tap) -> i64 {
+        if (d->polyphase) {
+            const u32 ph = i / Cp, c = i % Cp;
+            const int dy = 2 * ((int)(tap / 3) - 1) + (int)(ph >> 1), dx = 2 * ((int)(tap % 3) - 1) + (int)(ph & 1);
+            if (ph >= 4 || dy < -1 || dy > 1 || dx < -1 || dx > 1) return 0;
+            i = c;
+            tap = (u32)((dy + 1) * 3 + (dx + 1));
+        }
         if (o >= d->C_out || i >= d->C_in) return 0;
         if (P->dw) return o == i ? weights[(size_t)o * taps + tap] : 0;
         return weights[((size_t)o * wcin + i) * taps + tap];
@@ -2405,7 +2421,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     for (u32 g = 0; g < lay.out_groups; g++) {
         double s0q = 0, s1q = 0, sab = 0;
         for (u32 kk = 0; kk < P->K; kk++) {
-            u32 j = P->dw ? g : kk / P->n_rot, r = kk % P->n_rot;
+            u32 j = P->dw ? (kk / P->n_rot) * lay.out_groups + g : kk / P->n_rot, r = kk % P->n_rot;
             u32 tap = rl[r].tap, dg = rl[r].d;
             i64 s0, s1 = 0;
             if (P->packed) {

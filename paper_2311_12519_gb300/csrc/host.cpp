@@ -723,38 +723,53 @@ u32 rotation_galois(const he_params* p, i64 step) {
     return (u32)g;
 }
 
+// The plane geometry a layer's slots hold: the image itself, or for polyphase packing the four
+// phase planes in[2u + a][2v + b] of ceil(H/2) x ceil(W/2), each a channel of a stride-1 layer.
+void plane_geometry(const he_conv_desc* d, u32* H, u32* W, u32* S, u32* C_planes) {
+    if (d->polyphase) {
+        *H = (d->H + 1) / 2, *W = (d->W + 1) / 2, *S = 1;
+        *C_planes = 4 * ((d->C_in + d->c_n - 1) / d->c_n * d->c_n);
+    } else {
+        *H = d->H, *W = d->W, *S = d->stride, *C_planes = d->C_in;
+    }
+}
+
 void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* o) {
     if (!d->C_in || !d->C_out || !d->H || !d->W || !d->n_images) fail(HE_EINVAL, "empty layer");
     if (d->kh % 2 == 0 || d->kh > 7) fail(HE_EINVAL, "kernel must be odd, at most 7");
     if (d->stride < 1 || d->stride > 2) fail(HE_EINVAL, "stride must be 1 or 2");
     if (d->c_n != 1 && d->c_n != 2) fail(HE_EINVAL, "c_n must be 1 or 2");
     if (d->depthwise && d->C_in != d->C_out) fail(HE_EINVAL, "depthwise needs C_in == C_out");
+    if (d->polyphase > 1 || (d->polyphase && (d->stride != 2 || d->kh != 3)))
+        fail(HE_EINVAL, "polyphase packing is for 3x3 stride-2 layers (polyphase 0 or 1)");
     std::memset(o, 0, sizeof(*o));
     const u32 half = p->N / 2, P = (d->kh - 1) / 2;
+    u32 Hp, Wp, S, Cp;
+    plane_geometry(d, &Hp, &Wp, &S, &Cp);
     o->P = P;
     if (d->tile_h || d->tile_w) {
-        const u32 S = d->stride, th = d->tile_h, tw = d->tile_w;
-        if (!th || !tw || th > d->H || tw > d->W) fail(HE_EINVAL, "tile must be given in both directions, within the image");
-        if ((th % S && th != d->H) || (tw % S && tw != d->W)) fail(HE_EINVAL, "tile sides must be multiples of the stride");
+        const u32 th = d->tile_h, tw = d->tile_w;
+        if (!th || !tw || th > Hp || tw > Wp) fail(HE_EINVAL, "tile must be given in both directions, within the image");
+        if ((th % S && th != Hp) || (tw % S && tw != Wp)) fail(HE_EINVAL, "tile sides must be multiples of the stride");
         if ((u64)(th + 2 * P) * (tw + 2 * P) > half) fail(HE_EINVAL, "padded tile does not fit N/2 slots");
         o->T_h = th, o->T_w = tw;
     } else {
-        choose_tile(half, d->H, d->W, P, d->stride, &o->T_h, &o->T_w);
+        choose_tile(half, Hp, Wp, P, S, &o->T_h, &o->T_w);
     }
     o->W_b = o->T_w + 2 * P;
     o->block_slots = (o->T_h + 2 * P) * o->W_b;
     o->blocks_per_row = half / o->block_slots;
-    o->n_ty = (d->H + o->T_h - 1) / o->T_h;
-    o->n_tx = (d->W + o->T_w - 1) / o->T_w;
+    o->n_ty = (Hp + o->T_h - 1) / o->T_h;
+    o->n_tx = (Wp + o->T_w - 1) / o->T_w;
     o->units = d->n_images * o->n_ty * o->n_tx;
     u32 per_ct = o->blocks_per_row * (d->c_n == 1 ? 2 : 1);
     o->row_units = (o->units + per_ct - 1) / per_ct;
-    o->in_groups = (d->C_in + d->c_n - 1) / d->c_n;
+    o->in_groups = (Cp + d->c_n - 1) / d->c_n;
     o->out_groups = (d->C_out + d->c_n - 1) / d->c_n;
     o->n_ct_in = o->row_units * o->in_groups;
     o->n_ct_out = o->row_units * o->out_groups;
-    o->Ho = (d->H - 1) / d->stride + 1;
-    o->Wo = (d->W - 1) / d->stride + 1;
+    o->Ho = (Hp - 1) / S + 1;
+    o->Wo = (Wp - 1) / S + 1;
     o->scale = d->c_n == 2 ? (2 * p->k) % p->t : 1;
     std::vector<RotEntry> rl = rotation_list(p, d, *o);
     std::vector<u32> gs;
@@ -772,6 +787,8 @@ std::vector<RotEntry> rotation_list(const he_params* p, const he_conv_desc* d, c
     u32 tap = 0;
     for (i64 dy = -P; dy <= P; dy++)
         for (i64 dx = -P; dx <= P; dx++, tap++) {
+            // polyphase planes are read at offsets -1 and 0 only (tap index stays the 3x3 one)
+            if (d->polyphase && (dy > 0 || dx > 0)) continue;
             u32 g = rotation_galois(p, dy * (i64)lay.W_b + dx);
             for (u32 dg = 0; dg < ndiag; dg++) {
                 u32 gg = dg ? (u32)((u64)g * swap % (2ULL * p->N)) : g;
@@ -822,6 +839,18 @@ extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const h
         compute_layout(p, d, &lay);
         const u32 N = p->N, half = N / 2, P = lay.P;
         const u32 per_ct = lay.blocks_per_row * (d->c_n == 1 ? 2 : 1);
+        u32 Hp, Wp, S, Cplanes;
+        plane_geometry(d, &Hp, &Wp, &S, &Cplanes);
+        const u32 Cp = Cplanes / (d->polyphase ? 4 : 1);
+        // activation of plane channel c at plane position (Y, X): the image itself, or phase
+        // (a, b) = (c / Cp) of channel c % Cp at (2Y + a, 2X + b); zero outside the image
+        auto A = [&](u32 img, u32 c, i64 Y, i64 X) -> int64_t {
+            if (!d->polyphase) return act[(((size_t)img * d->C_in + c) * d->H + Y) * d->W + X];
+            const u32 ph = c / Cp, ch = c % Cp;
+            const i64 y = 2 * Y + (ph >> 1), x = 2 * X + (ph & 1);
+            if (ch >= d->C_in || y >= (i64)d->H || x >= (i64)d->W) return 0;
+            return act[(((size_t)img * d->C_in + ch) * d->H + y) * d->W + x];
+        };
         std::vector<int64_t> slots((size_t)lay.n_ct_in * N, 0);
         for (u32 unit = 0; unit < lay.units; unit++) {
             u32 ru = unit / per_ct, u = unit % per_ct;
@@ -829,10 +858,10 @@ extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const h
             u32 ty = rest / lay.n_tx, tx = rest % lay.n_tx;
             for (u32 yl = 0; yl < lay.T_h + 2 * P; yl++) {
                 i64 Y = (i64)ty * lay.T_h + yl - P;
-                if (Y < 0 || Y >= (i64)d->H) continue;
+                if (Y < 0 || Y >= (i64)Hp) continue;
                 for (u32 xl = 0; xl < lay.W_b; xl++) {
                     i64 X = (i64)tx * lay.T_w + xl - P;
-                    if (X < 0 || X >= (i64)d->W) continue;
+                    if (X < 0 || X >= (i64)Wp) continue;
                     u32 row, pos;
                     slot_of(d, lay, u, yl, xl, &row, &pos);
                     for (u32 j = 0; j < lay.in_groups; j++) {
@@ -840,11 +869,10 @@ extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const h
                         if (d->c_n == 2) {
                             for (u32 r = 0; r < 2; r++) {
                                 u32 c = 2 * j + r;
-                                if (c < d->C_in)
-                                    sv[r * half + pos] = act[(((size_t)img * d->C_in + c) * d->H + Y) * d->W + X];
+                                if (c < Cplanes) sv[r * half + pos] = A(img, c, Y, X);
                             }
                         } else {
-                            sv[row * half + pos] = act[(((size_t)img * d->C_in + j) * d->H + Y) * d->W + X];
+                            sv[row * half + pos] = A(img, j, Y, X);
                         }
                     }
                 }
@@ -865,7 +893,9 @@ extern "C" int he_decrypt_image(const he_params* p, const he_seckey* sk, const h
         if (!p || !sk || !d || !ct || !out) fail(HE_EINVAL, "null argument");
         he_layout lay;
         compute_layout(p, d, &lay);
-        const u32 N = p->N, half = N / 2, P = lay.P, S = d->stride;
+        u32 Hp, Wp, S, Cplanes;
+        plane_geometry(d, &Hp, &Wp, &S, &Cplanes);
+        const u32 N = p->N, half = N / 2, P = lay.P;
         const u32 per_ct = lay.blocks_per_row * (d->c_n == 1 ? 2 : 1);
         const size_t ctw = 2ULL * p->L * N;
         std::vector<int64_t> slots((size_t)lay.n_ct_out * N);
@@ -882,10 +912,10 @@ extern "C" int he_decrypt_image(const he_params* p, const he_seckey* sk, const h
             u32 ty = rest / lay.n_tx, tx = rest % lay.n_tx;
             for (u32 yl = P; yl < P + lay.T_h; yl++) {
                 u32 Y = ty * lay.T_h + yl - P;
-                if (Y >= d->H || Y % S) continue;
+                if (Y >= Hp || Y % S) continue;
                 for (u32 xl = P; xl < P + lay.T_w; xl++) {
                     u32 X = tx * lay.T_w + xl - P;
-                    if (X >= d->W || X % S) continue;
+                    if (X >= Wp || X % S) continue;
                     u32 row, pos;
                     slot_of(d, lay, u, yl, xl, &row, &pos);
                     for (u32 g = 0; g < lay.out_groups; g++) {

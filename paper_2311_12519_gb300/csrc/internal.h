@@ -166,6 +166,8 @@ struct RotEntry {
     u32 tap, d, galois;
 };
 void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* out);
+// plane height, width, stride and channel count the slots of a layer hold (polyphase: the phase planes)
+void plane_geometry(const he_conv_desc* d, u32* H, u32* W, u32* S, u32* C_planes);
 std::vector<RotEntry> rotation_list(const he_params* p, const he_conv_desc* d, const he_layout& lay);
 u32 rotation_galois(const he_params* p, i64 step);
 // log2 of the estimated worst output noise (6 sigma + rounding terms).

@@ -37,7 +37,7 @@ class he_param_info(ctypes.Structure):
 
 class he_conv_desc(ctypes.Structure):
     _fields_ = [(n, u32) for n in ("C_in", "C_out", "H", "W", "kh", "stride", "depthwise", "n_images", "c_n",
-                                   "tile_h", "tile_w")]
+                                   "tile_h", "tile_w", "polyphase")]
 
 
 class he_layout(ctypes.Structure):
@@ -215,8 +215,8 @@ def he_galkeys_destroy(gk):
 
 # ---------------------------------------------------------------------- layout
 def conv_desc(C_in, C_out, H, W, kh=3, stride=1, depthwise=False, n_images=1, c_n=2, tile_h=0,
-              tile_w=0) -> he_conv_desc:
-    return he_conv_desc(C_in, C_out, H, W, kh, stride, int(depthwise), n_images, c_n, tile_h, tile_w)
+              tile_w=0, polyphase=0) -> he_conv_desc:
+    return he_conv_desc(C_in, C_out, H, W, kh, stride, int(depthwise), n_images, c_n, tile_h, tile_w, int(polyphase))
 
 
 def he_layout_for_layer(p, d: he_conv_desc) -> he_layout:

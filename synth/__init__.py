@@ -118,12 +118,16 @@ STACKS = {
 }
 
 
-def stack_layer(stack: str, i: int) -> dict:
-    """Layer i of a stack as a layer description (3x3 or 1x1, Hyena packing c_n = 2)."""
+def stack_layer(stack: str, i: int, polyphase: bool = False) -> dict:
+    """Layer i of a stack as a layer description (3x3 or 1x1, Hyena packing c_n = 2); with
+    `polyphase`, a 3x3 stride-2 layer is marked for polyphase packing."""
     shapes, _, _, images = STACKS[stack]
     s = shapes()[i]
-    return dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
-                n_images=images, c_n=2)
+    d = dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
+             n_images=images, c_n=2)
+    if polyphase and s.stride == 2 and s.k == 3:
+        d["polyphase"] = 1
+    return d
 
 
 def stack_inputs(stack: str, i: int, t: int):

@@ -13,7 +13,8 @@ A deep layer's output ciphertext depends on all input ciphertexts of its row-uni
 here, each rotated 17 times), which takes the oracle minutes per layer even on all cores; the
 stored digests let the GPU tests compare every layer's sample word for word in seconds.
 
-Usage: python tests/golden/make_network_samples.py [--stacks vgg16,mobilenet]
+Usage: python tests/golden/make_network_samples.py [--stacks vgg16,mobilenet] [--polyphase]
+(--polyphase: the 3x3 stride-2 layers only, with polyphase packing, as entries '<stack>-polyphase').
 """
 from __future__ import annotations
 
@@ -41,25 +42,33 @@ def digest(ct: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(ct, dtype="<u8").tobytes()).hexdigest()
 
 
-def sample_layer(P, s, ksk, stack, i):
-    sp = synth.stack_layer(stack, i)
-    lay = conv.Layout(N=P.N, **sp)
+def sample_layer(P, s, ksk, stack, i, polyphase=False):
+    sp = synth.stack_layer(stack, i, polyphase)
     act, wt, enc_seed = synth.stack_inputs(stack, i, P.t)
+    poly = sp.get("polyphase", 0)
+    if poly:
+        # polyphase packing: the oracle's layer on the derived stride-1 layer of the phase planes
+        act_in = conv.polyphase_planes(act, sp["c_n"])
+        wt_in = conv.polyphase_weights(wt, sp["C_in"], sp["c_n"], sp["depthwise"])
+        lay = conv.Layout(N=P.N, **conv.polyphase_spec(sp))
+    else:
+        act_in, wt_in = act, wt
+        lay = conv.Layout(N=P.N, **sp)
     c = synth.sample_index(100 * STACK_LABEL[stack] + i, lay.n_ct_out)
     ru, g = divmod(c, lay.out_groups)
-    need = [ru * lay.in_groups + (g if sp["depthwise"] else j) for j in
-            ([0] if sp["depthwise"] else range(lay.in_groups))]
-    cts = conv.encrypt_image(P, lay, s, act, enc_seed, only=need)
+    dw = lay.depthwise
+    need = [ru * lay.in_groups + (g if dw else j) for j in ([0] if dw else range(lay.in_groups))]
+    cts = conv.encrypt_image(P, lay, s, act_in, enc_seed, only=need)
     for gal in conv.galois_elements(P, lay):
         if gal not in ksk:
             ksk[gal] = bfv.galois_key(P, s, gal, synth.SEED_KEYS)
-    out = conv.he_conv(P, lay, wt, cts, ksk, out_cts=[c])[c]
+    out = conv.he_conv(P, lay, wt_in, cts, ksk, out_cts=[c])[c]
     # the sampled ciphertext must decrypt to the plain convolution at its valid positions
     slots = bfv.decode(P, bfv.decrypt(P, s, out))
     inv = pow(conv.output_scale(P, lay), -1, P.t)
     pos = conv.ct_positions(lay, c)
     imgs = sorted({q[0] for q in pos})
-    plain = conv.conv_plain(act[imgs], wt, sp["stride"], lay.P, sp["depthwise"], P.t)
+    plain = conv.conv_plain(act[imgs], wt, sp["stride"], 1 if poly else lay.P, sp["depthwise"], P.t)
     ok = all(int(slots[x]) * inv % P.t == plain[imgs.index(im), ch, y, xx] for im, ch, y, xx, x in pos)
     assert pos and ok, f"{stack} layer {i}: oracle sample fails decryption"
     return {"layer": i, "n_ct_out": lay.n_ct_out, "ct": c, "sha256": digest(out),
@@ -69,6 +78,8 @@ def sample_layer(P, s, ksk, stack, i):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--stacks", default="vgg16,mobilenet")
+    ap.add_argument("--polyphase", action="store_true",
+                    help="sample the 3x3 stride-2 layers with polyphase packing (entries '<stack>-polyphase')")
     args = ap.parse_args()
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for stack in args.stacks.split(","):
@@ -77,12 +88,15 @@ def main():
         s = bfv.keygen(P, synth.SEED_KEYS)
         ksk = {}
         rows = []
-        for i in range(len(shapes())):
+        for i, sh in enumerate(shapes()):
+            if args.polyphase and not (sh.stride == 2 and sh.k == 3):
+                continue
             t0 = time.time()
-            rows.append(sample_layer(P, s, ksk, stack, i))
+            rows.append(sample_layer(P, s, ksk, stack, i, args.polyphase))
             print(f"{stack} layer {i}: ct {rows[-1]['ct']} in {time.time() - t0:.0f} s", flush=True)
-        data[stack] = {"N": N, "L": L, "w": 50, "images": images, "seeds": "keys 1, encryption 2 + layer, "
-                       "activations label = layer, weights label = layer", "samples": rows}
+        key = stack + ("-polyphase" if args.polyphase else "")
+        data[key] = {"N": N, "L": L, "w": 50, "images": images, "seeds": "keys 1, encryption 2 + layer, "
+                     "activations label = layer, weights label = layer", "samples": rows}
         with open(OUT, "w") as f:
             json.dump(data, f, indent=1)
     print("wrote", OUT)

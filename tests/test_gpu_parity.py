@@ -478,3 +478,41 @@ def test_other_limb_widths_and_digit_counts(limb_bits, L, w):
     spec = dict(C_in=4, C_out=6, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=2)
     S.layer(spec)
     S.layer(dict(spec, c_n=1))
+
+
+# ---------------------------------------------------------------- polyphase stride 2
+POLY = [
+    dict(C_in=3, C_out=5, H=7, W=9, kh=3, stride=2, depthwise=False, n_images=2, c_n=2, polyphase=1),
+    dict(C_in=4, C_out=6, H=10, W=10, kh=3, stride=2, depthwise=False, n_images=1, c_n=1, polyphase=1),
+    dict(C_in=4, C_out=4, H=8, W=6, kh=3, stride=2, depthwise=True, n_images=3, c_n=2, polyphase=1),
+    dict(C_in=3, C_out=3, H=9, W=7, kh=3, stride=2, depthwise=True, n_images=2, c_n=1, polyphase=1),
+    dict(C_in=6, C_out=200, H=6, W=6, kh=3, stride=2, depthwise=False, n_images=1, c_n=2, polyphase=1),
+]
+
+
+@pytest.mark.parametrize("impl", [0, 1, 4, 5])
+@pytest.mark.parametrize("spec", POLY)
+def test_polyphase_layer_matches_oracle(small, spec, impl):
+    """Polyphase packing of 3x3 stride-2 layers: every output ciphertext equals the oracle's layer
+    on the derived stride-1 layer of the phase planes, word for word (each MAC form the layer
+    admits), and decrypts to the stride-2 convolution."""
+    if impl in (4, 5) and spec["depthwise"]:
+        pytest.skip("depthwise layers run on CUDA cores")
+    S, N, L = small, small.N, small.L
+    d = H.conv_desc(**spec)
+    act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), S.P.t, label=spec["H"])
+    wt = synth.weights((spec["C_out"], 1 if spec["depthwise"] else spec["C_in"], 3, 3), label=spec["W"])
+    gk = H.he_galois_keys(S.p, S.sk, H.he_layer_galois(S.p, d), synth.SEED_KEYS)
+    cts = H.he_encrypt_image(S.p, S.sk, d, act, synth.SEED_ENC, S.info)
+    out = gpu_layer(S.p, gk, d, wt, cts, L, N, mac_impl=impl)
+    ol = conv.Layout(N=N, **conv.polyphase_spec(spec))
+    planes = conv.polyphase_planes(act, spec["c_n"])
+    ref_in = conv.encrypt_image(S.P, ol, S.s, planes, synth.SEED_ENC)
+    assert (ref_in == cts).all()
+    w2 = conv.polyphase_weights(wt, spec["C_in"], spec["c_n"], spec["depthwise"])
+    ref = conv.he_conv(S.P, ol, w2, ref_in, S.oracle_keys(conv.galois_elements(S.P, ol)))
+    bad = [c for c in range(len(out)) if not (out[c] == ref[c]).all()]
+    assert not bad, f"ciphertexts {bad[:8]} differ from the oracle"
+    dec = H.he_decrypt_image(S.p, S.sk, d, out)
+    assert (dec == conv.conv_plain(act, wt, 2, 1, spec["depthwise"], S.P.t)).all()
+    H.he_galkeys_destroy(gk)

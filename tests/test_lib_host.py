@@ -223,3 +223,40 @@ def test_cluster_and_form_choices_are_checked_without_a_device():
     assert H.he_conv_check(p, wide, ww, mac_impl=6) == H.HE_EINVAL
     assert H.he_conv_check(p, wide, ww, mac_impl=7) == H.HE_EINVAL
     H.he_params_destroy(p)
+
+
+POLY = [
+    dict(C_in=3, C_out=5, H=7, W=9, kh=3, stride=2, depthwise=False, n_images=2, c_n=2, polyphase=1),
+    dict(C_in=4, C_out=4, H=8, W=6, kh=3, stride=2, depthwise=True, n_images=3, c_n=2, polyphase=1),
+    dict(C_in=3, C_out=3, H=9, W=7, kh=3, stride=2, depthwise=True, n_images=2, c_n=1, polyphase=1),
+    dict(C_in=2, C_out=4, H=12, W=60, kh=3, stride=2, depthwise=False, n_images=1, c_n=2, polyphase=1,
+         tile_h=3, tile_w=30),
+]
+
+
+@pytest.mark.parametrize("spec", POLY)
+def test_polyphase_layout_and_encryption_match_the_oracle_derived_layer(spec):
+    """Polyphase packing: the library's layout is the oracle's derived stride-1 layer on the phase
+    planes, and its client encryption equals the oracle's encryption of the planes; its rotations
+    are the derived layer's taps at offsets -1 and 0 only (a subset of the oracle's)."""
+    N, L, w = 1024, 2, 25
+    p = H.he_params_create(N, L, decomp_bits=w)
+    info = H.he_params_info(p)
+    P = prm.make_params(N=N, L=L, w=w)
+    d = H.conv_desc(**spec)
+    lay = H.he_layout_for_layer(p, d)
+    ol = conv.Layout(N=N, **conv.polyphase_spec(spec))
+    assert (lay.T_h, lay.T_w, lay.blocks_per_row, lay.n_ct_in, lay.n_ct_out, lay.Ho, lay.Wo) == \
+        (ol.T_h, ol.T_w, ol.blocks_per_row, ol.n_ct_in, ol.n_ct_out, ol.Ho, ol.Wo)
+    gal = set(int(g) for g in H.he_layer_galois(p, d))
+    assert gal < set(conv.galois_elements(P, ol))
+    packed_dense = spec["c_n"] == 2 and not spec["depthwise"]
+    assert len(gal) == (7 if packed_dense else 3)
+    act = synth.activations((spec["n_images"], spec["C_in"], spec["H"], spec["W"]), P.t, label=spec["W"])
+    sk = H.he_keygen(p, 1)
+    s = bfv.keygen(P, 1)
+    ct = H.he_encrypt_image(p, sk, d, act, 2, info)
+    assert (ct == conv.encrypt_image(P, ol, s, conv.polyphase_planes(act, spec["c_n"]), 2)).all()
+    with pytest.raises(H.HyenaError):
+        H.he_layout_for_layer(p, H.conv_desc(**dict(spec, stride=1)))
+    H.he_params_destroy(p)

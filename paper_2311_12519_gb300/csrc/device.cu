@@ -295,6 +295,7 @@ struct LayerDev {
     __half* A16;               // images [row_units][2][L][N/128][ktiles][5 chunks][128 slots x 32 terms]
     const RotDev* rots_all;    // every rotation of the layer, identity included (key = ~0u)
     u32 img, in_pad, n_rot_all, id_rot;  // in_pad = in_groups rounded up to 8; id_rot = the identity's index
+    u32 ks_rg;                 // rotation groups of the image key switch (ksi_groups)
     u32 fused;                 // key switch inside the MAC (k_ksmac): no image buffer, no key-switch launch
 };
 
@@ -1077,18 +1078,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
 // Image of (row unit, polynomial, limb, slot tile nt, K tile kt): 5 chunks x 8 KB, chunk c at
 // byte c * 8192, element (slot row m, term kl) at (m >> 3) * 512 + (kl >> 3) * 128 + (m & 7) * 16
 // + (kl & 7) * 2, the layout smem_desc describes (LBO 128 B, SBO 512 B).
-constexpr int KSI_THREADS = 128;          // one 128-slot tile per block, thread = destination slot
 constexpr u32 KSI_JB = 8;                 // input ciphertexts per block (one group of eight)
 constexpr u32 IMG_HALVES = TC_CHUNKS * TC_MTILE * TC_KTILE;  // 20480 halves = 40 KB per image
 
-// Step 2, operand-image form.  Local block = (row unit, block of 32 input ciphertexts, rotation,
-// limb, slot tile), the tile varying fastest, so that the blocks resident together share the
-// digit transforms of the same input ciphertexts in L2.  As in k_keyswitch, a thread owns a
-// SOURCE slot y of the tile (coalesced loads) and produces the destination x = src^-1(y).  The
-// chunks of eight input ciphertexts go to a shared-memory copy of the tile's image rows (row
-// x & 127), which the block then writes out in 16-byte pieces, row by row.  The identity
-// rotation converts NTT(c0), NTT(c1) as they are.
-constexpr int KSI_JH = 4;  // input ciphertexts computed per pass (two passes per eight)
+// Step 2, operand-image form.  Local block = (row unit and group of eight input ciphertexts,
+// rotation group, source slot tile nt, limb k), the (row unit, group) pair varying fastest so
+// that consecutive blocks read the same key tiles.  The block keeps the digit transforms of its
+// eight ciphertexts (tile nt, limb k) in shared memory and runs every rotation of its group over
+// them: a digit transform is read from memory once, not once per rotation.  Thread (slot, half)
+// owns the SOURCE slot y = nt * 128 + slot (coalesced loads) and four of the eight ciphertexts;
+// for rotation r it produces the destination x = src_r^-1(y), which lies in one aligned
+// destination tile xt_r for the whole block (sigma maps aligned tiles onto aligned tiles).  The
+// key words of rotation r + 1 are copied into shared memory (cp.async) while rotation r is
+// computed.  The chunks of the eight ciphertexts gather in a shared copy of the destination
+// tile's image rows (row x & 127), which leave in 16-byte pieces.  Small layers split their
+// rotations into groups so that the grid still fills the GPU.
+constexpr int KSI_THREADS = 256;          // 128 source slots x 2 halves of the eight ciphertexts
+constexpr int KSI_JH = 4;                 // input ciphertexts per thread
+constexpr u32 KSI_TARGET_BLOCKS = 1024;   // rotation groups raise a layer's grid up to about this
+
+// rows [2][5][128] uint4, digit transforms [8][LL][128] u64, key words [2 buffers][2][LL][128] u64
+__host__ __device__ constexpr size_t ksi_smem_bytes(u32 LL) {
+    return (size_t)2 * TC_CHUNKS * TC_MTILE * 16 + ((size_t)KSI_JB * LL + 4 * LL) * TC_MTILE * 8;
+}
+
+// rotation groups of the image key switch: as few as give about KSI_TARGET_BLOCKS blocks
+__host__ __device__ inline u32 ksi_groups(u32 row_units, u32 in_pad, u32 n_rot_all, u32 L, u32 N) {
+    const u64 base = (u64)row_units * ((in_pad + KSI_JB - 1) / KSI_JB) * L * (N / TC_MTILE);
+    const u64 g = (KSI_TARGET_BLOCKS + base - 1) / base;
+    return (u32)(g < 1 ? 1 : (g > n_rot_all ? n_rot_all : g));
+}
 
 __device__ __forceinline__ uint2 chunk_pack4(const u64 (&v)[KSI_JH], int c) {
     u32 w[2];
@@ -1112,152 +1131,186 @@ __device__ __forceinline__ uint2 chunk_pack4(const u64 (&v)[KSI_JH], int c) {
     return make_uint2(w[0], w[1]);
 }
 
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int LL, int MAXB>
-__global__ void __launch_bounds__(KSI_THREADS, 6) k_keyswitch_img(const __grid_constant__ Batch<MAXB> B, KP kp) {
-    // image rows of eight terms: [polynomial][chunk][slot row][8 halves]
-    __shared__ __align__(16) uint4 rows[2][TC_CHUNKS][TC_MTILE];
+__global__ void __launch_bounds__(KSI_THREADS, LL <= 4 ? 3 : (LL <= 8 ? 2 : 1)) k_keyswitch_img(const __grid_constant__ Batch<MAXB> B, KP kp) {
+    extern __shared__ __align__(16) unsigned char ksm[];
+    uint4 (*rows)[TC_CHUNKS][TC_MTILE] = reinterpret_cast<uint4 (*)[TC_CHUNKS][TC_MTILE]>(ksm);
+    u64* const Dsm = reinterpret_cast<u64*>(ksm + 2 * TC_CHUNKS * TC_MTILE * 16);
+    u64* const Ksm = Dsm + KSI_JB * LL * TC_MTILE;
     const u32 li = find_layer(B, ST_KS, blockIdx.x);
     const LayerDev& Ly = B.L[li];
     const u32 N = kp.N, L = kp.L, logN = kp.logN, NT = N / TC_MTILE;
-    const u32 JC = (Ly.in_pad + KSI_JB - 1) / KSI_JB;
+    const u32 JC = (Ly.in_pad + KSI_JB - 1) / KSI_JB, QJ = Ly.row_units * JC, RG = Ly.ks_rg;
     u32 local = blockIdx.x - B.start[ST_KS][li];
-    const u32 nt = local % NT;
-    local /= NT;
-    const u32 k = local % L;
-    local /= L;
-    const u32 r = local % Ly.n_rot_all;
-    local /= Ly.n_rot_all;
-    const u32 jc = local % JC, ru = local / JC;
-    const u32 tid = threadIdx.x;
-    const u32 src = nt * TC_MTILE + tid;
-    const RotDev rd = Ly.rots_all[r];
+    const u32 q = local % QJ;
+    local /= QJ;
+    const u32 g = local % RG;
+    local /= RG;
+    const u32 nt = local % NT, k = local / NT;
+    const u32 ru = q / JC, jc = q % JC;
+    const u32 tid = threadIdx.x, slot = tid & (TC_MTILE - 1), h = tid / TC_MTILE;
+    const u32 src = nt * TC_MTILE + slot;
     const LimbC m = kp.limb[k];
-    const bool ident = r == Ly.id_rot;
-    const u32 e = 2 * (__brev(src) >> (32 - logN)) + 1;
-    const u32 e2 = (u32)(((u64)e * rd.galois_inv) & (2ull * N - 1));
-    const u32 x = __brev((e2 - 1) >> 1) >> (32 - logN);
-    // the destinations of a source tile fill one aligned destination tile xt (sigma maps aligned
-    // tiles onto aligned tiles), so xt is the same for every thread of the block
-    const u32 xl = x & (TC_MTILE - 1), xt = x / TC_MTILE;
-    const size_t ctw = 2ull * L * N;
+    const u32 rpg = (Ly.n_rot_all + RG - 1) / RG, r_begin = g * rpg, r_end = min(Ly.n_rot_all, r_begin + rpg);
+    const u32 j0 = jc * KSI_JB, ja = h * KSI_JH;  // the block's first ciphertext; this thread's within the eight
+    const u32 nj = j0 >= Ly.in_groups ? 0u : min(KSI_JB, Ly.in_groups - j0);  // real terms; the rest are padding
+    const size_t ctw = 2ull * L * N, d_step = (size_t)LL * L * N, dd_step = (size_t)L * N;
+    const size_t r_step = (size_t)Ly.r_slots * ctw;
     const u32 ktiles = Ly.Kpad / TC_KTILE;
-    __half* const img0 = Ly.A16 + ((((size_t)ru * 2 + 0) * L + k) * NT + xt) * ktiles * IMG_HALVES;
     const size_t p_stride = (size_t)L * NT * ktiles * IMG_HALVES;
-    const u32 row_off = (tid >> 3) * 256 + (tid & 7) * 8;  // halves: image row tid within a chunk
-    // keys of the destination x split at bit 25 (see k_keyswitch), in registers for the block
-    u32 k0l[LL], k0h[LL], k1l[LL], k1h[LL];
-    if (!ident) {
-        const u64* kb = Ly.ksk + (size_t)rd.key * LL * 2 * L * N;
+    const u32 e_src = 2 * (__brev(src) >> (32 - logN)) + 1;
+    const u32 row_off = (slot >> 3) * 256 + (slot & 7) * 8;  // halves: image row `slot` within a chunk
+    // this thread's four ciphertexts: c0 in registers, the digit transforms in shared memory (read
+    // back by this thread only, so no barrier is needed before their use)
+    const size_t c_first = (size_t)ru * Ly.in_groups + j0 + ja;
+    const u64* const Rp = Ly.R + (c_first * Ly.r_slots + Ly.r_id) * ctw + (size_t)k * N + src;
+    u64 c0[KSI_JH];
 #pragma unroll
-        for (int dd = 0; dd < LL; dd++) {
-            const u64 a = __ldg(kb + (((size_t)dd * 2 + 0) * L + k) * N + x);
-            const u64 b = __ldg(kb + (((size_t)dd * 2 + 1) * L + k) * N + x);
-            k0l[dd] = (u32)(a & 0x1FFFFFFu), k0h[dd] = (u32)(a >> 25);
-            k1l[dd] = (u32)(b & 0x1FFFFFFu), k1h[dd] = (u32)(b >> 25);
-        }
+    for (int jj = 0; jj < KSI_JH; jj++) {
+        const bool real = ja + jj < nj;
+        c0[jj] = real ? __ldg(Rp + jj * r_step) : 0;
+        const u64* Dc = Ly.D + (c_first + jj) * d_step + (size_t)k * N + src;
+#pragma unroll
+        for (int dd = 0; dd < LL; dd++) Dsm[((ja + jj) * LL + dd) * TC_MTILE + slot] = real ? __ldg(Dc + dd * dd_step) : 0;
     }
-    auto store_rows = [&](u32 kk) {
-        // the block's image rows of terms kk .. kk+7 of both polynomials, row tid, 16 bytes a chunk
-        const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
-        __half* d0 = img0 + (size_t)kt * IMG_HALVES + (kl >> 3) * 64 + row_off;
-#pragma unroll
-        for (int c = 0; c < TC_CHUNKS; c++) {
-            __stcs(reinterpret_cast<uint4*>(d0 + c * (TC_MTILE * TC_KTILE)), rows[0][c][tid]);
-            __stcs(reinterpret_cast<uint4*>(d0 + p_stride + c * (TC_MTILE * TC_KTILE)), rows[1][c][tid]);
-        }
+    auto dest = [&](u32 galois_inv) {
+        const u32 e2 = (u32)(((u64)e_src * galois_inv) & (2ull * N - 1));
+        return __brev((e2 - 1) >> 1) >> (32 - logN);
     };
-    // the block's input ciphertexts c = ru in_groups + j, j in [j0, j0 + 8), walked with running
-    // pointers; the loop is specialised by rotation kind and limb reduction outside the loop
-    const u32 j0 = jc * KSI_JB;
-    const u32 nj = j0 >= Ly.in_groups ? 0u : min(8u, Ly.in_groups - j0);  // real terms; the rest are padding
-    const size_t d_step = (size_t)LL * L * N, r_step = (size_t)Ly.r_slots * ctw, dd_step = (size_t)L * N;
-    const u64* Dp = Ly.D + (size_t)(ru * Ly.in_groups + j0) * d_step + (size_t)k * N + src;
-    const u64* Rp = Ly.R + ((size_t)(ru * Ly.in_groups + j0) * Ly.r_slots + Ly.r_id) * ctw + (size_t)k * N + src;
-    auto put = [&](u32 h, const u64 (&v0)[KSI_JH], const u64 (&v1)[KSI_JH]) {
+    // key words of rotation r at this thread's destination, polynomial h, every digit -> buffer b
+    auto fetch_keys = [&](u32 r, u32 b) {
+        const RotDev rd = Ly.rots_all[r];
+        if (r == Ly.id_rot) return;
+        const u64* kb = Ly.ksk + (size_t)rd.key * LL * 2 * L * N + ((size_t)h * L + k) * N + dest(rd.galois_inv);
+#pragma unroll
+        for (int dd = 0; dd < LL; dd++)
+            cp_async8(&Ksm[((b * 2 + h) * LL + dd) * TC_MTILE + slot], kb + (size_t)dd * 2 * L * N);
+        cp_async_commit();
+    };
+    const int kind = m.sm1 == 49 ? (m.delta ? 1 : 2) : 3;
+    fetch_keys(r_begin, 0);
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 1
+    for (u32 r = r_begin; r < r_end; r++) {
+        const u32 b = (r - r_begin) & 1;
+        if (r + 1 < r_end) fetch_keys(r + 1, b ^ 1);
+        const RotDev rd = Ly.rots_all[r];
+        const u32 x = dest(rd.galois_inv), xl = x & (TC_MTILE - 1), xt = x / TC_MTILE;
+        u64 v0[KSI_JH], v1[KSI_JH];
+        if (r == Ly.id_rot) {
+            // the identity converts NTT(c0), NTT(c1) as they are
+#pragma unroll
+            for (int jj = 0; jj < KSI_JH; jj++) {
+                v0[jj] = c0[jj];
+                v1[jj] = ja + jj < nj ? __ldg(Rp + jj * r_step + dd_step) : 0;
+            }
+        } else {
+            // keys of the destination x split at bit 25 (see k_keyswitch), for the four ciphertexts
+            u32 k0l[LL], k0h[LL], k1l[LL], k1h[LL];
+            const u64* K0 = Ksm + (size_t)(b * 2 + 0) * LL * TC_MTILE + slot;
+            const u64* K1 = Ksm + (size_t)(b * 2 + 1) * LL * TC_MTILE + slot;
+#pragma unroll
+            for (int dd = 0; dd < LL; dd++) {
+                const u64 a = K0[dd * TC_MTILE], bb = K1[dd * TC_MTILE];
+                k0l[dd] = (u32)(a & 0x1FFFFFFu), k0h[dd] = (u32)(a >> 25);
+                k1l[dd] = (u32)(bb & 0x1FFFFFFu), k1h[dd] = (u32)(bb >> 25);
+            }
+            if (kind <= 2) {
+                // 50-bit limbs: Karatsuba middle term, one reduction per sum (see k_keyswitch)
+                u32 k0s[LL], k1s[LL];
+#pragma unroll
+                for (int dd = 0; dd < LL; dd++) k0s[dd] = k0l[dd] + k0h[dd], k1s[dd] = k1l[dd] + k1h[dd];
+#pragma unroll
+                for (int jj = 0; jj < KSI_JH; jj++) {
+                    v0[jj] = v1[jj] = 0;
+                    if (ja + jj >= nj) continue;
+                    const u64* Dc = Dsm + (size_t)(ja + jj) * LL * TC_MTILE + slot;
+                    u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
+#pragma unroll
+                    for (int dd = 0; dd < LL; dd++) {
+                        const u64 dv = Dc[dd * TC_MTILE];
+                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
+                        mad_wide_u(lo0, dl, k0l[dd]);
+                        mad_wide_u(hi0, dh, k0h[dd]);
+                        mad_wide_u(mid0, ds, k0s[dd]);
+                        mad_wide_u(lo1, dl, k1l[dd]);
+                        mad_wide_u(hi1, dh, k1h[dd]);
+                        mad_wide_u(mid1, ds, k1s[dd]);
+                    }
+                    mid0 -= lo0 + hi0;
+                    mid1 -= lo1 + hi1;
+                    lo0 += c0[jj];  // + sigma(c0)
+                    if (kind == 1) {
+                        v0[jj] = fold_reduce50(lo0, mid0, hi0, m);
+                        v1[jj] = fold_reduce50(lo1, mid1, hi1, m);
+                    } else {
+                        v0[jj] = bred_split50(lo0, mid0, hi0, m);
+                        v1[jj] = bred_split50(lo1, mid1, hi1, m);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < KSI_JH; jj++) {
+                    v0[jj] = v1[jj] = 0;
+                    if (ja + jj >= nj) continue;
+                    const u64* Dc = Dsm + (size_t)(ja + jj) * LL * TC_MTILE + slot;
+                    u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
+#pragma unroll
+                    for (int dd = 0; dd < LL; dd++) {
+                        const u64 dv = Dc[dd * TC_MTILE];
+                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                        mad_wide_u(lo0, dl, k0l[dd]);
+                        mad_wide_u(mid0, dl, k0h[dd]);
+                        mad_wide_u(mid0, dh, k0l[dd]);
+                        mad_wide_u(hi0, dh, k0h[dd]);
+                        mad_wide_u(lo1, dl, k1l[dd]);
+                        mad_wide_u(mid1, dl, k1h[dd]);
+                        mad_wide_u(mid1, dh, k1l[dd]);
+                        mad_wide_u(hi1, dh, k1h[dd]);
+                    }
+                    lo0 += c0[jj];
+                    v0[jj] = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
+                    v1[jj] = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
+                }
+            }
+        }
 #pragma unroll
         for (int c = 0; c < TC_CHUNKS; c++) {
             reinterpret_cast<uint2*>(&rows[0][c][xl])[h] = chunk_pack4(v0, c);
             reinterpret_cast<uint2*>(&rows[1][c][xl])[h] = chunk_pack4(v1, c);
         }
-    };
-    const int kind = ident ? 0 : (m.sm1 == 49 ? (m.delta ? 1 : 2) : 3);
-#pragma unroll 1
-    for (u32 h = 0; h < 8 / KSI_JH; h++) {
-        u64 v0[KSI_JH], v1[KSI_JH];
-        if (kind == 0) {
+        __syncthreads();
+        {
+            // thread (slot, p = h) writes image row `slot` of polynomial h: terms r in_pad + j0 .. + 7
+            const u32 kk = r * Ly.in_pad + j0, kt = kk / TC_KTILE, kl = kk % TC_KTILE;
+            __half* d0 = Ly.A16 + ((((size_t)ru * 2 + h) * L + k) * NT + xt) * ktiles * IMG_HALVES +
+                         (size_t)kt * IMG_HALVES + (kl >> 3) * 64 + row_off;
 #pragma unroll
-            for (int jj = 0; jj < KSI_JH; jj++) {
-                const bool real = h * KSI_JH + jj < nj;
-                v0[jj] = real ? __ldg(Rp + jj * r_step) : 0;
-                v1[jj] = real ? __ldg(Rp + jj * r_step + dd_step) : 0;
-            }
-        } else if (kind <= 2) {
-            // 50-bit limbs: Karatsuba middle term, one reduction per sum (see k_keyswitch)
-#pragma unroll
-            for (int jj = 0; jj < KSI_JH; jj++) {
-                v0[jj] = v1[jj] = 0;
-                if (h * KSI_JH + jj >= nj) continue;
-                const u64* Dc = Dp + jj * d_step;
-                u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
-#pragma unroll
-                for (int dd = 0; dd < LL; dd++) {
-                    const u64 dv = __ldg(Dc + dd * dd_step);
-                    const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
-                    mad_wide_u(lo0, dl, k0l[dd]);
-                    mad_wide_u(hi0, dh, k0h[dd]);
-                    mad_wide_u(mid0, ds, k0l[dd] + k0h[dd]);
-                    mad_wide_u(lo1, dl, k1l[dd]);
-                    mad_wide_u(hi1, dh, k1h[dd]);
-                    mad_wide_u(mid1, ds, k1l[dd] + k1h[dd]);
-                }
-                mid0 -= lo0 + hi0;
-                mid1 -= lo1 + hi1;
-                lo0 += __ldg(Rp + jj * r_step);  // + sigma(c0)
-                if (kind == 1) {
-                    v0[jj] = fold_reduce50(lo0, mid0, hi0, m);
-                    v1[jj] = fold_reduce50(lo1, mid1, hi1, m);
-                } else {
-                    v0[jj] = bred_split50(lo0, mid0, hi0, m);
-                    v1[jj] = bred_split50(lo1, mid1, hi1, m);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int jj = 0; jj < KSI_JH; jj++) {
-                v0[jj] = v1[jj] = 0;
-                if (h * KSI_JH + jj >= nj) continue;
-                const u64* Dc = Dp + jj * d_step;
-                u64 lo0 = 0, mid0 = 0, hi0 = 0, lo1 = 0, mid1 = 0, hi1 = 0;
-#pragma unroll
-                for (int dd = 0; dd < LL; dd++) {
-                    const u64 dv = __ldg(Dc + dd * dd_step);
-                    const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
-                    mad_wide_u(lo0, dl, k0l[dd]);
-                    mad_wide_u(mid0, dl, k0h[dd]);
-                    mad_wide_u(mid0, dh, k0l[dd]);
-                    mad_wide_u(hi0, dh, k0h[dd]);
-                    mad_wide_u(lo1, dl, k1l[dd]);
-                    mad_wide_u(mid1, dl, k1h[dd]);
-                    mad_wide_u(mid1, dh, k1l[dd]);
-                    mad_wide_u(hi1, dh, k1h[dd]);
-                }
-                lo0 += __ldg(Rp + jj * r_step);
-                v0[jj] = bred128(((u128)hi0 << 50) + ((u128)mid0 << 25) + lo0, m);
-                v1[jj] = bred128(((u128)hi1 << 50) + ((u128)mid1 << 25) + lo1, m);
-            }
+            for (int c = 0; c < TC_CHUNKS; c++)
+                __stcs(reinterpret_cast<uint4*>(d0 + c * (TC_MTILE * TC_KTILE)), rows[h][c][slot]);
         }
-        put(h, v0, v1);
-        Dp += KSI_JH * d_step;
-        Rp += KSI_JH * r_step;
+        cp_async_wait_all();  // the next rotation's keys, made visible to the other half by the barrier
+        __syncthreads();
     }
-    __syncthreads();
-    store_rows(r * Ly.in_pad + j0);
-    __syncthreads();
     // the terms past n_rot in_pad that fill the last K tile carry zero scalars; their operands must
-    // still be finite numbers (a NaN times 0 is NaN), so the last block of the last rotation zeroes them
-    if (r + 1 == Ly.n_rot_all && jc + 1 == JC) {
-        for (int c = 0; c < TC_CHUNKS; c++) rows[0][c][tid] = rows[1][c][tid] = make_uint4(0, 0, 0, 0);
-        for (u32 kk = Ly.n_rot_all * Ly.in_pad; kk < Ly.Kpad; kk += 8) store_rows(kk);
+    // still be finite numbers (a NaN times 0 is NaN), so the blocks of the last ciphertext group and
+    // rotation group zero them, each for the destination tile numbered as its source tile
+    if (jc + 1 == JC && g + 1 == RG) {
+        __half* d0 = Ly.A16 + ((((size_t)ru * 2 + h) * L + k) * NT + nt) * ktiles * IMG_HALVES + row_off;
+        for (u32 kk = Ly.n_rot_all * Ly.in_pad; kk < Ly.Kpad; kk += 8) {
+            const u32 kt = kk / TC_KTILE, kl = kk % TC_KTILE;
+#pragma unroll
+            for (int c = 0; c < TC_CHUNKS; c++)
+                __stcs(reinterpret_cast<uint4*>(d0 + (size_t)kt * IMG_HALVES + (kl >> 3) * 64 + c * (TC_MTILE * TC_KTILE)),
+                       make_uint4(0, 0, 0, 0));
+        }
     }
 }
 
@@ -1982,7 +2035,7 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
     switch (stage) {
         case ST_NTT: return d.n_ct_in * (L + (p->l == 1 ? 0 : L) + L * p->l * L);
         case ST_KS:
-            if (d.img) return d.row_units * ((d.in_pad + KSI_JB - 1) / KSI_JB) * d.n_rot_all * L * (N / TC_MTILE);
+            if (d.img) return d.row_units * ((d.in_pad + KSI_JB - 1) / KSI_JB) * d.ks_rg * L * (N / TC_MTILE);
             return d.n_ks * L * (N / KS_THREADS);
         case ST_MAC:
             if (s.mv.eager) return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + 3) / 4);
@@ -1996,7 +2049,10 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
 
 template <int LL, int MAXB>
 void ks_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s, bool img) {
-    if (img) k_keyswitch_img<LL, MAXB><<<blocks, KSI_THREADS, 0, s>>>(B, kp);
+    if (img) {
+        allow_smem(k_keyswitch_img<LL, MAXB>, ksi_smem_bytes(LL));
+        k_keyswitch_img<LL, MAXB><<<blocks, KSI_THREADS, ksi_smem_bytes(LL), s>>>(B, kp);
+    }
     else k_keyswitch<LL, MAXB><<<blocks, KS_THREADS, 0, s>>>(B, kp);
 }
 
@@ -2332,6 +2388,7 @@ struct he_plan {
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
         L.tmem_cols = tmem_cols, L.r_slots = r_slots, L.r_id = r_id;
         L.img = img, L.in_pad = in_pad, L.n_rot_all = n_rot, L.id_rot = rot_id, L.rots_all = d_rots_all;
+        L.ks_rg = img ? ksi_groups(lay.row_units, in_pad, n_rot, p->L, p->N) : 1;
         L.A16 = img ? (__half*)(ws + off_A) : nullptr;
         if (use_tc && !img) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;

@@ -1163,7 +1163,6 @@ __global__ void __launch_bounds__(KSI_THREADS, LL <= 4 ? 3 : (LL <= 8 ? 2 : 1)) 
     const size_t ctw = 2ull * L * N, d_step = (size_t)LL * L * N, dd_step = (size_t)L * N;
     const size_t r_step = (size_t)Ly.r_slots * ctw;
     const u32 ktiles = Ly.Kpad / TC_KTILE;
-    const size_t p_stride = (size_t)L * NT * ktiles * IMG_HALVES;
     const u32 e_src = 2 * (__brev(src) >> (32 - logN)) + 1;
     const u32 row_off = (slot >> 3) * 256 + (slot & 7) * 8;  // halves: image row `slot` within a chunk
     // this thread's four ciphertexts: c0 in registers, the digit transforms in shared memory (read
@@ -1553,6 +1552,333 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
     }
     // no CTA leaves while another CTA of its cluster may still copy into its shared memory
     if (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ operand images, CTA pairs
+// Step 3, operand-image form on CTA pairs (tcgen05 cta_group::2), for layers of many output rows.
+// The roles of the operands swap: the scalar rows are the MMA's M dimension (128 rows in each
+// CTA, 256 per pair) and the NTT slots its N dimension (64 per pair; each CTA holds 32 of them),
+// so per K tile a CTA copies an 8 KB scalar tile and 10 KB of image (five chunks of 32 slots)
+// for 128 x 64 x 32 products per chunk.  Rows of a CTA's tile are ordered diagonal-major: row
+// l < 64 is (group g0 + l, diagonal 0), row 64 + l is (group g0 + l, diagonal 1) (unpacked: row l
+// is group g0 + l).  An item is (row unit, polynomial, limb, 64-slot tile, 256-row pair tile).
+// Roles: warp 0 copies (both CTAs); warp 1 issues the MMAs (lane 0 of CTA 0) or relays the peer's
+// copy completions (CTA 1); warps 4..15 run the epilogue.  Barriers (all bounded waits):
+//   full[s]    this CTA's copies of stream position g landed in stage s (1 + tx)
+//   peer[s]    CTA 0 only: CTA 1's stage s landed (one remote arrival by CTA 1's warp 1)
+//   empty[s]   the pair's MMAs of stage s done (commit, multicast to both CTAs)
+//   acc_full   last MMA of an accumulation segment done (commit, multicast)
+//   acc_empty  CTA 0 only: accumulators of both CTAs read (every epilogue warp of both CTAs)
+//   xf[t], xe[t]  packed layers: diagonal-1 products handed to the diagonal-0 warps of column
+//                 group t (xf: written, xe: consumed), through a 4 KB exchange buffer per t
+constexpr int TCP_STAGES = 10;
+constexpr u32 TCP_N = 64;                                   // NTT slots per pair (MMA N)
+constexpr u32 TCP_ROWS = 128;                               // scalar rows per CTA (half the MMA M)
+constexpr u32 TCP_A_BYTES = TCP_ROWS * TC_KTILE * 2;        // 8 KB scalar tile
+constexpr u32 TCP_B_CHUNK = (TCP_N / 2) * TC_KTILE * 2;     // 2 KB: 32 slots x 32 terms of one chunk
+constexpr u32 TCP_STAGE_BYTES = TCP_A_BYTES + TC_CHUNKS * TCP_B_CHUNK;  // 18 KB
+constexpr u32 TCP_X_OFF = TCP_STAGES * TCP_STAGE_BYTES;
+constexpr u32 TCP_X_BYTES = 3 * 64 * 8 * 8;                 // [column group][group][8 slots] u64
+constexpr u32 TCP_BAR_OFF = TCP_X_OFF + TCP_X_BYTES;
+constexpr int TCP_NB = 3 * TCP_STAGES + 2 + 6;
+constexpr u32 TCP_SMEM_BYTES = TCP_BAR_OFF + TCP_NB * 8 + 16;
+static_assert(TCP_SMEM_BYTES <= 227 * 1024, "CTA-pair MAC exceeds shared memory");
+
+// item of the CTA-pair MAC: layer, row unit, polynomial, limb, first slot, pair tile
+template <int MAXB>
+__device__ __forceinline__ bool tcp_item(const Batch<MAXB>& B, u32 item, u32 N, u32 L, TcItem& it) {
+    if (item >= B.start[ST_MAC][B.n]) return false;
+    const u32 li = find_layer(B, ST_MAC, item);
+    const LayerDev& Ly = B.L[li];
+    const u32 npairs = (Ly.tc_rows + 2 * TCP_ROWS - 1) / (2 * TCP_ROWS), nn = N / TCP_N;
+    const u32 local = item - B.start[ST_MAC][li];
+    const u32 pt = local % npairs, n64 = (local / npairs) % nn, z = local / (npairs * nn);
+    it.ly = &Ly;
+    it.k = z % L, it.p = (z / L) & 1, it.ru = z / (2 * L);
+    it.n0 = n64 * TCP_N;
+    it.row0 = pt;  // the pair tile
+    it.nrows = 2 * TCP_ROWS;
+    it.n_tiles = Ly.Kpad / TC_KTILE;
+    return true;
+}
+
+// bounded wait on a barrier that threads of the other CTA of the pair arrive at
+__device__ __forceinline__ bool mbar_wait_cluster(u32 bar, u32 parity, long long limit, volatile int* abort_flag) {
+    for (long long it = 0; it < limit; it++) {
+        if (*abort_flag) return false;
+        u32 ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+// arrive on the barrier at the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ void mbar_arrive_remote(u32 bar, u32 rank) {
+    u32 remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(bar), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
+template <bool PACKED, int MAXB>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constant__ Batch<MAXB> B, KP kp) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const u32 N = kp.N, L = kp.L, NT = N / TC_MTILE;
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    u32 rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const u32 cid = blockIdx.x / 2, n_cl = gridDim.x / 2;
+    u64* bars = reinterpret_cast<u64*>(tsm + TCP_BAR_OFF);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    constexpr int FULL = 0, PEER = TCP_STAGES, EMPTY = 2 * TCP_STAGES, ACC_FULL = 3 * TCP_STAGES,
+                  ACC_EMPTY = ACC_FULL + 1, XF = ACC_FULL + 2, XE = XF + 3;
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + TCP_BAR_OFF + TCP_NB * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + TCP_BAR_OFF + TCP_NB * 8 + 4);
+    u64* xch = reinterpret_cast<u64*>(tsm + TCP_X_OFF);
+
+    if (tid == 0) {
+        for (int i = 0; i < TCP_STAGES; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(FULL + i)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(PEER + i)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_FULL)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_EMPTY)), "r"(2 * TC_EPI));
+        for (int t = 0; t < 3; t++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(XF + t)), "r"(2));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(XE + t)), "r"(2));
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        // the pair's accumulators: one warp of each CTA allocates, collectively, the same columns in both
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    // both CTAs' barriers are initialised before either copies, commits or arrives across the pair
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const u32 tmem = *tmem_slot;
+
+    auto wait = [&](int i, u32 parity) -> bool {
+        return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, nullptr);
+    };
+    auto wait_cl = [&](int i, u32 parity) -> bool { return mbar_wait_cluster(bar(i), parity, TC_SPIN_LIMIT, abort_flag); };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- copies (both CTAs)
+        u32 g = 0;
+        TcItem it;
+        bool ok = true;
+        for (u32 item = cid; ok && tcp_item(B, item, N, L, it); item += n_cl) {
+            const LayerDev& Ly = *it.ly;
+            const u32 ktiles = Ly.Kpad / TC_KTILE, mt = it.row0 * 2 + rank;
+            // this CTA's 32 slots of the 64: image rows (n0 mod 128) + 32 rank .. + 31 of tile n0 / 128
+            const unsigned char* ibase = reinterpret_cast<const unsigned char*>(
+                Ly.A16 + ((((size_t)it.ru * 2 + it.p) * L + it.k) * NT + it.n0 / TC_MTILE) * ktiles * IMG_HALVES) +
+                ((it.n0 % TC_MTILE) + rank * (TCP_N / 2)) / 8 * TC_SBO;
+            for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                const u32 s = g % TCP_STAGES;
+                const bool fr = g < TCP_STAGES || wait(EMPTY + s, ((g / TCP_STAGES) - 1) & 1);
+                if (!__all_sync(0xffffffffu, fr)) { ok = false; break; }
+                if (lane == 0) {
+                    const u32 st = smem_u32(tsm + s * TCP_STAGE_BYTES);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)),
+                                 "r"(TCP_STAGE_BYTES)
+                                 : "memory");
+                    const __half* asrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (TCP_ROWS * TC_KTILE);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(st),
+                        "l"(asrc), "r"(TCP_A_BYTES), "r"(bar(FULL + s))
+                        : "memory");
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                st + TCP_A_BYTES + c * TCP_B_CHUNK),
+                            "l"(ibase + (size_t)t * TCI_A_BYTES + c * TC_A_CHUNK_BYTES), "r"(TCP_B_CHUNK),
+                            "r"(bar(FULL + s))
+                            : "memory");
+                }
+                __syncwarp();
+            }
+            if (*abort_flag) ok = false;
+        }
+        // the other CTA's MMAs commit to this CTA's empty barriers: wait for the commits of the last
+        // uses of every stage, so none is still on its way when this CTA leaves
+        if (ok) {
+            for (u32 gg = g > TCP_STAGES ? g - TCP_STAGES : 0; gg < g; gg++)
+                if (!__all_sync(0xffffffffu, wait(EMPTY + gg % TCP_STAGES, (gg / TCP_STAGES) & 1))) break;
+        }
+    } else if (warp == 1 && rank == 1) {
+        // ---------------------------------------------------------------- relay (CTA 1)
+        if (lane == 0) {
+            u32 g = 0;
+            TcItem it;
+            bool ok = true;
+            for (u32 item = cid; ok && tcp_item(B, item, N, L, it); item += n_cl)
+                for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                    const u32 s = g % TCP_STAGES;
+                    if (!wait(FULL + s, (g / TCP_STAGES) & 1)) { ok = false; break; }
+                    mbar_arrive_remote(bar(PEER + s), 0);
+                }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMAs (CTA 0, lane 0)
+        if (lane == 0) {
+            u32 g = 0, unit = 0;
+            TcItem it;
+            const u32 idesc = tc_idesc(2 * TCP_ROWS, TCP_N);
+            for (u32 item = cid; tcp_item(B, item, N, L, it); item += n_cl) {
+                bool okk = true;
+                for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                    const u32 s = g % TCP_STAGES, tseg = t % TC_SEG_TILES;
+                    if (tseg == 0) {
+                        if (unit > 0 && !wait_cl(ACC_EMPTY, (unit - 1) & 1)) { okk = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                    }
+                    if (!wait(FULL + s, (g / TCP_STAGES) & 1) || !wait_cl(PEER + s, (g / TCP_STAGES) & 1)) {
+                        okk = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const u32 st = smem_u32(tsm + s * TCP_STAGE_BYTES);
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+#pragma unroll
+                        for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                            const u64 ad = smem_desc(st + ks * 256);
+                            const u64 bd = smem_desc(st + TCP_A_BYTES + c * TCP_B_CHUNK + ks * 256);
+                            const u32 acc = (tseg > 0 || ks > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + c * TCP_N),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        }
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+                        " [%0], %1;" ::"r"(bar(EMPTY + s)),
+                        "h"((uint16_t)3));
+                    if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
+                        asm volatile(
+                            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+                            " [%0], %1;" ::"r"(bar(ACC_FULL)),
+                            "h"((uint16_t)3));
+                        unit++;
+                    }
+                }
+                if (!okk) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------------- epilogue (both CTAs)
+        // warp (sp, t): TMEM lanes 32 sp .. + 31 (rows), column groups of 8 slots t, t + 3, t + 6
+        const u32 sp = warp & 3, t = (warp - 4) >> 2, rl = sp * 32 + lane;
+        const bool diag1 = PACKED && rl >= 64;
+        u32 unit = 0, xn = 0;  // accumulation units; exchanges of this column group
+        TcItem it;
+        for (u32 item = cid; tcp_item(B, item, N, L, it); item += n_cl) {
+            const LayerDev& Ly = *it.ly;
+            const u32 n_seg = (it.n_tiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
+            const u32 gl = PACKED ? (rl & 63) : rl;
+            const u32 g = it.row0 * (PACKED ? TCP_ROWS : 2 * TCP_ROWS) + rank * (PACKED ? 64 : TCP_ROWS) + gl;
+            const bool live = g < Ly.out_groups;
+            const u32 row = PACKED ? g * 2 + (diag1 ? 1 : 0) : g;  // the row in the scalar matrix
+            const u32 k = it.k, p = it.p;
+            const LimbC m = kp.limb[k];
+            bool okk = true;
+            for (u32 seg = 0; seg < n_seg && okk; seg++) {
+                if (!__all_sync(0xffffffffu, wait(ACC_FULL, unit & 1))) { okk = false; break; }
+                unit++;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const long long b = live ? Ly.bias[(size_t)seg * Ly.tc_rows + row] : 0;  // 512 S of the segment
+                for (u32 cb = t; cb < TCP_N / 8; cb += 3) {
+                    u32 d[TC_CHUNKS][8];
+#pragma unroll
+                    for (int c = 0; c < TC_CHUNKS; c++) {
+                        const u32 ta = tmem + ((sp * 32u) << 16) + (u32)(c * TCP_N) + cb * 8;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
+                                       "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
+                                     : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    u64 red[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const long long lo = ((long long)__float2int_rn(__uint_as_float(d[0][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[1][j])) + b) << 10) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
+                        const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
+                                             (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
+                        const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+                        red[j] = bred128((u128)a, m);
+                    }
+                    const u32 x0 = it.n0 + cb * 8;
+                    u64* xb = xch + ((size_t)t * 64 + gl) * 8;
+                    if (PACKED && diag1) {
+                        // A1 NTT(P_k) to the diagonal-0 thread of the same group and slots
+                        if (xn > 0 && !__all_sync(0xffffffffu, wait(XE + t, (xn - 1) & 1))) { okk = false; break; }
+#pragma unroll
+                        for (int j = 0; j < 8; j++) xb[j] = mulmod(red[j], Ly.pk[(size_t)k * N + x0 + j], m);
+                        __syncwarp();
+                        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(XF + t)) : "memory");
+                        xn++;
+                        continue;
+                    }
+                    u64 add[8];
+                    if (PACKED) {
+                        if (!__all_sync(0xffffffffu, wait(XF + t, xn & 1))) { okk = false; break; }
+#pragma unroll
+                        for (int j = 0; j < 8; j++) add[j] = xb[j];
+                        __syncwarp();
+                        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(XE + t)) : "memory");
+                        xn++;
+                    }
+                    if (live) {
+                        u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + g) * 2 + p) * L * N + (size_t)k * N + x0;
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            u64 out = PACKED ? addq(mulmod(kp.kmul, red[j], m), add[j], m.q) : red[j];
+                            if (seg > 0) out = addq(out, o[j], m.q);  // this thread stored the earlier segments
+                            o[j] = out;
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) {
+                    if (rank == 0) asm volatile("mbarrier.arrive.release.cluster.shared::cta.b64 _, [%0];" ::"r"(bar(ACC_EMPTY)) : "memory");
+                    else mbar_arrive_remote(bar(ACC_EMPTY), 0);
+                }
+            }
+            if (!okk) break;
+        }
+    }
+    // drain: after an abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    if (*abort_flag && tid == 0) {
+        for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
+        for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    // no CTA frees the pair's accumulators or leaves while the other may still arrive at its barriers
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
 }
 
 // ------------------------------------------------------------------ fused key switch + MAC
@@ -2016,11 +2342,11 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
-    bool tc = false, packed = false, dw = false, eager = false, img = false, fused = false;
+    bool tc = false, packed = false, dw = false, eager = false, img = false, fused = false, pair = false;
     u32 gt = 8, cl = 1;  // cl: CTAs per cluster of the operand-image MAC
     bool operator==(const MacVariant& o) const {
         return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img && cl == o.cl &&
-               fused == o.fused && (tc || eager || gt == o.gt);
+               fused == o.fused && pair == o.pair && (tc || eager || gt == o.gt);
     }
 };
 
@@ -2039,6 +2365,7 @@ u32 stage_blocks(const he_params* p, const StageLayer& s, int stage) {
             return d.n_ks * L * (N / KS_THREADS);
         case ST_MAC:
             if (s.mv.eager) return d.row_units * 2 * L * (N / MAC_THREADS) * ((d.out_groups + 3) / 4);
+            if (s.mv.pair) return d.row_units * 2 * L * (N / TCP_N) * ((d.tc_rows + 2 * TCP_ROWS - 1) / (2 * TCP_ROWS));
             if (s.mv.tc)
                 return d.row_units * 2 * L * (N / TC_MTILE) * ((d.tc_rows + d.tc_rows_per_cta - 1) / d.tc_rows_per_cta) /
                        s.mv.cl;
@@ -2107,6 +2434,36 @@ void mac_img_launch(bool packed, u32 items, const Batch<MAXB>& B, const KP& kp, 
     CUDA_OK(cudaLaunchKernelEx(&cfg, kern, B, kp, cols));
 }
 
+// Persistent launch of the CTA-pair MAC: as many pairs as fit the device at once, at most one per item.
+template <int MAXB>
+void mac_pair_launch(bool packed, u32 items, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
+    auto kern = packed ? k_mac_pair<true, MAXB> : k_mac_pair<false, MAXB>;
+    allow_smem(kern, TCP_SMEM_BYTES);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TCP_SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int cached = 0;  // pairs that fit at once (one device per process)
+    if (!cached) {
+        int n = 0;
+        cfg.gridDim = dim3(128);
+        if (cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = sm_count() / 2;
+        }
+        cached = std::max(n, 1);
+    }
+    cfg.gridDim = dim3(2 * std::min<u32>(items, (u32)cached));
+    CUDA_OK(cudaLaunchKernelEx(&cfg, kern, B, kp));
+}
+
 template <int LL, int MAXB>
 void ksmac_launch(bool packed, u32 grid, const Batch<MAXB>& B, const KP& kp, u32 cols, cudaStream_t s) {
     if (packed) {
@@ -2147,6 +2504,10 @@ void launch_mac_b(const he_params* p, const MacVariant& mv, u32 blocks, const Ba
         const u32 grid = std::min(blocks, (u32)sm_count());
         if (mv.fused) {
             launch_ksmac_b<MAXB>(p, mv.packed, grid, B, kp, cols, s);
+            return;
+        }
+        if (mv.pair) {
+            mac_pair_launch<MAXB>(mv.packed, blocks, B, kp, s);
             return;
         }
         if (mv.img) {
@@ -2346,7 +2707,7 @@ struct he_plan {
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
     bool packed = false, dw = false;
     u32 mac_groups = 8;
-    bool use_tc = false, eager = false, img = false, fused = false;
+    bool use_tc = false, eager = false, img = false, fused = false, pair = false;
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0, cl = 1;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
@@ -2392,7 +2753,7 @@ struct he_plan {
         L.A16 = img ? (__half*)(ws + off_A) : nullptr;
         if (use_tc && !img) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
-        s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused;
+        s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused, s.mv.pair = pair;
         L.fused = fused;
         if (fused) L.A16 = nullptr;
         return s;
@@ -2509,7 +2870,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     if ((impl == 2 || impl >= 4) && !tc_ok)
         fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
-    if (impl > 6) fail(HE_EINVAL, "mac_impl must be 0..6");
+    if (impl > 7) fail(HE_EINVAL, "mac_impl must be 0..7");
     if (tune && tune->tc_cluster && tune->tc_cluster != 2 && tune->tc_cluster != 4 && tune->tc_cluster != 8)
         fail(HE_EINVAL, "tc_cluster must be 0, 2, 4 or 8");
     P->eager = impl == 3;
@@ -2535,8 +2896,12 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 form = (impl >= 4) ? impl : (words ? 4u : 5u);
         if (form == 6 && (!one_tile || (tune && tune->tc_cluster)))
             fail(HE_EINVAL, "the fused key switch + MAC needs a layer whose rows fit one CTA and no cluster");
+        if (form == 7 && ((tune && tune->tc_cluster) || tc_rows_req))
+            fail(HE_EINVAL, "the CTA-pair MAC takes no tc_rows and no tc_cluster");
         P->img = form != 4;
         P->fused = form == 6;
+        P->pair = form == 7;
+        if (P->pair) P->tc_rows_per_cta = TCP_ROWS;
         P->cl = 1;
         const u32 cl_req = tune ? tune->tc_cluster : 0;
         if (cl_req > 1) {
@@ -2544,7 +2909,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
             // tile are split into a multiple of cl_req tiles of at most 96 rows, none of them empty
             const u32 m = cl_req * ((P->tc_rows + TC_NMAX * cl_req - 1) / (TC_NMAX * cl_req));
             const u32 rpc = ((P->tc_rows + m - 1) / m + 15) / 16 * 16;
-            if (!P->img || P->fused || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
+            if (!P->img || P->fused || P->pair || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
                 fail(HE_EINVAL, "tc_cluster needs the image-form tensor-core MAC, no tc_rows, and at least " +
                                     std::to_string(16 * (m - 1) + 16) + " output rows");
             P->cl = cl_req, P->tc_rows_per_cta = rpc;
@@ -2590,16 +2955,18 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 k_terms = P->img ? P->n_rot * P->in_pad : P->K;
         P->tc_kpad = (k_terms + TC_KTILE - 1) / TC_KTILE * TC_KTILE;
         // scalar tiles stored as the exact shared-memory image the MMA reads (K-major, no
-        // swizzle), one block of rows_per_cta x 32 terms per (row tile, K tile)
+        // swizzle), one block of rows_per_cta x 32 terms per (row tile, K tile); the CTA-pair form
+        // has two tiles of 128 rows per pair tile, each ordered diagonal-major (see k_mac_pair)
         const u32 rpc = P->tc_rows_per_cta, ktiles = P->tc_kpad / TC_KTILE;
-        const u32 mtiles = (P->tc_rows + rpc - 1) / rpc;
+        const u32 mtiles = P->pair ? 2 * ((P->tc_rows + 2 * TCP_ROWS - 1) / (2 * TCP_ROWS)) : (P->tc_rows + rpc - 1) / rpc;
         std::vector<__half> h16((size_t)mtiles * ktiles * rpc * TC_KTILE, __float2half(0.0f));
         // bias [segment][row] = 512 x the sum of the row's scalars over the segment's terms
         const u32 n_seg = (ktiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
         std::vector<int> bias((size_t)n_seg * P->tc_rows, 0);
         for (u32 g = 0; g < lay.out_groups; g++)
             for (u32 r = 0; r < NR; r++) {
-                const u32 row = g * NR + r, mt = row / rpc, rl = row % rpc;
+                const u32 row = g * NR + r, per = P->packed ? TCP_ROWS / 2 : TCP_ROWS;
+                const u32 mt = P->pair ? g / per : row / rpc, rl = P->pair ? r * (TCP_ROWS / 2) + g % per : row % rpc;
                 for (u32 kk0 = 0; kk0 < P->K; kk0++) {
                     int v = sc[((size_t)g * NR + r) * P->K + kk0];
                     const u32 kk = P->img ? (kk0 % P->n_rot) * P->in_pad + kk0 / P->n_rot : kk0;
@@ -2618,7 +2985,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     if (P->use_tc) {
         u32 cols = 32;
         while (cols < (u32)TC_CHUNKS * P->tc_rows_per_cta) cols <<= 1;
-        P->tmem_cols = cols;
+        P->tmem_cols = P->pair ? 512 : cols;  // the pair form holds 5 x 64 columns
     }
     CUDA_OK(cudaStreamSynchronize(s));
     // workspace: R [n_ct_in][r_slots][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N] and, for
@@ -2780,7 +3147,7 @@ extern "C" int he_conv_time(const he_params* p, const he_conv_desc* d, const int
 extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
     return guard([&] {
         if (!plan || !mac_impl) fail(HE_EINVAL, "null argument");
-        *mac_impl = plan->use_tc ? (plan->fused ? 6 : (plan->img ? 5 : 4)) : (plan->eager ? 3 : 1);
+        *mac_impl = plan->use_tc ? (plan->pair ? 7 : (plan->fused ? 6 : (plan->img ? 5 : 4))) : (plan->eager ? 3 : 1);
     });
 }
 

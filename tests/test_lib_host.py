@@ -210,7 +210,8 @@ def test_noalloc_scratch_size_matches_the_header():
 
 def test_cluster_and_form_choices_are_checked_without_a_device():
     """he_conv_check applies the tensor-core form and cluster rules on the host: clusters need a
-    layer wider than one row tile, the fused form a layer that fits one."""
+    layer wider than one row tile, the fused form a layer that fits one, the CTA-pair form takes
+    neither clusters nor a row tile."""
     p = H.he_params_create(1024, 2, decomp_bits=25)
     narrow = H.conv_desc(C_in=6, C_out=16, H=3, W=3, kh=3, stride=1, n_images=1, c_n=2)
     wide = H.conv_desc(C_in=6, C_out=512, H=3, W=3, kh=3, stride=1, n_images=1, c_n=2)
@@ -221,7 +222,11 @@ def test_cluster_and_form_choices_are_checked_without_a_device():
     assert H.he_conv_check(p, wide, ww, tc_cluster=3) == H.HE_EINVAL
     assert H.he_conv_check(p, narrow, wn, mac_impl=6) == H.HE_OK
     assert H.he_conv_check(p, wide, ww, mac_impl=6) == H.HE_EINVAL
-    assert H.he_conv_check(p, wide, ww, mac_impl=7) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, mac_impl=7) == H.HE_OK
+    assert H.he_conv_check(p, narrow, wn, mac_impl=7) == H.HE_OK
+    assert H.he_conv_check(p, wide, ww, mac_impl=7, tc_cluster=2) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, mac_impl=7, tc_rows=64) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, mac_impl=8) == H.HE_EINVAL
     H.he_params_destroy(p)
 
 

@@ -273,7 +273,9 @@ __host__ __device__ constexpr size_t ntt_smem_bytes(u32 N) { return ((size_t)N +
 // (binary search; empty layers are skipped) and works on local block
 // b - start[stage][l].  A single layer is a table of one.
 struct LayerDev {
-    CUtensorMap rmap;          // R as a 3-D tensor (slot, polynomial*L + limb, row = ct*n_rot + rot), tensor-core MAC
+    CUtensorMap rmap;          // R as a 3-D tensor (slot, polynomial*L + limb, row = ct*n_rot + rot), tensor-core MAC;
+                               // CTA-pair MAC: the operand images (tcp_encode_maps)
+    CUtensorMap smap;          // CTA-pair MAC: the scalar tiles
     const u64* in;             // input ciphertexts [n_ct_in][2][L][N]
     u64* R;                    // rotated copies [n_ct_in][n_rot][2][L][N], NTT form
     u64* D;                    // digit NTTs [n_ct_in][L l][L][N]
@@ -1055,11 +1057,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
     }
     // drain: every copy that was issued is waited for by the converters in the normal path; after an
     // abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    // (after every role has left its loop, so that a wait that gave up late is still reported)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
     if (*abort_flag && tid == 0) {
         for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
         for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -1540,11 +1544,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         }
     }
     // drain: after an abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    // (after every role has left its loop, so that a wait that gave up late is still reported)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
     if (*abort_flag && tid == 0) {
         for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
         for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -1562,10 +1568,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
 // for 128 x 64 x 32 products per chunk.  Rows of a CTA's tile are ordered diagonal-major: row
 // l < 64 is (group g0 + l, diagonal 0), row 64 + l is (group g0 + l, diagonal 1) (unpacked: row l
 // is group g0 + l).  An item is (row unit, polynomial, limb, 64-slot tile, 256-row pair tile).
-// Roles: warp 0 copies (both CTAs); warp 1 issues the MMAs (lane 0 of CTA 0) or relays the peer's
-// copy completions (CTA 1); warps 4..15 run the epilogue.  Barriers (all bounded waits):
-//   full[s]    this CTA's copies of stream position g landed in stage s (1 + tx)
-//   peer[s]    CTA 0 only: CTA 1's stage s landed (one remote arrival by CTA 1's warp 1)
+// Roles: warp 0 copies (both CTAs, tensor copies with .cta_group::2 so that CTA 1's copies complete
+// on CTA 0's barrier); warp 1 issues the MMAs (lane 0 of CTA 0); warps 4..15 run the epilogue.
+// Barriers (all bounded waits):
+//   full[s]    CTA 0 only: both CTAs' copies of stream position g landed in stage s (CTA 0 arrives
+//              once and expects the bytes of both)
 //   empty[s]   the pair's MMAs of stage s done (commit, multicast to both CTAs)
 //   acc_full   last MMA of an accumulation segment done (commit, multicast)
 //   acc_empty  CTA 0 only: accumulators of both CTAs read (every epilogue warp of both CTAs)
@@ -1580,7 +1587,7 @@ constexpr u32 TCP_STAGE_BYTES = TCP_A_BYTES + TC_CHUNKS * TCP_B_CHUNK;  // 18 KB
 constexpr u32 TCP_X_OFF = TCP_STAGES * TCP_STAGE_BYTES;
 constexpr u32 TCP_X_BYTES = 3 * 64 * 8 * 8;                 // [column group][group][8 slots] u64
 constexpr u32 TCP_BAR_OFF = TCP_X_OFF + TCP_X_BYTES;
-constexpr int TCP_NB = 3 * TCP_STAGES + 2 + 6;
+constexpr int TCP_NB = 2 * TCP_STAGES + 2 + 6;
 constexpr u32 TCP_SMEM_BYTES = TCP_BAR_OFF + TCP_NB * 8 + 16;
 static_assert(TCP_SMEM_BYTES <= 227 * 1024, "CTA-pair MAC exceeds shared memory");
 
@@ -1636,7 +1643,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constan
     const u32 cid = blockIdx.x / 2, n_cl = gridDim.x / 2;
     u64* bars = reinterpret_cast<u64*>(tsm + TCP_BAR_OFF);
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
-    constexpr int FULL = 0, PEER = TCP_STAGES, EMPTY = 2 * TCP_STAGES, ACC_FULL = 3 * TCP_STAGES,
+    constexpr int FULL = 0, EMPTY = TCP_STAGES, ACC_FULL = 2 * TCP_STAGES,
                   ACC_EMPTY = ACC_FULL + 1, XF = ACC_FULL + 2, XE = XF + 3;
     u32* tmem_slot = reinterpret_cast<u32*>(tsm + TCP_BAR_OFF + TCP_NB * 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + TCP_BAR_OFF + TCP_NB * 8 + 4);
@@ -1645,7 +1652,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constan
     if (tid == 0) {
         for (int i = 0; i < TCP_STAGES; i++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(FULL + i)), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(PEER + i)), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(1));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_FULL)), "r"(1));
@@ -1679,35 +1685,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constan
         u32 g = 0;
         TcItem it;
         bool ok = true;
+        u32 full0;  // CTA 0's full barriers, as shared::cluster addresses
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(full0) : "r"(bar(FULL)), "r"(0));
         for (u32 item = cid; ok && tcp_item(B, item, N, L, it); item += n_cl) {
             const LayerDev& Ly = *it.ly;
             const u32 ktiles = Ly.Kpad / TC_KTILE, mt = it.row0 * 2 + rank;
-            // this CTA's 32 slots of the 64: image rows (n0 mod 128) + 32 rank .. + 31 of tile n0 / 128
-            const unsigned char* ibase = reinterpret_cast<const unsigned char*>(
-                Ly.A16 + ((((size_t)it.ru * 2 + it.p) * L + it.k) * NT + it.n0 / TC_MTILE) * ktiles * IMG_HALVES) +
-                ((it.n0 % TC_MTILE) + rank * (TCP_N / 2)) / 8 * TC_SBO;
+            // this CTA's 32 slots of the 64: quarter (n0 mod 128) / 32 + rank of image tile n0 / 128
+            const u32 quarter = (it.n0 % TC_MTILE) / (TCP_N / 2) + rank;
+            const u32 img0 = (((it.ru * 2 + it.p) * L + it.k) * NT + it.n0 / TC_MTILE) * ktiles;
             for (u32 t = 0; t < it.n_tiles; t++, g++) {
                 const u32 s = g % TCP_STAGES;
                 const bool fr = g < TCP_STAGES || wait(EMPTY + s, ((g / TCP_STAGES) - 1) & 1);
                 if (!__all_sync(0xffffffffu, fr)) { ok = false; break; }
                 if (lane == 0) {
-                    const u32 st = smem_u32(tsm + s * TCP_STAGE_BYTES);
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)),
-                                 "r"(TCP_STAGE_BYTES)
-                                 : "memory");
-                    const __half* asrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (TCP_ROWS * TC_KTILE);
+                    const u32 st = smem_u32(tsm + s * TCP_STAGE_BYTES), fb = full0 + s * 8;
+                    if (rank == 0)
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)),
+                                     "r"(2 * TCP_STAGE_BYTES)
+                                     : "memory");
+                    // scalar tile (mt, t): rows (mt ktiles + t) 16 .. + 15 of 512 bytes
                     asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(st),
-                        "l"(asrc), "r"(TCP_A_BYTES), "r"(bar(FULL + s))
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(st),
+                        "l"(&Ly.smap), "r"(0), "r"((mt * ktiles + t) * 16), "r"(fb)
                         : "memory");
-#pragma unroll
-                    for (int c = 0; c < TC_CHUNKS; c++)
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                st + TCP_A_BYTES + c * TCP_B_CHUNK),
-                            "l"(ibase + (size_t)t * TCI_A_BYTES + c * TC_A_CHUNK_BYTES), "r"(TCP_B_CHUNK),
-                            "r"(bar(FULL + s))
-                            : "memory");
+                    // image (img0 + t): core-matrix rows 4 quarter .. + 3 of every chunk
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+                        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(st + TCP_A_BYTES),
+                        "l"(&Ly.rmap), "r"(0), "r"(4 * quarter), "r"(0), "r"(img0 + t), "r"(fb)
+                        : "memory");
                 }
                 __syncwarp();
             }
@@ -1719,21 +1726,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constan
             for (u32 gg = g > TCP_STAGES ? g - TCP_STAGES : 0; gg < g; gg++)
                 if (!__all_sync(0xffffffffu, wait(EMPTY + gg % TCP_STAGES, (gg / TCP_STAGES) & 1))) break;
         }
-    } else if (warp == 1 && rank == 1) {
-        // ---------------------------------------------------------------- relay (CTA 1)
-        if (lane == 0) {
-            u32 g = 0;
-            TcItem it;
-            bool ok = true;
-            for (u32 item = cid; ok && tcp_item(B, item, N, L, it); item += n_cl)
-                for (u32 t = 0; t < it.n_tiles; t++, g++) {
-                    const u32 s = g % TCP_STAGES;
-                    if (!wait(FULL + s, (g / TCP_STAGES) & 1)) { ok = false; break; }
-                    mbar_arrive_remote(bar(PEER + s), 0);
-                }
-        }
-        __syncwarp();
-    } else if (warp == 1) {
+    } else if (warp == 1 && rank == 0) {
         // ---------------------------------------------------------------- MMAs (CTA 0, lane 0)
         if (lane == 0) {
             u32 g = 0, unit = 0;
@@ -1747,10 +1740,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constan
                         if (unit > 0 && !wait_cl(ACC_EMPTY, (unit - 1) & 1)) { okk = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;");
                     }
-                    if (!wait(FULL + s, (g / TCP_STAGES) & 1) || !wait_cl(PEER + s, (g / TCP_STAGES) & 1)) {
-                        okk = false;
-                        break;
-                    }
+                    if (!wait(FULL + s, (g / TCP_STAGES) & 1)) { okk = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const u32 st = smem_u32(tsm + s * TCP_STAGE_BYTES);
 #pragma unroll
@@ -1868,11 +1858,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_pair(const __grid_constan
         }
     }
     // drain: after an abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    // (after every role has left its loop, so that a wait that gave up late is still reported)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
     if (*abort_flag && tid == 0) {
         for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
         for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
     // no CTA frees the pair's accumulators or leaves while the other may still arrive at its barriers
     asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
     if (warp == 0) {
@@ -2176,11 +2168,13 @@ __global__ void __launch_bounds__(KF_THREADS, 1) k_ksmac(const __grid_constant__
             if (!okk) break;
         }
     }
+    // (after every role has left its loop, so that a wait that gave up late is still reported)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
     if (*abort_flag && tid == 0) {
         for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
         for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -2266,7 +2260,8 @@ KP make_kp(const he_params* p) {
 u32 ntt_threads(u32 N) { return std::min<u32>(NTT_MAX_THREADS, N / NTT_E); }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
-void encode_rmap(CUtensorMap* map, const u64* R, u32 N, u32 L, u32 rows) {
+void encode_tiled(CUtensorMap* map, CUtensorMapDataType type, u32 rank, const void* base, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -2277,14 +2272,32 @@ void encode_rmap(CUtensorMap* map, const u64* R, u32 N, u32 L, u32 rows) {
             fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
     });
     if (!fn) fail(HE_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(map, type, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(HE_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+void encode_rmap(CUtensorMap* map, const u64* R, u32 N, u32 L, u32 rows) {
     const cuuint64_t dims[3] = {N, 2ull * L, rows};
     const cuuint64_t strides[2] = {(cuuint64_t)N * 8, 2ull * L * N * 8};
     const cuuint32_t box[3] = {TC_MTILE, 1, TC_KTILE};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)R, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) fail(HE_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, R, dims, strides, box);
+}
+
+// The CTA-pair MAC's copies.  Images as (512-byte core-matrix row of 256 halves, row 0..15 of a
+// chunk, chunk 0..4, image), one copy taking 4 rows of each chunk (a CTA's 32 slots, 10 KB);
+// scalar tiles as rows of 512 bytes, one copy taking the 16 rows of a tile (8 KB).
+void tcp_encode_maps(CUtensorMap* imap, CUtensorMap* smap, const __half* A16, u64 n_img, const __half* sc16,
+                     u64 n_tiles) {
+    const cuuint64_t idims[4] = {256, 16, TC_CHUNKS, n_img};
+    const cuuint64_t istr[3] = {TC_SBO, TC_A_CHUNK_BYTES, TCI_A_BYTES};
+    const cuuint32_t ibox[4] = {256, 4, TC_CHUNKS, 1};
+    encode_tiled(imap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, A16, idims, istr, ibox);
+    const cuuint64_t sdims[2] = {256, n_tiles * 16};
+    const cuuint64_t sstr[1] = {512};
+    const cuuint32_t sbox[2] = {256, 16};
+    encode_tiled(smap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, sc16, sdims, sstr, sbox);
 }
 
 int sm_count() {
@@ -2752,6 +2765,11 @@ struct he_plan {
         L.ks_rg = img ? ksi_groups(lay.row_units, in_pad, n_rot, p->L, p->N) : 1;
         L.A16 = img ? (__half*)(ws + off_A) : nullptr;
         if (use_tc && !img) encode_rmap(&L.rmap, L.R, p->N, p->L, lay.n_ct_in * n_rot);
+        if (pair) {
+            const u64 ktiles = tc_kpad / TC_KTILE, npairs = (tc_rows + 2 * TCP_ROWS - 1) / (2 * TCP_ROWS);
+            tcp_encode_maps(&L.rmap, &L.smap, L.A16, (u64)lay.row_units * 2 * p->L * (p->N / TC_MTILE) * ktiles,
+                            d_sc16, 2 * npairs * ktiles);
+        }
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
         s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused, s.mv.pair = pair;
         L.fused = fused;

@@ -570,9 +570,10 @@ def run_gpu(args, rank, world):
     top = max(stages_b, key=lambda k: stages_b[k][0])
     # the kernels of each stage: he_conv_info 1 CUDA-core MAC, 3 eager, 4 tensor-core with in-kernel
     # conversion, 5 tensor-core on operand images, 6 fused key switch + tensor-core MAC, 7 operand
-    # images on CTA pairs
-    mac_k = {1: "k_mac", 3: "k_mac_eager", 4: "k_mac_tc", 5: "k_mac_img", 6: "k_ksmac", 7: "k_mac_pair"}
-    ks_k = {1: "k_keyswitch", 3: "k_keyswitch", 4: "k_keyswitch", 5: "k_keyswitch_img", 7: "k_keyswitch_img"}
+    # images on CTA pairs, 8 operand images in chunk passes
+    mac_k = {1: "k_mac", 3: "k_mac_eager", 4: "k_mac_tc", 5: "k_mac_img", 6: "k_ksmac", 7: "k_mac_pair", 8: "k_mac_cp"}
+    ks_k = {1: "k_keyswitch", 3: "k_keyswitch", 4: "k_keyswitch", 5: "k_keyswitch_img", 7: "k_keyswitch_img",
+            8: "k_keyswitch_img"}
     kname = {"mac": " + ".join(sorted({mac_k[i] for i in impls})),
              "keyswitch": " + ".join(sorted({ks_k[i] for i in impls if i != 6})) or "none (fused)",
              "ntt_in": "k_ntt_inputs", "ntt_out": "k_intt"}
@@ -866,7 +867,7 @@ def run_forms(args):
         d = H.conv_desc(**s)
         _, wt, _ = synth.stack_inputs(args.workload, i, H.he_params_info(p).t)
         row = {"mode": "forms", "workload": args.workload, "layer": i}
-        for impl in (0, 4, 5, 6, 7):
+        for impl in (0, 4, 5, 6, 7, 8):
             try:
                 total, stages = H.he_conv_time(p, d, wt, mac_impl=impl, reps=max(3, args.steps),
                                                stream=stream.cuda_stream)

@@ -186,7 +186,10 @@ typedef struct {
                                 6 key switch fused into the tensor-core MAC (rows fitting one CTA only);
                                 7 tensor-core MAC on operand images in CTA pairs (tcgen05 cta_group::2,
                                   256 output rows per pair as the MMA's M dimension, 64 slots as N;
-                                  HE_EINVAL with tc_rows or tc_cluster set) */
+                                  HE_EINVAL with tc_rows or tc_cluster set);
+                                8 tensor-core MAC on operand images in chunk passes (up to 256 output rows
+                                  per CTA, floor(512 / rows) chunks accumulated per pass; HE_EINVAL with
+                                  tc_rows or tc_cluster set) */
     uint32_t tc_rows;        /* tensor-core MAC: output rows per CTA, a multiple of 16 up to 96 (0 -> 96) */
     uint32_t tc_cluster;     /* image-form tensor-core MAC: 0 (default) or 2, 4, 8 -- run in clusters of
                                 that many CTAs that share each operand image by TMA multicast, each CTA
@@ -220,7 +223,8 @@ int he_conv_forward_host(const he_plan* plan, const uint64_t* h_in, uint64_t* h_
  * an earlier forward of this plan gave up (the outputs are then invalid). */
 int he_conv_status(const he_plan* plan);
 /* *mac_impl = 1 (CUDA-core MAC), 3 (eager), or the tensor-core form: 4 (in-kernel conversion),
- * 5 (operand images), 6 (key switch fused) or 7 (operand images in CTA pairs) for this plan.  The
+ * 5 (operand images), 6 (key switch fused), 7 (operand images in CTA pairs) or 8 (operand images
+ * in chunk passes) for this plan.  The
  * tensor-core form (fp16 10-bit chunks, fp32 sums of at most 2048 terms per
  * accumulation) is chosen automatically when it is exact: no depthwise,
  * |s| <= 16 and every limb below 2^50 (five chunks). */

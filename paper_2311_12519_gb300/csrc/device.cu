@@ -1560,6 +1560,226 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
     if (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// ------------------------------------------------------------------ operand images, chunk passes
+// Step 3, operand-image form with chunk passes, for layers of many output rows.  TMEM holds 512
+// columns of fp32 accumulators for the CTA's 128 slots, so five chunk accumulators allow at most
+// 102 rows; here a work item takes up to 256 rows and accumulates `cpp` = floor(512 / rows) chunks
+// of the residues per pass (two chunks for 256 rows, four for 128, all five for 96 or fewer),
+// running ceil(5 / cpp) passes over its K tiles, each copying only its chunks of the images.  A
+// 512-row layer then reads each image twice (two 256-row items) instead of six times (six
+// 96-row items), and its MMAs have N = 256, the shape that reaches the tensor pipe's peak.  Each
+// (pass, segment) accumulation is reduced in the epilogue to sum_c 2^(10 c) (D_c + 512 S) mod q
+// over its chunks, put through the Hadamard PMult (linear in A0, A1) and added mod q into the
+// output, like the segments of the other forms.  Roles and barriers as in k_mac_img (CL = 1).
+constexpr int TCC_STAGES = 4;
+constexpr u32 TCC_ROWS = 256;                                   // rows per item at most (MMA N)
+constexpr u32 TCC_B_OFF = TCI_A_BYTES;                          // scalar tile after the image chunks
+constexpr u32 TCC_STAGE_BYTES = TCI_A_BYTES + TCC_ROWS * TC_KTILE * 2;  // 40 KB + 16 KB
+constexpr u32 TCC_BAR_OFF = TCC_STAGES * TCC_STAGE_BYTES;
+constexpr u32 TCC_SMEM_BYTES = TCC_BAR_OFF + 128;
+static_assert(TCC_SMEM_BYTES <= 227 * 1024, "chunk-pass MAC exceeds shared memory");
+
+__host__ __device__ constexpr u32 tcc_cpp(u32 rows_per_cta) {
+    return 512 / rows_per_cta >= (u32)TC_CHUNKS ? (u32)TC_CHUNKS : 512 / rows_per_cta;
+}
+
+template <bool PACKED, int MAXB>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mac_cp(const __grid_constant__ Batch<MAXB> B, KP kp) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    constexpr int NR = PACKED ? 2 : 1;
+    constexpr int NB = 2 * TCC_STAGES + 2;
+    const u32 N = kp.N, L = kp.L, NT = N / TC_MTILE;
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    u64* bars = reinterpret_cast<u64*>(tsm + TCC_BAR_OFF);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    constexpr int FULL = 0, EMPTY = TCC_STAGES, ACC_FULL = 2 * TCC_STAGES, ACC_EMPTY = 2 * TCC_STAGES + 1;
+    u32* tmem_slot = reinterpret_cast<u32*>(tsm + TCC_BAR_OFF + NB * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tsm + TCC_BAR_OFF + NB * 8 + 4);
+
+    if (tid == 0) {
+        for (int i = 0; i < TCC_STAGES; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(FULL + i)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(EMPTY + i)), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_FULL)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(ACC_EMPTY)), "r"(TC_EPI));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const u32 tmem = *tmem_slot;
+
+    auto wait = [&](int i, u32 parity) -> bool {
+        return mbar_wait_bounded(bar(i), parity, TC_SPIN_LIMIT, abort_flag, nullptr);
+    };
+    auto arrive = [&](int i) { asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(i)) : "memory"); };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- copies
+        u32 g = 0;
+        TcItem it;
+        bool ok = true;
+        for (u32 item = blockIdx.x; ok && tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 rpc = Ly.tc_rows_per_cta, cpp = tcc_cpp(rpc), bbytes = rpc * TC_KTILE * 2;
+            const u32 ktiles = Ly.Kpad / TC_KTILE, mt = it.row0 / rpc, nt = it.n0 / TC_MTILE;
+            const unsigned char* abase = reinterpret_cast<const unsigned char*>(
+                Ly.A16 + ((((size_t)it.ru * 2 + it.p) * L + it.k) * NT + nt) * ktiles * IMG_HALVES);
+            for (u32 c0 = 0; ok && c0 < (u32)TC_CHUNKS; c0 += cpp) {
+                const u32 ncp = min(cpp, (u32)TC_CHUNKS - c0);
+                for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                    const u32 s = g % TCC_STAGES;
+                    const bool fr = g < TCC_STAGES || wait(EMPTY + s, ((g / TCC_STAGES) - 1) & 1);
+                    if (!__all_sync(0xffffffffu, fr)) { ok = false; break; }
+                    if (lane == 0) {
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(FULL + s)),
+                                     "r"(ncp * TC_A_CHUNK_BYTES + bbytes)
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                smem_u32(tsm + s * TCC_STAGE_BYTES)),
+                            "l"(abase + (size_t)t * TCI_A_BYTES + c0 * TC_A_CHUNK_BYTES), "r"(ncp * TC_A_CHUNK_BYTES),
+                            "r"(bar(FULL + s))
+                            : "memory");
+                        const __half* bsrc = Ly.sc16 + ((size_t)mt * ktiles + t) * (rpc * TC_KTILE);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                smem_u32(tsm + s * TCC_STAGE_BYTES + TCC_B_OFF)),
+                            "l"(bsrc), "r"(bbytes), "r"(bar(FULL + s))
+                            : "memory");
+                    }
+                    __syncwarp();
+                }
+            }
+            if (*abort_flag) ok = false;
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMAs (lane 0)
+        if (lane == 0) {
+            u32 g = 0, unit = 0;  // unit = (item, pass, segment): one accumulation in TMEM
+            TcItem it;
+            bool okk = true;
+            for (u32 item = blockIdx.x; okk && tc_item(B, item, N, L, it); item += gridDim.x) {
+                const u32 idesc = tc_idesc(TC_MTILE, it.nrows), cpp = tcc_cpp(it.ly->tc_rows_per_cta);
+                for (u32 c0 = 0; okk && c0 < (u32)TC_CHUNKS; c0 += cpp) {
+                    const u32 ncp = min(cpp, (u32)TC_CHUNKS - c0);
+                    for (u32 t = 0; t < it.n_tiles; t++, g++) {
+                        const u32 s = g % TCC_STAGES, tseg = t % TC_SEG_TILES;
+                        if (tseg == 0) {
+                            if (unit > 0 && !wait(ACC_EMPTY, (unit - 1) & 1)) { okk = false; break; }
+                            asm volatile("tcgen05.fence::after_thread_sync;");
+                        }
+                        if (!wait(FULL + s, (g / TCC_STAGES) & 1)) { okk = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const u32 a_base = smem_u32(tsm + s * TCC_STAGE_BYTES), b_base = a_base + TCC_B_OFF;
+                        for (u32 c = 0; c < ncp; c++) {
+#pragma unroll
+                            for (int ks = 0; ks < TC_KTILE / 16; ks++) {
+                                const u64 ad = smem_desc(a_base + c * TC_A_CHUNK_BYTES + ks * 256);
+                                const u64 bd = smem_desc(b_base + ks * 256);
+                                const u32 acc = (tseg > 0 || ks > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + c * it.nrows),
+                                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            bar(EMPTY + s)));
+                        if (tseg == TC_SEG_TILES - 1 || t + 1 == it.n_tiles) {
+                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                bar(ACC_FULL)));
+                            unit++;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------------- epilogue
+        u32 unit = 0;
+        TcItem it;
+        bool okk = true;
+        for (u32 item = blockIdx.x; okk && tc_item(B, item, N, L, it); item += gridDim.x) {
+            const LayerDev& Ly = *it.ly;
+            const u32 n_seg = (it.n_tiles + TC_SEG_TILES - 1) / TC_SEG_TILES, cpp = tcc_cpp(Ly.tc_rows_per_cta);
+            const u32 sp = warp & 3, third = (warp - 4) >> 2;
+            const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
+            const LimbC m = kp.limb[k];
+            const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+            for (u32 c0 = 0; okk && c0 < (u32)TC_CHUNKS; c0 += cpp) {
+                const u32 ncp = min(cpp, (u32)TC_CHUNKS - c0);
+                for (u32 seg = 0; seg < n_seg; seg++) {
+                    if (!__all_sync(0xffffffffu, wait(ACC_FULL, unit & 1))) { okk = false; break; }
+                    unit++;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const bool first = c0 == 0 && seg == 0;
+                    for (u32 cb = third * 8; cb < nrows; cb += 24) {
+                        u32 d[TC_CHUNKS][8];
+#pragma unroll
+                        for (int c = 0; c < TC_CHUNKS; c++) {
+                            if ((u32)c >= ncp) break;
+                            const u32 ta = tmem + ((sp * 32u) << 16) + (u32)c * nrows + cb;
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                         : "=r"(d[c][0]), "=r"(d[c][1]), "=r"(d[c][2]), "=r"(d[c][3]), "=r"(d[c][4]),
+                                           "=r"(d[c][5]), "=r"(d[c][6]), "=r"(d[c][7])
+                                         : "r"(ta));
+                        }
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        u64 red[8];
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const long long b = Ly.bias[(size_t)seg * Ly.tc_rows + row0 + cb + j];  // 512 S of the segment
+                            i128 a = (i128)m.q << 40;  // keeps the sum positive; a multiple of q
+#pragma unroll
+                            for (int c = 0; c < TC_CHUNKS; c++) {
+                                if ((u32)c >= ncp) break;
+                                a += (i128)((long long)__float2int_rn(__uint_as_float(d[c][j])) + b) << (10 * (c0 + c));
+                            }
+                            red[j] = bred128((u128)a, m);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; j += NR) {
+                            const u32 row = row0 + cb + j;
+                            const u32 gg = row / NR;
+                            if (gg >= Ly.out_groups) continue;
+                            u64 out = red[j];
+                            if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                            u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
+                            if (!first) out = addq(out, *o, m.q);  // this thread stored the earlier accumulations
+                            *o = out;
+                        }
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) arrive(ACC_EMPTY);  // accumulators free
+                }
+            }
+        }
+    }
+    // drain: after an abort, give in-flight copies and MMAs a bounded time to land before TMEM is freed
+    // (after every role has left its loop, so that a wait that gave up late is still reported)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (*abort_flag && tid == 0) {
+        for (u32 i = 0; i < B.n; i++) atomicExch(B.L[i].err, 1);
+        for (long long i = 0; i < TC_SPIN_LIMIT / 16; i++) __nanosleep(64);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
 // ------------------------------------------------------------------ operand images, CTA pairs
 // Step 3, operand-image form on CTA pairs (tcgen05 cta_group::2), for layers of many output rows.
 // The roles of the operands swap: the scalar rows are the MMA's M dimension (128 rows in each
@@ -2355,11 +2575,11 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
-    bool tc = false, packed = false, dw = false, eager = false, img = false, fused = false, pair = false;
+    bool tc = false, packed = false, dw = false, eager = false, img = false, fused = false, pair = false, cp = false;
     u32 gt = 8, cl = 1;  // cl: CTAs per cluster of the operand-image MAC
     bool operator==(const MacVariant& o) const {
         return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img && cl == o.cl &&
-               fused == o.fused && pair == o.pair && (tc || eager || gt == o.gt);
+               fused == o.fused && pair == o.pair && cp == o.cp && (tc || eager || gt == o.gt);
     }
 };
 
@@ -2521,6 +2741,16 @@ void launch_mac_b(const he_params* p, const MacVariant& mv, u32 blocks, const Ba
         }
         if (mv.pair) {
             mac_pair_launch<MAXB>(mv.packed, blocks, B, kp, s);
+            return;
+        }
+        if (mv.cp) {
+            if (mv.packed) {
+                allow_smem(k_mac_cp<true, MAXB>, TCC_SMEM_BYTES);
+                k_mac_cp<true, MAXB><<<grid, TC_THREADS, TCC_SMEM_BYTES, s>>>(B, kp);
+            } else {
+                allow_smem(k_mac_cp<false, MAXB>, TCC_SMEM_BYTES);
+                k_mac_cp<false, MAXB><<<grid, TC_THREADS, TCC_SMEM_BYTES, s>>>(B, kp);
+            }
             return;
         }
         if (mv.img) {
@@ -2720,7 +2950,7 @@ struct he_plan {
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
     bool packed = false, dw = false;
     u32 mac_groups = 8;
-    bool use_tc = false, eager = false, img = false, fused = false, pair = false;
+    bool use_tc = false, eager = false, img = false, fused = false, pair = false, cp = false;
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0, cl = 1;
     u64* d_ksk = nullptr;
     RotDev* d_rots = nullptr;
@@ -2771,7 +3001,7 @@ struct he_plan {
                             d_sc16, 2 * npairs * ktiles);
         }
         s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
-        s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused, s.mv.pair = pair;
+        s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused, s.mv.pair = pair, s.mv.cp = cp;
         L.fused = fused;
         if (fused) L.A16 = nullptr;
         return s;
@@ -2888,7 +3118,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     if ((impl == 2 || impl >= 4) && !tc_ok)
         fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
-    if (impl > 7) fail(HE_EINVAL, "mac_impl must be 0..7");
+    if (impl > 8) fail(HE_EINVAL, "mac_impl must be 0..8");
     if (tune && tune->tc_cluster && tune->tc_cluster != 2 && tune->tc_cluster != 4 && tune->tc_cluster != 8)
         fail(HE_EINVAL, "tc_cluster must be 0, 2, 4 or 8");
     P->eager = impl == 3;
@@ -2914,12 +3144,14 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         const u32 form = (impl >= 4) ? impl : (words ? 4u : 5u);
         if (form == 6 && (!one_tile || (tune && tune->tc_cluster)))
             fail(HE_EINVAL, "the fused key switch + MAC needs a layer whose rows fit one CTA and no cluster");
-        if (form == 7 && ((tune && tune->tc_cluster) || tc_rows_req))
-            fail(HE_EINVAL, "the CTA-pair MAC takes no tc_rows and no tc_cluster");
+        if (form >= 7 && ((tune && tune->tc_cluster) || tc_rows_req))
+            fail(HE_EINVAL, "the CTA-pair and chunk-pass MACs take no tc_rows and no tc_cluster");
         P->img = form != 4;
         P->fused = form == 6;
         P->pair = form == 7;
+        P->cp = form == 8;
         if (P->pair) P->tc_rows_per_cta = TCP_ROWS;
+        if (P->cp) P->tc_rows_per_cta = std::min<u32>(TCC_ROWS, P->tc_rows);
         P->cl = 1;
         const u32 cl_req = tune ? tune->tc_cluster : 0;
         if (cl_req > 1) {
@@ -2927,7 +3159,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
             // tile are split into a multiple of cl_req tiles of at most 96 rows, none of them empty
             const u32 m = cl_req * ((P->tc_rows + TC_NMAX * cl_req - 1) / (TC_NMAX * cl_req));
             const u32 rpc = ((P->tc_rows + m - 1) / m + 15) / 16 * 16;
-            if (!P->img || P->fused || P->pair || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
+            if (!P->img || P->fused || P->pair || P->cp || tc_rows_req || P->tc_rows <= (m - 1) * rpc)
                 fail(HE_EINVAL, "tc_cluster needs the image-form tensor-core MAC, no tc_rows, and at least " +
                                     std::to_string(16 * (m - 1) + 16) + " output rows");
             P->cl = cl_req, P->tc_rows_per_cta = rpc;
@@ -3003,7 +3235,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     if (P->use_tc) {
         u32 cols = 32;
         while (cols < (u32)TC_CHUNKS * P->tc_rows_per_cta) cols <<= 1;
-        P->tmem_cols = P->pair ? 512 : cols;  // the pair form holds 5 x 64 columns
+        P->tmem_cols = (P->pair || P->cp) ? 512 : cols;  // the pair form holds 5 x 64 columns, chunk passes all 512
     }
     CUDA_OK(cudaStreamSynchronize(s));
     // workspace: R [n_ct_in][r_slots][2][L][N], D [n_ct_in][L l][L][N], O [n_ct_out][2][L][N] and, for
@@ -3165,7 +3397,8 @@ extern "C" int he_conv_time(const he_params* p, const he_conv_desc* d, const int
 extern "C" int he_conv_info(const he_plan* plan, int* mac_impl) {
     return guard([&] {
         if (!plan || !mac_impl) fail(HE_EINVAL, "null argument");
-        *mac_impl = plan->use_tc ? (plan->pair ? 7 : (plan->fused ? 6 : (plan->img ? 5 : 4))) : (plan->eager ? 3 : 1);
+        *mac_impl = plan->use_tc ? (plan->cp ? 8 : plan->pair ? 7 : (plan->fused ? 6 : (plan->img ? 5 : 4)))
+                                 : (plan->eager ? 3 : 1);
     });
 }
 

@@ -258,14 +258,14 @@ def test_repeat_on_side_stream_and_host_path(small):
 
 
 # ---------------------------------------------------------------- both MAC implementations
-@pytest.mark.parametrize("impl", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("impl", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("spec", [SMALL[0], SMALL[1], SMALL[4], SMALL[7], SMALL[11]])
 def test_mac_implementations(small, spec, impl):
     """1 lazy CUDA-core, 2 tensor-core in the automatic form, 3 eager (reduced after every CMult
     and HAdd, Sec. 3.2.2's conventional form), 4 tensor-core with in-kernel fp16 conversion, 5
     tensor-core fed with operand images written by the key switch, 6 key switch fused into the
-    tensor-core MAC, 7 operand images on CTA pairs (rows as the MMA's M): all give the oracle's
-    words."""
+    tensor-core MAC, 7 operand images on CTA pairs (rows as the MMA's M), 8 operand images in chunk
+    passes (up to 256 rows per CTA): all give the oracle's words."""
     small.layer(spec, mac_impl=impl)
 
 
@@ -307,7 +307,7 @@ def test_tensor_core_mac_at_the_exactness_bound(pairs):
     lay = H.he_layout_for_layer(S.p, d)
     zero = np.zeros((lay.n_ct_in, 2, 2, 1024), dtype=np.uint64)
     w = np.full((4, C_in, 3, 3), 8)
-    for impl in (2, 4, 5, 6, 7):
+    for impl in (2, 4, 5, 6, 7, 8):
         out_tc = gpu_layer(S.p, gk, d, w, zero, 2, 1024, mac_impl=impl)
         assert (out_tc == 0).all()
     # and on a real encryption, the tensor-core path equals the CUDA-core path word for word
@@ -320,19 +320,21 @@ def test_tensor_core_mac_at_the_exactness_bound(pairs):
     e = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=5)
     f = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=6)
     h = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=7)
+    i = gpu_layer(S.p, gk, d, w, cts, 2, 1024, mac_impl=8)
     assert (a == b).all() and (a == c).all() and (a == e).all() and (a == f).all() and (a == h).all()
+    assert (a == i).all()
     dec = H.he_decrypt_image(S.p, S.sk, d, b)
     assert (dec == conv.conv_plain(act, w, 1, 1, False, S.P.t)).all()
 
 
-@pytest.mark.parametrize("impl", [4, 5, 6, 7])
+@pytest.mark.parametrize("impl", [4, 5, 6, 7, 8])
 @pytest.mark.parametrize("C_in", [240, 512])
 def test_tensor_core_multi_segment_matches_oracle(small, C_in, impl):
     """Contractions longer than one exact fp32 accumulation: K = 2160 terms (two segments of at
     most 2048) and K = 4608 (three segments, the 512-channel layers of VGG-16), whose segment
     results add mod q in the output, in each tensor-core form (in-kernel conversion 4, operand
-    images 5, fused key switch 6, operand images on CTA pairs 7); every output ciphertext word for
-    word against the oracle."""
+    images 5, fused key switch 6, operand images on CTA pairs 7, chunk passes 8); every output
+    ciphertext word for word against the oracle."""
     spec = dict(C_in=C_in, C_out=6, H=4, W=4, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
     small.layer(spec, label=C_in, mac_impl=impl)
 
@@ -355,14 +357,24 @@ def test_cta_pair_mac_matches_oracle(small, C_out, c_n):
     small.layer(spec, label=C_out, mac_impl=7)
 
 
+@pytest.mark.parametrize("C_out,c_n", [(256, 2), (512, 2), (300, 2), (128, 1), (520, 1), (96, 2), (40, 2)])
+def test_chunk_pass_mac_matches_oracle(small, C_out, c_n):
+    """The operand-image MAC in chunk passes (mac_impl 8: up to 256 rows per CTA, floor(512 / rows)
+    chunks per pass): items of 256, ragged and fewer rows, two to five chunks per pass, packed and
+    unpacked; every output ciphertext word for word against the oracle."""
+    spec = dict(C_in=6, C_out=C_out, H=3, W=3, kh=3, stride=1, depthwise=False, n_images=1, c_n=c_n)
+    small.layer(spec, label=C_out + 1, mac_impl=8)
+
+
 def test_cta_pair_mac_takes_no_cluster_or_rows(small):
     spec = dict(C_in=6, C_out=16, H=3, W=3, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
     d = H.conv_desc(**spec)
     gk = H.he_galois_keys(small.p, small.sk, H.he_layer_galois(small.p, d), synth.SEED_KEYS)
-    for kw in ({"tc_cluster": 2}, {"tc_rows": 32}):
-        with pytest.raises(H.HyenaError) as e:
-            H.he_conv_plan(small.p, gk, d, synth.weights((16, 6, 3, 3)), mac_impl=7, **kw)
-        assert e.value.code == H.HE_EINVAL
+    for impl in (7, 8):
+        for kw in ({"tc_cluster": 2}, {"tc_rows": 32}):
+            with pytest.raises(H.HyenaError) as e:
+                H.he_conv_plan(small.p, gk, d, synth.weights((16, 6, 3, 3)), mac_impl=impl, **kw)
+            assert e.value.code == H.HE_EINVAL
     H.he_galkeys_destroy(gk)
 
 

@@ -226,7 +226,9 @@ def test_cluster_and_form_choices_are_checked_without_a_device():
     assert H.he_conv_check(p, narrow, wn, mac_impl=7) == H.HE_OK
     assert H.he_conv_check(p, wide, ww, mac_impl=7, tc_cluster=2) == H.HE_EINVAL
     assert H.he_conv_check(p, wide, ww, mac_impl=7, tc_rows=64) == H.HE_EINVAL
-    assert H.he_conv_check(p, wide, ww, mac_impl=8) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, mac_impl=8) == H.HE_OK
+    assert H.he_conv_check(p, wide, ww, mac_impl=8, tc_rows=64) == H.HE_EINVAL
+    assert H.he_conv_check(p, wide, ww, mac_impl=9) == H.HE_EINVAL
     H.he_params_destroy(p)
 
 

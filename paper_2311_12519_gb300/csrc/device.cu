@@ -38,6 +38,7 @@ struct LimbC {
     u64 q, mu;       // Barrett constant for x < 2^(s+63)
     u32 sm1, delta;  // s - 1; delta = 2^50 - q if that is below 2^22 (else 0)
     u64 ninv, ninv_sh;
+    u64 ksh;         // Shoup companion of the [k,-k] plaintext's k: floor(k 2^64 / q)
 };
 struct KP {
     u32 N, logN, L, l, w;
@@ -79,6 +80,29 @@ __device__ __forceinline__ u64 bred(u64 lo, u64 hi, const LimbC& m) {
 }
 __device__ __forceinline__ u64 bred128(u128 x, const LimbC& m) { return bred((u64)x, (u64)(x >> 64), m); }
 __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const LimbC& m) { return bred(a * b, __umul64hi(a, b), m); }
+// a w mod q for w < q with its Shoup companion wsh = floor(w 2^64 / q), any a < 2^64 (Shoup's
+// product: the quotient estimate mulhi(a, wsh) is exact or one short, so one subtraction remains)
+__device__ __forceinline__ u64 mulmod_shoup(u64 a, u64 w, u64 wsh, u64 q) {
+    const u64 r = a * w - __umul64hi(a, wsh) * q;
+    return r >= q ? r - q : r;
+}
+// A = hi 2^30 + lo mod q, the tensor-core MAC's recombined chunk sums (|lo| < 2^46, |hi| < 2^36).
+// For q = 2^50 - delta (delta < 2^22) the part of A above bit 50 folds down once: with hi = hh 2^20
+// + hl, A = hh 2^50 + hl 2^30 + lo = hh delta + hl 2^30 + lo (mod q), a sum S with |S| < 2^51; then
+// t = S + 4q lies in [0, 2^53) and t - floor(t / 2^50) q = floor(t / 2^50) delta + (t mod 2^50) is
+// below q + 6 delta, one conditional subtraction from [0, q).  Other limbs: 128-bit Barrett.
+__device__ __forceinline__ u64 tc_reduce(long long lo, long long hi, const LimbC& m) {
+    if (m.delta) {
+        const long long hh = hi >> 20;  // arithmetic: hi = hh 2^20 + hl, 0 <= hl < 2^20
+        const long long hl = hi & 0xFFFFF;
+        const long long S = hh * (long long)m.delta + (hl << 30) + lo;
+        const u64 t = (u64)(S + 4 * (long long)m.q);
+        const u64 r = t - (t >> 50) * m.q;
+        return r >= m.q ? r - m.q : r;
+    }
+    const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
+    return bred128((u128)a, m);
+}
 __device__ __forceinline__ u64 addq(u64 a, u64 b, u64 q) {
     u64 s = a + b;
     return s >= q ? s - q : s;
@@ -287,6 +311,7 @@ struct LayerDev {
     const RotDev* rots;        // rotations that need a key switch
     const int16_t* scal;       // CUDA-core MAC scalars [out_groups][c_n][K]
     const u64* pk;             // NTT(P_k) [L][N]
+    const u64* pksh;           // Shoup companions floor(NTT(P_k) 2^64 / q) [L][N]
     const __half* sc16;        // tensor-core MAC scalars, one shared-memory tile image per (row tile, K tile)
     const int* bias;           // tensor-core MAC row offsets 512 sum(s)
     int* err;                  // bounded-wait status
@@ -1012,7 +1037,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                 const u32 sp = warp & 3, third = (warp - 4) >> 2;
                 const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
                 const LimbC m = kp.limb[k];
-                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0, pksv = PACKED ? Ly.pksh[(size_t)k * N + x] : 0;
                 for (u32 cb = third * 8; cb < nrows; cb += 24) {
                     u32 d[TC_CHUNKS][8];
 #pragma unroll
@@ -1033,8 +1058,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                                              (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
                         const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
                                              (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
-                        const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
-                        red[j] = bred128((u128)a, m);
+                        red[j] = tc_reduce(lo, hi, m);
                     }
 #pragma unroll
                     for (int j = 0; j < 8; j += NR) {
@@ -1042,7 +1066,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_tc(const __grid_constant_
                         const u32 gg = row / NR;
                         if (gg >= Ly.out_groups) continue;
                         u64 out = red[j];
-                        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                        if (PACKED) out = addq(mulmod_shoup(out, kp.kmul, m.ksh, m.q), mulmod_shoup(red[j + 1], pkv, pksv, m.q), m.q);
                         u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
                         if (seg > 0) out = addq(out, *o, m.q);  // this thread stored the earlier segments
                         *o = out;
@@ -1500,7 +1524,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
                 const u32 sp = warp & 3, third = (warp - 4) >> 2;
                 const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
                 const LimbC m = kp.limb[k];
-                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+                const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0, pksv = PACKED ? Ly.pksh[(size_t)k * N + x] : 0;
                 for (u32 cb = third * 8; cb < nrows; cb += 24) {
                     u32 d[TC_CHUNKS][8];
 #pragma unroll
@@ -1521,8 +1545,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
                                              (((long long)__float2int_rn(__uint_as_float(d[2][j])) + b) << 20);
                         const long long hi = ((long long)__float2int_rn(__uint_as_float(d[3][j])) + b) +
                                              (((long long)__float2int_rn(__uint_as_float(d[4][j])) + b) << 10);
-                        const i128 a = (i128)lo + ((i128)hi << 30) + ((i128)m.q << 40);
-                        red[j] = bred128((u128)a, m);
+                        red[j] = tc_reduce(lo, hi, m);
                     }
 #pragma unroll
                     for (int j = 0; j < 8; j += NR) {
@@ -1530,7 +1553,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
                         const u32 gg = row / NR;
                         if (gg >= Ly.out_groups) continue;
                         u64 out = red[j];
-                        if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                        if (PACKED) out = addq(mulmod_shoup(out, kp.kmul, m.ksh, m.q), mulmod_shoup(red[j + 1], pkv, pksv, m.q), m.q);
                         u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
                         if (seg > 0) out = addq(out, *o, m.q);  // this thread stored the earlier segments
                         *o = out;
@@ -2472,6 +2495,7 @@ KP make_kp(const he_params* p) {
         kp.limb[k].delta = (p->q[k] < (1ull << 50) && d50 < (1ull << 22)) ? (u32)d50 : 0u;
         kp.limb[k].ninv = p->ntt[k].ninv;
         kp.limb[k].ninv_sh = p->ntt[k].ninv_sh;
+        kp.limb[k].ksh = (u64)((((unsigned __int128)(p->k % p->q[k])) << 64) / p->q[k]);
     }
     kp.tw = T.tw, kp.itw = T.itw;
     return kp;
@@ -2957,6 +2981,7 @@ struct he_plan {
     RotDev* d_rots_all = nullptr;
     int16_t* d_scal = nullptr;
     u64* d_pk = nullptr;
+    u64* d_pksh = nullptr;
     __half* d_sc16 = nullptr;
     int* d_bias = nullptr;
     int* d_err = nullptr;
@@ -2972,6 +2997,7 @@ struct he_plan {
         cudaFree(d_rots_all);
         cudaFree(d_scal);
         cudaFree(d_pk);
+        cudaFree(d_pksh);
         cudaFree(d_sc16);
         cudaFree(d_bias);
         cudaFree(d_err);
@@ -2986,7 +3012,7 @@ struct he_plan {
         L.R = (u64*)(ws + off_R), L.D = (u64*)(ws + off_D), L.O = (u64*)(ws + off_O);
         L.isrc = L.O;
         L.isrc_stride = 2ull * p->L * p->N;
-        L.ksk = d_ksk, L.rots = d_rots, L.scal = d_scal, L.pk = d_pk, L.sc16 = d_sc16, L.bias = d_bias, L.err = d_err;
+        L.ksk = d_ksk, L.rots = d_rots, L.scal = d_scal, L.pk = d_pk, L.pksh = d_pksh, L.sc16 = d_sc16, L.bias = d_bias, L.err = d_err;
         L.n_ct_in = lay.n_ct_in, L.n_ct_out = lay.n_ct_out, L.n_rot = n_rot, L.rot_id = rot_id, L.n_ks = n_ks;
         L.K = K, L.Kpad = tc_kpad, L.in_groups = lay.in_groups, L.out_groups = lay.out_groups;
         L.row_units = lay.row_units, L.tc_rows = tc_rows, L.tc_rows_per_cta = tc_rows_per_cta;
@@ -3197,6 +3223,13 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         }
         CUDA_OK(cudaMalloc(&P->d_pk, pk.size() * 8));
         CUDA_OK(cudaMemcpy(P->d_pk, pk.data(), pk.size() * 8, cudaMemcpyHostToDevice));
+        std::vector<u64> pksh(pk.size());
+        for (size_t i = 0; i < pk.size(); i++) {
+            const u64 q = p->q[i / p->N];
+            pksh[i] = (u64)((((unsigned __int128)pk[i]) << 64) / q);
+        }
+        CUDA_OK(cudaMalloc(&P->d_pksh, pksh.size() * 8));
+        CUDA_OK(cudaMemcpy(P->d_pksh, pksh.data(), pksh.size() * 8, cudaMemcpyHostToDevice));
     }
     CUDA_OK(cudaMalloc(&P->d_err, sizeof(int)));
     CUDA_OK(cudaMemset(P->d_err, 0, sizeof(int)));

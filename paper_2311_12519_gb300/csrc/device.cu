@@ -1130,11 +1130,15 @@ __host__ __device__ constexpr size_t ksi_smem_bytes(u32 LL) {
     return (size_t)2 * TC_CHUNKS * TC_MTILE * 16 + ((size_t)KSI_JB * LL + 4 * LL) * TC_MTILE * 8;
 }
 
-// rotation groups of the image key switch: as few as give about KSI_TARGET_BLOCKS blocks
+// rotation groups of the image key switch: as few as give about KSI_TARGET_BLOCKS blocks, each of
+// ceil(n_rot_all / groups) rotations, and none empty (9 rotations in 4 groups of 3 would leave the
+// fourth without a rotation: they become 3 groups)
 __host__ __device__ inline u32 ksi_groups(u32 row_units, u32 in_pad, u32 n_rot_all, u32 L, u32 N) {
     const u64 base = (u64)row_units * ((in_pad + KSI_JB - 1) / KSI_JB) * L * (N / TC_MTILE);
-    const u64 g = (KSI_TARGET_BLOCKS + base - 1) / base;
-    return (u32)(g < 1 ? 1 : (g > n_rot_all ? n_rot_all : g));
+    u64 g = (KSI_TARGET_BLOCKS + base - 1) / base;
+    g = g < 1 ? 1 : (g > n_rot_all ? n_rot_all : g);
+    const u64 per = (n_rot_all + g - 1) / g;
+    return (u32)((n_rot_all + per - 1) / per);
 }
 
 __device__ __forceinline__ uint2 chunk_pack4(const u64 (&v)[KSI_JH], int c) {
@@ -1221,7 +1225,7 @@ __global__ void __launch_bounds__(KSI_THREADS, LL <= 4 ? 3 : (LL <= 8 ? 2 : 1)) 
         cp_async_commit();
     };
     const int kind = m.sm1 == 49 ? (m.delta ? 1 : 2) : 3;
-    fetch_keys(r_begin, 0);
+    if (r_begin < r_end) fetch_keys(r_begin, 0);  // (ksi_groups leaves no group empty)
     cp_async_wait_all();
     __syncthreads();
 #pragma unroll 1

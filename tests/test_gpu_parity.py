@@ -366,6 +366,16 @@ def test_chunk_pass_mac_matches_oracle(small, C_out, c_n):
     small.layer(spec, label=C_out + 1, mac_impl=8)
 
 
+@pytest.mark.parametrize("c_n", [1, 2])
+def test_image_key_switch_rotation_groups(small, c_n):
+    """A small image-form layer whose key switch splits its rotations into groups to fill the GPU:
+    136 input channels at N = 1024 ask for 4 groups of 9 rotations (unpacked) or 8 of 18 (packed),
+    which as groups of ceil(9 / 4) = 3 and ceil(18 / 8) = 3 rotations need only 3 and 6; every
+    rotation is keyed once and every output ciphertext equals the oracle's."""
+    spec = dict(C_in=136, C_out=8, H=3, W=3, kh=3, stride=1, depthwise=False, n_images=1, c_n=c_n)
+    small.layer(spec, label=136 + c_n, mac_impl=5)
+
+
 def test_cta_pair_mac_takes_no_cluster_or_rows(small):
     spec = dict(C_in=6, C_out=16, H=3, W=3, kh=3, stride=1, depthwise=False, n_images=1, c_n=2)
     d = H.conv_desc(**spec)

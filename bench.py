@@ -418,13 +418,16 @@ def run_gpu(args, rank, world):
     info = H.he_params_info(p)
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
-    tunes = [({"mac_impl": args.mac_impl} if args.mac_impl else {}) for _ in specs]
-    if args.tc_cluster:
-        # clusters where the layer is wide enough to take them (more than one row tile per CTA pair)
+    tunes = [{} for _ in specs]
+    if args.mac_impl or args.tc_cluster:
+        # a forced MAC form or cluster size where the layer admits it (depthwise layers take no
+        # tensor-core form; clusters need more than one row tile per CTA); the automatic form elsewhere
         p0 = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=50)
         for i, s in enumerate(specs):
-            if H.he_conv_check(p0, H.conv_desc(**s), synth.stack_inputs(wl, index[i], H.he_params_info(p0).t)[1],
-                               tc_cluster=args.tc_cluster) == H.HE_OK:
+            d0, w0 = H.conv_desc(**s), synth.stack_inputs(wl, index[i], H.he_params_info(p0).t)[1]
+            if args.mac_impl and H.he_conv_check(p0, d0, w0, mac_impl=args.mac_impl) == H.HE_OK:
+                tunes[i]["mac_impl"] = args.mac_impl
+            if args.tc_cluster and H.he_conv_check(p0, d0, w0, tc_cluster=args.tc_cluster, **tunes[i]) == H.HE_OK:
                 tunes[i]["tc_cluster"] = args.tc_cluster
         H.he_params_destroy(p0)
     tuned = None
@@ -893,7 +896,7 @@ def main():
     ap.add_argument("--tc-cluster", type=int, default=0,
                     help="run the image-form MAC of layers wider than one row tile in clusters of this many CTAs")
     ap.add_argument("--mac-impl", type=int, default=0,
-                    help="force every layer's MAC form (he_tune.mac_impl; 0 = automatic per layer)")
+                    help="force the MAC form of every layer that admits it (he_tune.mac_impl; 0 = automatic per layer)")
     ap.add_argument("--layers", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     help="run only these layer indices of the stack (comma list), e.g. for profiler captures")
     ap.add_argument("--tuned", action="store_true",

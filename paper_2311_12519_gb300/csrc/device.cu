@@ -1741,7 +1741,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_cp(const __grid_constant_
             const u32 sp = warp & 3, third = (warp - 4) >> 2;
             const u32 nl = sp * 32 + lane, x = it.n0 + nl, nrows = it.nrows, row0 = it.row0, k = it.k, p = it.p;
             const LimbC m = kp.limb[k];
-            const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+            const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0, pksv = PACKED ? Ly.pksh[(size_t)k * N + x] : 0;
             for (u32 c0 = 0; okk && c0 < (u32)TC_CHUNKS; c0 += cpp) {
                 const u32 ncp = min(cpp, (u32)TC_CHUNKS - c0);
                 for (u32 seg = 0; seg < n_seg; seg++) {
@@ -1765,13 +1765,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_cp(const __grid_constant_
 #pragma unroll
                         for (int j = 0; j < 8; j++) {
                             const long long b = Ly.bias[(size_t)seg * Ly.tc_rows + row0 + cb + j];  // 512 S of the segment
-                            i128 a = (i128)m.q << 40;  // keeps the sum positive; a multiple of q
+                            // this pass's chunks of A = hi 2^30 + lo (chunks 0..2 in lo, 3..4 in hi)
+                            long long lo = 0, hi = 0;
 #pragma unroll
                             for (int c = 0; c < TC_CHUNKS; c++) {
                                 if ((u32)c >= ncp) break;
-                                a += (i128)((long long)__float2int_rn(__uint_as_float(d[c][j])) + b) << (10 * (c0 + c));
+                                const long long v = (long long)__float2int_rn(__uint_as_float(d[c][j])) + b;
+                                const u32 e = c0 + c;
+                                if (e < 3) lo += v << (10 * e);
+                                else hi += v << (10 * (e - 3));
                             }
-                            red[j] = bred128((u128)a, m);
+                            red[j] = tc_reduce(lo, hi, m);
                         }
 #pragma unroll
                         for (int j = 0; j < 8; j += NR) {
@@ -1779,7 +1783,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_cp(const __grid_constant_
                             const u32 gg = row / NR;
                             if (gg >= Ly.out_groups) continue;
                             u64 out = red[j];
-                            if (PACKED) out = addq(mulmod(kp.kmul, out, m), mulmod(red[j + 1], pkv, m), m.q);
+                            if (PACKED) out = addq(mulmod_shoup(out, kp.kmul, m.ksh, m.q), mulmod_shoup(red[j + 1], pkv, pksv, m.q), m.q);
                             u64* o = Ly.O + ((size_t)(it.ru * Ly.out_groups + gg) * 2 + p) * L * N + (size_t)k * N + x;
                             if (!first) out = addq(out, *o, m.q);  // this thread stored the earlier accumulations
                             *o = out;

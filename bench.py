@@ -54,7 +54,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "network_samples.json")
 # DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source with this digest prefix
 # (kernel_source_digest), per workload; reported as roofline traffic only while the kernels are unchanged
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    # profiles/vgg16_stack_batched_launches.md: the key-switch stage's 4 launches of one forward
+    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("6868a6de5f58fb2a", 41435856320),
+}
 
 
 def kernel_source_digest():

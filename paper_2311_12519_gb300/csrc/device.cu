@@ -845,6 +845,37 @@ __device__ __forceinline__ bool tc_item(const Batch<MAXB>& B, u32 item, u32 N, u
     return true;
 }
 
+// The work items of one CTA (or cluster) of the operand-image MAC, in order.  With clusters the items
+// of the launch go round-robin over the clusters.  Without, the items of each layer run in rounds of
+// G = floor(n_cl / R) R CTAs, R the layer's row tiles: the R row tiles of a slot tile (consecutive
+// items) then always run in the same round, on CTAs that ran one slot tile's tiles together in the
+// round before, so they stream the same images at about the same time and the later readers find
+// them in L2 (with G = n_cl a team would straddle rounds whenever R does not divide n_cl, and its
+// members would read the images an item apart, from DRAM).
+struct TcWalk {
+    u32 li, local, item;
+};
+template <int MAXB>
+__device__ __forceinline__ bool tc_walk(const Batch<MAXB>& B, u32 cid, u32 n_cl, u32 N, u32 L, TcWalk& w, bool first,
+                                        TcItem& it, u32 rank, u32 CL) {
+    if (CL > 1) {
+        w.item = first ? cid : w.item + n_cl;
+        return tc_item(B, w.item, N, L, it, rank, CL);
+    }
+    auto rounds = [&](u32 li) {
+        const LayerDev& Ly = B.L[li];
+        const u32 R = max(1u, (Ly.tc_rows + Ly.tc_rows_per_cta - 1) / Ly.tc_rows_per_cta);
+        return n_cl >= R ? n_cl / R * R : n_cl;
+    };
+    if (first) w.li = 0, w.local = cid;
+    else w.local += rounds(w.li);
+    for (; w.li < B.n; w.li++, w.local = cid) {
+        if (cid < rounds(w.li) && w.local < B.start[ST_MAC][w.li + 1] - B.start[ST_MAC][w.li])
+            return tc_item(B, B.start[ST_MAC][w.li] + w.local, N, L, it, 0, 1);
+    }
+    return false;
+}
+
 // Warp roles: warp 0 issues the copies, warp 1 (lane 0) issues the MMAs, warps 2..15 convert
 // residues to fp16 chunks, warps 4..15 also run the epilogue.  Barriers (all bounded waits):
 //   raw_full[s]   copies of stream position g landed in slot s = g % TC_RAW   (1 arrive + tx)
@@ -1420,7 +1451,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         u32 g = 0;
         TcItem it;
         bool ok = true;
-        for (u32 item = cid; ok && tc_item(B, item, N, L, it, rank, CL); item += n_cl) {
+        TcWalk wk;
+        for (bool f = true; ok && tc_walk(B, cid, n_cl, N, L, wk, f, it, rank, CL); f = false) {
             const LayerDev& Ly = *it.ly;
             const u32 bbytes = Ly.tc_rows_per_cta * TC_KTILE * 2, ktiles = Ly.Kpad / TC_KTILE;
             const u32 mt = it.row0 / Ly.tc_rows_per_cta, nt = it.n0 / TC_MTILE;
@@ -1470,7 +1502,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         if (lane == 0) {
             u32 g = 0, unit = 0;  // unit = (item, segment): one accumulation in TMEM
             TcItem it;
-            for (u32 item = cid; tc_item(B, item, N, L, it, rank, CL); item += n_cl) {
+            TcWalk wk;
+            for (bool f = true; tc_walk(B, cid, n_cl, N, L, wk, f, it, rank, CL); f = false) {
                 const u32 idesc = tc_idesc(TC_MTILE, it.nrows);
                 bool okk = true;
                 for (u32 t = 0; t < it.n_tiles; t++, g++) {
@@ -1517,7 +1550,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mac_img(const __grid_constant
         // ---------------------------------------------------------------- epilogue
         u32 unit = 0;
         TcItem it;
-        for (u32 item = cid; tc_item(B, item, N, L, it, rank, CL); item += n_cl) {
+        TcWalk wk;
+        for (bool f = true; tc_walk(B, cid, n_cl, N, L, wk, f, it, rank, CL); f = false) {
             const LayerDev& Ly = *it.ly;
             const u32 n_seg = (it.n_tiles + TC_SEG_TILES - 1) / TC_SEG_TILES;
             bool okk = true;

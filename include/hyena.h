@@ -326,7 +326,9 @@ int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* co
  * A batch of several waves runs its waves in order on `stream`, while the
  * inputs stream in ahead of them and a finished wave's outputs stream out
  * during the next wave, on two more streams the batch owns.  Outputs equal
- * he_batch_forward's. */
+ * he_batch_forward's.  Host buffers: on a GB300 with many separately pinned
+ * multi-GB buffers live at once, host-to-device copies from them ran at about
+ * a quarter of the rate of buffers that are views of one pinned allocation. */
 int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, uint64_t* const* h_out, uint64_t* const* d_in,
                           uint64_t* const* d_out, void* d_workspace, void* stream);
 void he_batch_destroy(he_batch* b);

@@ -56,7 +56,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "network_samples.json")
 # (kernel_source_digest), per workload; reported as roofline traffic only while the kernels are unchanged
 PROFILED_TRAFFIC = {
     # profiles/vgg16_stack_batched_launches.md: the key-switch stage's 4 launches of one forward
-    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("30dc1282ada69593", 41440975680),
+    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("3323b86852c31128", 41500227104),
 }
 
 

@@ -302,7 +302,7 @@ struct LayerDev {
     CUtensorMap smap;          // CTA-pair MAC: the scalar tiles
     const u64* in;             // input ciphertexts [n_ct_in][2][L][N]
     u64* R;                    // rotated copies [n_ct_in][n_rot][2][L][N], NTT form
-    u64* D;                    // digit NTTs [n_ct_in][L l][L][N]
+    u64* D;                    // digit NTTs [n_ct_in][L l][L][N], each word split at bit 25 (low bits | rest << 32)
     u64* O;                    // NTT-form outputs [n_ct_out][2][L][N]
     u64* out;                  // output ciphertexts [n_ct_out][2][L][N]
     const u64* isrc;           // inverse-NTT source (O, or a rotated copy for he_rotate)
@@ -370,11 +370,13 @@ __global__ void __launch_bounds__(NTHR, MINB) k_ntt_inputs(const __grid_constant
     u64* dst2 = nullptr;
     u32 limb, shift = 0;
     u64 mask = ~0ull;
+    bool split = false;  // digit transforms are stored split at bit 25 (see k_keyswitch)
     if (y < L + c1_jobs) {
         limb = y % L;
         src = Ly.in + c * ctw + (size_t)y * N;
         dst = Rid + (size_t)y * N;
     } else {
+        split = true;
         const u32 z = y - L - c1_jobs, dd = z / L;
         limb = z % L;
         src = Ly.in + c * ctw + (size_t)(L + dd / l) * N;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_ntt_inputs(const __grid_constant
         sm, N, kp.logN, kp.tw + 2 * (size_t)limb * N, m.q,
         [&](u32 i) { return shift >= 64 ? 0ull : (__ldg(src + i) >> shift) & mask; },
         [&](u32 i, u64 v) {
-            dst[i] = v;
+            dst[i] = split ? (v & 0x1FFFFFFull) | ((v >> 25) << 32) : v;
             if (dst2) dst2[i] = v;
         });
 }
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
 #pragma unroll
             for (int dd = 0; dd < LL; dd++) {
                 const u64 dv = __ldg(Dc + (size_t)dd * L * N);
-                const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
+                const u32 dl = (u32)dv, dh = (u32)(dv >> 32), ds = dl + dh;  // stored split at bit 25
                 mad_wide_u(lo0, dl, k0l[dd]);
                 mad_wide_u(hi0, dh, k0h[dd]);
                 mad_wide_u(mid0, ds, k0s[dd]);
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
 #pragma unroll
         for (int dd = 0; dd < LL; dd++) {
             const u64 dv = __ldg(Dc + (size_t)dd * L * N);
-            const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+            const u32 dl = (u32)dv, dh = (u32)(dv >> 32);  // stored split at bit 25
             mad_wide_u(lo0, dl, k0l[dd]);
             mad_wide_u(mid0, dl, k0h[dd]);
             mad_wide_u(mid0, dh, k0l[dd]);
@@ -1298,7 +1300,7 @@ __global__ void __launch_bounds__(KSI_THREADS, LL <= 4 ? 3 : (LL <= 8 ? 2 : 1)) 
 #pragma unroll
                     for (int dd = 0; dd < LL; dd++) {
                         const u64 dv = Dc[dd * TC_MTILE];
-                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25), ds = dl + dh;
+                        const u32 dl = (u32)dv, dh = (u32)(dv >> 32), ds = dl + dh;  // stored split at bit 25
                         mad_wide_u(lo0, dl, k0l[dd]);
                         mad_wide_u(hi0, dh, k0h[dd]);
                         mad_wide_u(mid0, ds, k0s[dd]);
@@ -1327,7 +1329,7 @@ __global__ void __launch_bounds__(KSI_THREADS, LL <= 4 ? 3 : (LL <= 8 ? 2 : 1)) 
 #pragma unroll
                     for (int dd = 0; dd < LL; dd++) {
                         const u64 dv = Dc[dd * TC_MTILE];
-                        const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                        const u32 dl = (u32)dv, dh = (u32)(dv >> 32);  // stored split at bit 25
                         mad_wide_u(lo0, dl, k0l[dd]);
                         mad_wide_u(mid0, dl, k0h[dd]);
                         mad_wide_u(mid0, dh, k0l[dd]);
@@ -2353,7 +2355,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) k_ksmac(const __grid_constant__
 #pragma unroll
                             for (int dd = 0; dd < LL; dd++) {
                                 const u64 dv = __ldg(Dc + dd * dd_step);
-                                const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                                const u32 dl = (u32)dv, dh = (u32)(dv >> 32);  // stored split at bit 25
                                 mad_wide_u(lo, dl, kl_[dd]);
                                 mad_wide_u(hi, dh, kh_[dd]);
                                 mad_wide_u(mid, dl + dh, kl_[dd] + kh_[dd]);
@@ -2372,7 +2374,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) k_ksmac(const __grid_constant__
 #pragma unroll
                             for (int dd = 0; dd < LL; dd++) {
                                 const u64 dv = __ldg(Dc + dd * dd_step);
-                                const u32 dl = (u32)(dv & 0x1FFFFFFu), dh = (u32)(dv >> 25);
+                                const u32 dl = (u32)dv, dh = (u32)(dv >> 32);  // stored split at bit 25
                                 mad_wide_u(lo, dl, kl_[dd]);
                                 mad_wide_u(mid, dl, kh_[dd]);
                                 mad_wide_u(mid, dh, kl_[dd]);

@@ -11,8 +11,20 @@ Readings of the paper:
     W_b = T_w + 2P.  Tap (dy, dx) is then a left rotation by dy*W_b + dx.
     With c_n = 2, row 0 of input ciphertext j carries channel 2j and row 1
     channel 2j+1; with c_n = 1 both rows carry channel j for different tiles.
+  * c_n = 4 (Sec. 3.1 generalises the pair to the 4 x 4 Walsh-Hadamard
+    basis without fixing which slots form the four parts): channel 4j + c
+    of input ciphertext j sits in row c >> 1 at the slots of parity c & 1,
+    so a block position pos is slot 2 pos + (c & 1) of its row and a row
+    holds N/4 positions.  The four +-1 patterns of H_4 over these classes
+    (row sign, slot parity and their product) encode to sparse plaintexts,
+    where contiguous quarter rows would give dense ones.  A left rotation
+    by 2o keeps each class and shifts by o positions; one by 2m + 1 moves
+    parity 1 at offset m into parity 0 and parity 0 at offset m + 1 into
+    parity 1.
   * Hadamard scalars (Eq. 1) are used without the 1/2: s0 = v0 + v1,
     s1 = v0 - v1, so the output decrypts to 2k * conv (k from Sec. 3.2.1).
+    With c_n = 4, s_b = sum_c H4[b][c] v_c and the output decrypts to
+    4 k4 * conv, k4 chosen for the three patterns together (k4_select).
   * Output-channel alignment (Sec. 3.1 rotates partial sums) is applied on
     the input side: the row swap is composed with every tap rotation
     (diagonal d = 1), which gives the same slots.
@@ -78,6 +90,8 @@ class Layout:
             raise ValueError("odd square kernels only")
         if self.depthwise and self.C_in != self.C_out:
             raise ValueError("depthwise needs C_in == C_out")
+        if self.c_n not in (1, 2, 4):
+            raise ValueError("c_n must be 1, 2 or 4")
         self.P = (self.kh - 1) // 2
         if self.tile_h or self.tile_w:
             # a caller-chosen tile: any size whose padded block fits one slot row, with tile
@@ -87,13 +101,18 @@ class Layout:
                 raise ValueError("tile must lie within the image, in both directions")
             if (th % S and th != self.H) or (tw % S and tw != self.W):
                 raise ValueError("tile sides must be multiples of the stride")
-            if (th + 2 * self.P) * (tw + 2 * self.P) > self.N // 2:
+            if (th + 2 * self.P) * (tw + 2 * self.P) > self.row_positions:
                 raise ValueError("padded tile does not fit one slot row")
             self.T_h, self.T_w = th, tw
         else:
-            self.T_h, self.T_w = choose_tile(self.N // 2, self.H, self.W, self.P, self.stride)
+            self.T_h, self.T_w = choose_tile(self.row_positions, self.H, self.W, self.P, self.stride)
 
     # geometry -------------------------------------------------------------
+    @property
+    def row_positions(self):
+        """block positions a slot row holds: N/2, or N/4 with c_n = 4 (two parities per position)"""
+        return self.N // 4 if self.c_n == 4 else self.N // 2
+
     @property
     def W_b(self):
         return self.T_w + 2 * self.P
@@ -104,7 +123,7 @@ class Layout:
 
     @property
     def blocks_per_row(self):
-        return (self.N // 2) // self.block_slots
+        return self.row_positions // self.block_slots
 
     @property
     def n_ty(self):
@@ -157,11 +176,21 @@ class Layout:
 
     # slot placement -------------------------------------------------------
     def slot_of(self, u_local: int, yl: int, xl: int) -> tuple[int, int]:
-        """(row, slot index within the row) of block-local position (yl, xl)
+        """(row, position within the row) of block-local position (yl, xl)
         of the u_local-th tile held by a ciphertext."""
         B = self.blocks_per_row
-        row, b = (0, u_local) if self.c_n == 2 else (u_local // B, u_local % B)
+        row, b = (u_local // B, u_local % B) if self.c_n == 1 else (0, u_local)
         return row, b * self.block_slots + yl * self.W_b + xl
+
+    def flat_slot(self, row: int, pos: int, r: int) -> int:
+        """Flat slot index of channel r (0 .. c_n - 1) of a ciphertext at (row, pos) from slot_of:
+        c_n = 1 uses the row; c_n = 2 puts channel r in row r; c_n = 4 in row r >> 1 at parity r & 1."""
+        half = self.N // 2
+        if self.c_n == 1:
+            return row * half + pos
+        if self.c_n == 2:
+            return r * half + pos
+        return (r >> 1) * half + 2 * pos + (r & 1)
 
     def unit_coords(self, unit: int) -> tuple[int, int, int]:
         img, rest = divmod(unit, self.n_ty * self.n_tx)
@@ -170,7 +199,7 @@ class Layout:
 
 
 def choose_tile(half: int, H: int, W: int, P: int, S: int) -> tuple[int, int]:
-    """Interior tile size (T_h, T_w) whose padded block fits one slot row.
+    """Interior tile size (T_h, T_w) whose padded block fits one slot row of `half` positions.
     Whole image if it fits; else full-width strips of a multiple of S rows;
     else square-ish tiles with sides a multiple of S."""
     if (H + 2 * P) * (W + 2 * P) <= half:
@@ -190,7 +219,7 @@ def choose_tile(half: int, H: int, W: int, P: int, S: int) -> tuple[int, int]:
 def pack_slots(lay: Layout, act: np.ndarray, row_units=None) -> np.ndarray:
     """Input activations [I][C_in][H][W] -> slot vectors [n_ct_in][N].
     `row_units` (optional) fills only the ciphertexts of those row-units."""
-    N, half, P = lay.N, lay.N // 2, lay.P
+    N, P = lay.N, lay.P
     out = np.zeros((lay.n_ct_in, N), dtype=np.int64)
     for unit in range(lay.units):
         ru, u_local = divmod(unit, lay.units_per_ct)
@@ -208,19 +237,16 @@ def pack_slots(lay: Layout, act: np.ndarray, row_units=None) -> np.ndarray:
                     if X < 0 or X >= lay.W:
                         continue
                     row, pos = lay.slot_of(u_local, yl, xl)
-                    if lay.c_n == 2:
-                        for r in range(2):
-                            c = 2 * j + r
-                            if c < lay.C_in:
-                                out[ct, r * half + pos] = act[img, c, Y, X]
-                    else:
-                        out[ct, row * half + pos] = act[img, j, Y, X]
+                    for r in range(lay.c_n):
+                        c = lay.c_n * j + r
+                        if c < lay.C_in:
+                            out[ct, lay.flat_slot(row, pos, r)] = act[img, c, Y, X]
     return out
 
 
 def unpack_slots(lay: Layout, slots: np.ndarray) -> np.ndarray:
     """Output slot vectors [n_ct_out][N] -> [I][C_out][Ho][Wo] (valid positions only)."""
-    half, P, S = lay.N // 2, lay.P, lay.stride
+    P, S = lay.P, lay.stride
     out = np.zeros((lay.n_images, lay.C_out, lay.Ho, lay.Wo), dtype=np.int64)
     for unit in range(lay.units):
         ru, u_local = divmod(unit, lay.units_per_ct)
@@ -236,20 +262,17 @@ def unpack_slots(lay: Layout, slots: np.ndarray) -> np.ndarray:
                     if X >= lay.W or X % S:
                         continue
                     row, pos = lay.slot_of(u_local, yl, xl)
-                    if lay.c_n == 2:
-                        for r in range(2):
-                            c = 2 * g + r
-                            if c < lay.C_out:
-                                out[img, c, Y // S, X // S] = slots[ct, r * half + pos]
-                    else:
-                        out[img, g, Y // S, X // S] = slots[ct, row * half + pos]
+                    for r in range(lay.c_n):
+                        c = lay.c_n * g + r
+                        if c < lay.C_out:
+                            out[img, c, Y // S, X // S] = slots[ct, lay.flat_slot(row, pos, r)]
     return out
 
 
 def ct_positions(lay: Layout, c: int) -> list[tuple[int, int, int, int, int]]:
     """Valid outputs carried by output ciphertext c: (image, channel, y, x, flat slot) tuples,
     the same placement as unpack_slots, for checking one ciphertext of a large layer."""
-    half, P, S = lay.N // 2, lay.P, lay.stride
+    P, S = lay.P, lay.stride
     ru, g = divmod(c, lay.out_groups)
     res = []
     for u_local in range(lay.units_per_ct):
@@ -266,12 +289,9 @@ def ct_positions(lay: Layout, c: int) -> list[tuple[int, int, int, int, int]]:
                 if X >= lay.W or X % S:
                     continue
                 row, pos = lay.slot_of(u_local, yl, xl)
-                if lay.c_n == 2:
-                    for r in range(2):
-                        if 2 * g + r < lay.C_out:
-                            res.append((img, 2 * g + r, Y // S, X // S, r * half + pos))
-                else:
-                    res.append((img, g, Y // S, X // S, row * half + pos))
+                for r in range(lay.c_n):
+                    if lay.c_n * g + r < lay.C_out:
+                        res.append((img, lay.c_n * g + r, Y // S, X // S, lay.flat_slot(row, pos, r)))
     return res
 
 
@@ -329,6 +349,8 @@ def polyphase_spec(spec: dict) -> dict:
     if spec["stride"] != 2 or spec["kh"] != 3:
         raise ValueError("polyphase packing is for 3x3 stride-2 layers")
     c_n = spec["c_n"]
+    if c_n not in (1, 2):
+        raise ValueError("polyphase packing is built for c_n 1 and 2")
     Cp = -(-spec["C_in"] // c_n) * c_n
     d = dict(spec, C_in=4 * Cp, H=-(-spec["H"] // 2), W=-(-spec["W"] // 2), stride=1, depthwise=False)
     d.pop("polyphase", None)
@@ -336,11 +358,30 @@ def polyphase_spec(spec: dict) -> dict:
 
 
 # ---------------------------------------------------------------- keys used
+def rotation_steps4(lay: Layout) -> list[int]:
+    """Left-rotation steps of a c_n = 4 layer, ascending: 2o for every tap offset o = dy W_b + dx
+    and, unless the layer is depthwise (an output class then reads only its own class), the
+    parity-changing steps 2o - 1 and 2o + 1."""
+    offs = [dy * lay.W_b + dx for dy, dx in lay.taps()]
+    steps = {2 * o for o in offs}
+    if not lay.depthwise:
+        steps |= {2 * o + e for o in offs for e in (-1, 1)}
+    return sorted(steps)
+
+
 def rotation_plan(P: Params, lay: Layout):
-    """List of (tap index, d, Galois element) for every rotated copy of an
-    input ciphertext; Galois element 1 is the identity (no key switch)."""
+    """List of (key, d, Galois element) for every rotated copy of an input ciphertext; Galois
+    element 1 is the identity (no key switch).  key is the tap index for c_n = 1, 2 and the
+    rotation step (rotation_steps4) for c_n = 4; d = 1 composes the row swap."""
     rows = []
-    diag = (0, 1) if (lay.c_n == 2 and not lay.depthwise) else (0,)
+    diag = (0, 1) if (lay.c_n in (2, 4) and not lay.depthwise) else (0,)
+    if lay.c_n == 4:
+        for step in rotation_steps4(lay):
+            g_step = bfv.rotation_element(P, step)
+            for d in diag:
+                g = g_step if d == 0 else (g_step * bfv.row_swap_element(P)) % (2 * P.N)
+                rows.append((step, d, g))
+        return rows
     for ti, (dy, dx) in enumerate(lay.taps()):
         g_tap = bfv.rotation_element(P, dy * lay.W_b + dx)
         for d in diag:
@@ -375,8 +416,84 @@ def hadamard_scalars(lay: Layout, weights: np.ndarray, g: int, j: int, ti: int, 
     return v0 + v1, v0 - v1
 
 
+# the 4 x 4 Walsh-Hadamard basis of Sec. 3.1, row b over the slot classes c = 0..3
+H4 = ((1, 1, 1, 1), (1, -1, 1, -1), (1, 1, -1, -1), (1, -1, -1, 1))
+# search range of k4: [1, min(t - 1, K4_MAX)]
+K4_MAX = 1 << 20
+
+
+def hadamard4_scalars(lay: Layout, weights: np.ndarray, g: int, j: int, step: int, d: int) -> list[int]:
+    """(s_0, .., s_3) = H4 v for output group g, input group j and the rotated copy (step, d)
+    of a c_n = 4 layer, v_c the weight the copy carries into output class c (Sec. 3.1 with the
+    4 x 4 basis, without the 1/4).  Output class c = 2 r + e sits in row r at parity e; the copy
+    brings the input of row r ^ d, parity e' = (e + step) mod 2, from offset o = (e + step - e') / 2
+    positions away, which is tap (dy, dx) if dy W_b + dx = o with |dy|, |dx| <= P and no tap
+    otherwise (unique because W_b > 2P)."""
+    taps = {dy * lay.W_b + dx: (dy, dx) for dy, dx in lay.taps()}
+    v = [0, 0, 0, 0]
+    for c in range(4):
+        e = c & 1
+        e_src = (e + step) & 1
+        tap = taps.get((e + step - e_src) // 2)
+        if tap is None:
+            continue
+        o, i = 4 * g + c, 4 * j + 2 * ((c >> 1) ^ d) + e_src
+        if o >= lay.C_out or i >= lay.C_in:
+            continue
+        dy, dx = tap[0] + lay.P, tap[1] + lay.P
+        if lay.depthwise:
+            v[c] = int(weights[o, 0, dy, dx]) if o == i else 0
+        else:
+            v[c] = int(weights[o, i, dy, dx])
+    return [sum(H4[b][c] * v[c] for c in range(4)) for b in range(4)]
+
+
+def hadamard4_patterns(P: Params) -> list[np.ndarray]:
+    """Centred coefficients of the plaintexts whose slot of class c (row r, index i: c = 2r +
+    (i mod 2)) holds H4[b][c], for b = 1, 2, 3 (slot parity, row, their product)."""
+    half = P.N // 2
+    cls = np.array([2 * r + (i & 1) for r in range(2) for i in range(half)])
+    out = []
+    for b in (1, 2, 3):
+        m = bfv.encode(P, np.array(H4[b], dtype=np.int64)[cls]).astype(np.int64)
+        out.append(np.where(m > P.t // 2, m - P.t, m))
+    return out
+
+
+_K4_CACHE: dict = {}
+
+
+def k4_select(P: Params) -> int:
+    """The k of c_n = 4 (reading of Sec. 3.2.1 for three PMult plaintexts): the k in
+    [1, min(t - 1, K4_MAX)] minimising k + sum of |[k a]_t| over the non-zero coefficients a of
+    the three patterns (the bound on the noise growth of CMult by k plus the three PMults by the
+    k-scaled patterns); ties go to the smallest k."""
+    key = (P.N, P.t, P.zeta)
+    if key not in _K4_CACHE:
+        coeffs = [int(a) % P.t for pat in hadamard4_patterns(P) for a in pat if a]
+        ks = np.arange(1, min(P.t - 1, K4_MAX) + 1, dtype=np.int64)
+        G = ks.copy()
+        for a in coeffs:
+            v = (ks * a) % P.t
+            G += np.minimum(v, P.t - v)
+        _K4_CACHE[key] = int(ks[int(np.argmin(G))])
+    return _K4_CACHE[key]
+
+
+def hadamard4_plaintexts(P: Params) -> tuple[int, list[np.ndarray]]:
+    """(k4, [k4 x pattern b, centred, for b = 1, 2, 3])."""
+    k4 = k4_select(P)
+    out = []
+    for pat in hadamard4_patterns(P):
+        m = (pat * k4) % P.t
+        out.append(np.where(m > P.t // 2, m - P.t, m))
+    return k4, out
+
+
 def output_scale(P: Params, lay: Layout) -> int:
-    """The factor the layer's output carries: 2k with packing, 1 without."""
+    """The factor the layer's output carries: 2k with pair packing, 4 k4 with c_n = 4, 1 without."""
+    if lay.c_n == 4:
+        return (4 * k4_select(P)) % P.t
     return (2 * P.k) % P.t if lay.c_n == 2 else 1
 
 
@@ -413,7 +530,7 @@ def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk
         raise ValueError(f"output ciphertext index out of range [0, {n_out})")
     need_ru = sorted({c // lay.out_groups for c in todo})
     out = np.zeros((n_out, 2, P.L, P.N), dtype=np.uint64)
-    pk = bfv.hadamard_plaintext(P) if lay.c_n == 2 else None
+    pk = bfv.hadamard_plaintext(P) if lay.c_n == 2 else (hadamard4_plaintexts(P) if lay.c_n == 4 else None)
     pool = ThreadPoolExecutor(max_workers=threads or oracle_threads())
 
     def rotations_of(ru: int, j: int) -> dict:
@@ -447,7 +564,21 @@ def he_conv(P: Params, lay: Layout, weights: np.ndarray, cts_in: np.ndarray, ksk
 def _output_ct(P: Params, lay: Layout, weights: np.ndarray, plan, rot: dict, pk, c: int) -> np.ndarray:
     """Output ciphertext c of the layer from the rotated copies of its row-unit's inputs."""
     g_out = c % lay.out_groups
-    if lay.c_n == 2:
+    if lay.c_n == 4:
+        # four sums A_b = sum s_b x, then out = k4 A_0 + sum_b PMult(A_b, k4 pattern_b)
+        A = np.zeros((4, 2, P.L, P.N), dtype=np.uint64)
+        js = [g_out] if lay.depthwise else range(lay.in_groups)
+        for j in js:
+            for step, d, _ in plan:
+                sv = hadamard4_scalars(lay, weights, g_out, j, step, d)
+                for b in range(4):
+                    if sv[b]:
+                        bfv.cmult_add(P, A[b], rot[(j, step, d)], sv[b])
+        k4, pks = pk
+        res = bfv.cmult(P, A[0], k4)
+        for b in range(1, 4):
+            res = bfv.hadd(P, res, bfv.pmult(P, A[b], pks[b - 1]))
+    elif lay.c_n == 2:
         A0 = np.zeros((2, P.L, P.N), dtype=np.uint64)
         A1 = np.zeros((2, P.L, P.N), dtype=np.uint64)
         js = [g_out] if lay.depthwise else range(lay.in_groups)

@@ -56,7 +56,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "network_samples.json")
 # (kernel_source_digest), per workload; reported as roofline traffic only while the kernels are unchanged
 PROFILED_TRAFFIC = {
     # profiles/vgg16_stack_batched_launches.md: the key-switch stage's 4 launches of one forward
-    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("3323b86852c31128", 41500227104),
+    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("11a1931d13bc8197", 41487433856),
 }
 
 
@@ -764,6 +764,8 @@ ABLATION = [
     ("lazy tensor-core, w=50", "(e) on tcgen05, the automatic form (in-kernel conversion for layers of one "
      "row tile, operand images for wider ones)", 50, 2, 2),
     ("lazy tensor-core, w=50, c_n=1", "padded convolution without output-channel packing (Sec. 2.4)", 50, 1, 2),
+    ("lazy CUDA-core, w=50, c_n=4", "Sec. 3.1's 4 x 4 Walsh-Hadamard basis over row x slot-parity classes "
+     "(compare with the c_n=2 CUDA-core row)", 50, 4, 1),
 ]
 
 

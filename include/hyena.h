@@ -80,6 +80,9 @@ typedef struct {
     double log2_delta;       /* log2 floor(q / t) */
     double est_noise_log2;   /* noise estimate behind the choice of w (log2) */
     uint64_t q[HE_MAX_LIMBS];
+    uint64_t k4;             /* the k of c_n = 4 packing: in [1, min(t - 1, 2^20)], minimising
+                                k + sum |[k a]_t| over the non-zero coefficients a of the three
+                                +-1 patterns of the 4 x 4 Walsh-Hadamard basis (ties -> smallest) */
 } he_param_info;
 
 /* Runs the selection of Sec. 3.2.1: primes p = q_i = 1 (mod 2N), h_{p,n}, the
@@ -120,12 +123,17 @@ typedef struct {
     uint32_t stride;         /* 1 or 2 */
     uint32_t depthwise;      /* 0 or 1 */
     uint32_t n_images;       /* images packed into the same ciphertexts (same client key) */
-    uint32_t c_n;            /* channels per ciphertext: 2 (Hyena packing) or 1 (padded conv) */
+    uint32_t c_n;            /* channels per ciphertext: 2 (Hyena packing), 1 (padded conv) or 4
+                                (Sec. 3.1's 4 x 4 Walsh-Hadamard basis: channel 4j + c of ciphertext
+                                j in slot row c >> 1 at slot parity c & 1, N/4 block positions per
+                                row; rotations 2o and 2o +- 1 per tap offset o; CUDA-core MAC only,
+                                no polyphase) */
     uint32_t tile_h, tile_w; /* interior tile size, or both 0 for the default: the whole image if its
                                 padded block fits half a ring, else full-width strips, else square
                                 tiles, each as large as fits.  Given tiles must fit the image, be
                                 multiples of the stride unless they span the image, and their padded
-                                block (tile_h + kh - 1)(tile_w + kh - 1) must fit N/2 slots. */
+                                block (tile_h + kh - 1)(tile_w + kh - 1) must fit N/2 slots (N/4
+                                positions with c_n = 4). */
     uint32_t polyphase;      /* 3x3 stride-2 layers only: 1 packs the four phase planes
                                 in[2u + a][2v + b] of the input (channel (2a + b) Cp + c, Cp = C_in
                                 rounded up to c_n) and runs the layer as a stride-1 layer on them,
@@ -139,7 +147,7 @@ typedef struct {
     uint32_t T_h, T_w;       /* interior tile size */
     uint32_t W_b;            /* block row width T_w + 2P: tap (dy,dx) = rotation by dy W_b + dx */
     uint32_t block_slots;    /* (T_h + 2P) W_b */
-    uint32_t blocks_per_row; /* tiles held by one slot row (N/2 slots) */
+    uint32_t blocks_per_row; /* tiles held by one slot row (N/2 slots; N/4 positions with c_n = 4) */
     uint32_t n_ty, n_tx;     /* tiles per image */
     uint32_t units;          /* n_images n_ty n_tx */
     uint32_t row_units;      /* ciphertext columns: units / tiles per ciphertext, rounded up */
@@ -147,7 +155,7 @@ typedef struct {
     uint32_t n_ct_in, n_ct_out;     /* row_units * groups */
     uint32_t Ho, Wo;         /* output size */
     uint32_t n_galois;       /* distinct non-identity Galois elements the layer rotates by */
-    uint64_t scale;          /* output = scale * conv (mod t): 2k with packing, 1 without */
+    uint64_t scale;          /* output = scale * conv (mod t): 2k with c_n = 2, 4 k4 with c_n = 4, 1 with c_n = 1 */
 } he_layout;
 
 /* Tiles the zero-padded input into blocks that fit one slot row; host only. */
@@ -175,8 +183,11 @@ int he_decrypt_slots(const he_params* p, const he_seckey* sk, const uint64_t* ct
 /* Server side: one convolution layer on the GPU                      */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block (0 -> default) */
-    uint32_t mac_impl;       /* 0 auto, 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL if not exact)
+    uint32_t mac_groups;     /* CUDA-core MAC: output channel groups per block, 1, 2, 4, 8 or 16
+                                (0 -> 8; at most 8 are used with c_n = 2 and 4 with c_n = 4) */
+    uint32_t mac_impl;       /* 0 auto (c_n = 4: the CUDA-core MAC; every other value but 1 is
+                                HE_EINVAL there), 1 CUDA-core lazy MAC, 2 tensor-core MAC (HE_EINVAL
+                                if not exact)
                                 in the form auto picks: 4 when the layer's output rows fit one CTA and its
                                 input channel groups are not a multiple of 8 or its digit transforms fit
                                 64 MB, else 5;

@@ -42,7 +42,8 @@ struct LimbC {
 };
 struct KP {
     u32 N, logN, L, l, w;
-    u64 kmul;  // the k of the [k,-k] plaintext
+    u64 kmul;   // the k of the [k,-k] plaintext
+    u64 kmul4;  // the k of the c_n = 4 patterns
     LimbC limb[HE_MAX_LIMBS];
     const u64* tw;   // [L][N][2]: psi^rev(k) and its Shoup companion, side by side (one 16-byte load)
     const u64* itw;  // [L][N][2]: psi^-rev(k) and its Shoup companion
@@ -573,8 +574,9 @@ __global__ void __launch_bounds__(KS_THREADS) k_keyswitch(const __grid_constant_
 // Step 3: lazy channel multiply-accumulate (CMult^- and HAdd^128 of Sec. 3.2.2).
 // Each residue v < 2^50 is split v = vh 2^25 + vl; s*vl and s*vh accumulate
 // exactly in int64 (|s| <= 2^15, at most 2^14 terms), and A = hi 2^25 + lo is
-// reduced once.  PACKED: rows r = 0, 1 of the Walsh-Hadamard pair and the
-// epilogue out = k*[A0] + [A1] * NTT(P_k); otherwise out = [A0].
+// reduced once.  NR rows per output group: NR = 2, the Walsh-Hadamard pair with the
+// epilogue out = k*[A0] + [A1] * NTT(P_k); NR = 4, the 4 x 4 basis with
+// out = k4*[A0] + sum_b [A_b] * NTT(k4 pattern_b); NR = 1, out = [A0].
 constexpr int MAC_THREADS = 256;
 constexpr int MAC_KC = 128;
 
@@ -590,9 +592,9 @@ __device__ __forceinline__ void mad_wide(i64& acc, int a, int b) {
 
 // Local block = ((row unit, polynomial, limb), slot tile, group tile); the
 // group tile varies fastest so that blocks reading the same residues run together.
-template <int GT, bool PACKED, bool DW, int MAXB>
+template <int GT, int NR, bool DW, int MAXB>
 __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Batch<MAXB> B, KP kp) {
-    constexpr int NR = PACKED ? 2 : 1;
+    static_assert(NR == 1 || NR == 2 || NR == 4, "rows per output group: 1, 2 or 4");
     constexpr int NS = GT * NR;            // scalars used per term
     constexpr int NSP = (NS + 3) & ~3;     // padded to whole int4 loads
     __shared__ __align__(16) int ss[MAC_KC][NSP];
@@ -645,14 +647,19 @@ __global__ void __launch_bounds__(MAC_THREADS) k_mac(const __grid_constant__ Bat
         }
         __syncthreads();
     }
-    const u64 pkv = PACKED ? Ly.pk[(size_t)k * N + x] : 0;
+    // NTT of the pattern plaintexts at this slot: pk [NR - 1][L][N]
+    u64 pkv[NR > 1 ? NR - 1 : 1];
+#pragma unroll
+    for (int b = 0; b < NR - 1; b++) pkv[b] = Ly.pk[((size_t)b * L + k) * N + x];
 #pragma unroll
     for (int g = 0; g < GT; g++) {
         if (g0 + g >= out_groups) break;
         u64 out = reduce_split(lo[g * NR], hi[g * NR], m);
-        if (PACKED) {
-            const u64 a1 = reduce_split(lo[g * NR + 1], hi[g * NR + 1], m);
-            out = addq(mulmod(kp.kmul, out, m), mulmod(a1, pkv, m), m.q);
+        if (NR > 1) {
+            out = mulmod(NR == 2 ? kp.kmul : kp.kmul4, out, m);
+#pragma unroll
+            for (int b = 1; b < NR; b++)
+                out = addq(out, mulmod(reduce_split(lo[g * NR + b], hi[g * NR + b], m), pkv[b - 1], m), m.q);
         }
         Ly.O[((size_t)(ru * out_groups + g0 + g) * 2 + p) * L * N + (size_t)k * N + x] = out;
     }
@@ -2531,6 +2538,7 @@ KP make_kp(const he_params* p) {
     std::memset(&kp, 0, sizeof(kp));
     kp.N = p->N, kp.logN = p->logN, kp.L = p->L, kp.l = p->l, kp.w = p->w;
     kp.kmul = p->k;
+    kp.kmul4 = p->k4;
     for (u32 k = 0; k < p->L; k++) {
         kp.limb[k].q = p->q[k];
         kp.limb[k].mu = p->mod[k].mu;
@@ -2644,9 +2652,10 @@ void fill_uniform(const KP& kp, u64* d, size_t n_polys, u64 seed, cudaStream_t s
 // MAC kernel variants: tensor core (packed or not) or CUDA cores (group tile, packed, depthwise)
 struct MacVariant {
     bool tc = false, packed = false, dw = false, eager = false, img = false, fused = false, pair = false, cp = false;
+    bool h4 = false;     // c_n = 4: four rows per output group (CUDA-core MAC)
     u32 gt = 8, cl = 1;  // cl: CTAs per cluster of the operand-image MAC
     bool operator==(const MacVariant& o) const {
-        return tc == o.tc && packed == o.packed && dw == o.dw && eager == o.eager && img == o.img && cl == o.cl &&
+        return tc == o.tc && packed == o.packed && h4 == o.h4 && dw == o.dw && eager == o.eager && img == o.img && cl == o.cl &&
                fused == o.fused && pair == o.pair && cp == o.cp && (tc || eager || gt == o.gt);
     }
 };
@@ -2698,9 +2707,9 @@ void launch_keyswitch_b(const he_params* p, u32 blocks, const Batch<MAXB>& B, co
     }
 }
 
-template <int GT, bool PACKED, bool DW, int MAXB>
+template <int GT, int NR, bool DW, int MAXB>
 void mac_cuda_launch(u32 blocks, const Batch<MAXB>& B, const KP& kp, cudaStream_t s) {
-    k_mac<GT, PACKED, DW, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
+    k_mac<GT, NR, DW, MAXB><<<blocks, MAC_THREADS, 0, s>>>(B, kp);
 }
 
 // Persistent launch of the operand-image MAC in clusters of CL CTAs: as many clusters as fit the
@@ -2840,24 +2849,32 @@ void launch_mac_b(const he_params* p, const MacVariant& mv, u32 blocks, const Ba
         return;
     }
     if (mv.dw) {
-        if (mv.packed) mac_cuda_launch<1, true, true, MAXB>(blocks, B, kp, s);
-        else mac_cuda_launch<1, false, true, MAXB>(blocks, B, kp, s);
+        if (mv.h4) mac_cuda_launch<1, 4, true, MAXB>(blocks, B, kp, s);
+        else if (mv.packed) mac_cuda_launch<1, 2, true, MAXB>(blocks, B, kp, s);
+        else mac_cuda_launch<1, 1, true, MAXB>(blocks, B, kp, s);
         return;
     }
-    if (mv.packed) {
+    if (mv.h4) {
+        // four rows per group: at most 4 groups per block (16 accumulator pairs, as 8 pair groups)
         switch (mv.gt) {
-            case 1: mac_cuda_launch<1, true, false, MAXB>(blocks, B, kp, s); break;
-            case 2: mac_cuda_launch<2, true, false, MAXB>(blocks, B, kp, s); break;
-            case 4: mac_cuda_launch<4, true, false, MAXB>(blocks, B, kp, s); break;
-            default: mac_cuda_launch<8, true, false, MAXB>(blocks, B, kp, s); break;
+            case 1: mac_cuda_launch<1, 4, false, MAXB>(blocks, B, kp, s); break;
+            case 2: mac_cuda_launch<2, 4, false, MAXB>(blocks, B, kp, s); break;
+            default: mac_cuda_launch<4, 4, false, MAXB>(blocks, B, kp, s); break;
+        }
+    } else if (mv.packed) {
+        switch (mv.gt) {
+            case 1: mac_cuda_launch<1, 2, false, MAXB>(blocks, B, kp, s); break;
+            case 2: mac_cuda_launch<2, 2, false, MAXB>(blocks, B, kp, s); break;
+            case 4: mac_cuda_launch<4, 2, false, MAXB>(blocks, B, kp, s); break;
+            default: mac_cuda_launch<8, 2, false, MAXB>(blocks, B, kp, s); break;
         }
     } else {
         switch (mv.gt) {
-            case 1: mac_cuda_launch<1, false, false, MAXB>(blocks, B, kp, s); break;
-            case 2: mac_cuda_launch<2, false, false, MAXB>(blocks, B, kp, s); break;
-            case 4: mac_cuda_launch<4, false, false, MAXB>(blocks, B, kp, s); break;
-            case 8: mac_cuda_launch<8, false, false, MAXB>(blocks, B, kp, s); break;
-            default: mac_cuda_launch<16, false, false, MAXB>(blocks, B, kp, s); break;
+            case 1: mac_cuda_launch<1, 1, false, MAXB>(blocks, B, kp, s); break;
+            case 2: mac_cuda_launch<2, 1, false, MAXB>(blocks, B, kp, s); break;
+            case 4: mac_cuda_launch<4, 1, false, MAXB>(blocks, B, kp, s); break;
+            case 8: mac_cuda_launch<8, 1, false, MAXB>(blocks, B, kp, s); break;
+            default: mac_cuda_launch<16, 1, false, MAXB>(blocks, B, kp, s); break;
         }
     }
 }
@@ -3016,7 +3033,7 @@ struct he_plan {
     he_layout lay{};
     int device = 0;
     u32 n_rot = 0, rot_id = 0, K = 0, n_ks = 0;
-    bool packed = false, dw = false;
+    bool packed = false, h4 = false, dw = false;
     u32 mac_groups = 8;
     bool use_tc = false, eager = false, img = false, fused = false, pair = false, cp = false;
     u32 tc_rows = 0, tc_rows_per_cta = 0, tc_kpad = 0, in_pad = 0, cl = 1;
@@ -3070,7 +3087,9 @@ struct he_plan {
             tcp_encode_maps(&L.rmap, &L.smap, L.A16, (u64)lay.row_units * 2 * p->L * (p->N / TC_MTILE) * ktiles,
                             d_sc16, 2 * npairs * ktiles);
         }
-        s.mv.tc = use_tc, s.mv.packed = packed, s.mv.dw = dw, s.mv.gt = dw ? 1 : mac_groups, s.mv.eager = eager;
+        s.mv.tc = use_tc, s.mv.packed = packed, s.mv.h4 = h4, s.mv.dw = dw, s.mv.eager = eager;
+        // groups per CUDA-core MAC block: as many as the kernel holds accumulators for (16 rows)
+        s.mv.gt = dw ? 1 : std::min(mac_groups, h4 ? 4u : (packed ? 8u : 16u));
         s.mv.img = img, s.mv.cl = cl, s.mv.fused = fused, s.mv.pair = pair, s.mv.cp = cp;
         L.fused = fused;
         if (fused) L.A16 = nullptr;
@@ -3089,6 +3108,7 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     compute_layout(p, d, &P->lay);
     const he_layout& lay = P->lay;
     P->packed = d->c_n == 2;
+    P->h4 = d->c_n == 4;
     P->dw = d->depthwise != 0;
     std::vector<RotEntry> rl = rotation_list(p, d, lay);
     P->n_rot = (u32)rl.size();
@@ -3119,8 +3139,8 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         keys.push_back(k);
     }
     if (p->L * p->l > 16) fail(HE_EINVAL, "L * l must be at most 16");
-    // Hadamard scalars s0 = v0 + v1, s1 = v0 - v1 (Eq. 1 without the 1/2)
-    const u32 NR = P->packed ? 2 : 1;
+    // Hadamard scalars s0 = v0 + v1, s1 = v0 - v1 (Eq. 1 without the 1/2); with c_n = 4, s_b = H4 v
+    const u32 NR = P->h4 ? 4 : (P->packed ? 2 : 1);
     // a depthwise output reads its own channel's input ciphertext, or with polyphase packing the
     // ciphertexts of its channel's four phase planes (input groups phase-major: phase * out_groups + g)
     const u32 phases = d->polyphase ? 4 : 1;
@@ -3153,13 +3173,37 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
         if (P->dw) return o == i ? weights[(size_t)o * taps + tap] : 0;
         return weights[((size_t)o * wcin + i) * taps + tap];
     };
-    double worst0 = 0, worst1 = 0, worst_abs = 0;
+    // c_n = 4: tap index of a block offset dy W_b + dx (unique since W_b > 2P), or none
+    std::vector<std::pair<i64, u32>> tap_at;
+    for (int dy = -(int)lay.P; dy <= (int)lay.P; dy++)
+        for (int dx = -(int)lay.P; dx <= (int)lay.P; dx++)
+            tap_at.push_back({(i64)dy * lay.W_b + dx, (u32)((dy + (int)lay.P) * d->kh + dx + (int)lay.P)});
+    static const int H4_BASIS[4][4] = {{1, 1, 1, 1}, {1, -1, 1, -1}, {1, 1, -1, -1}, {1, -1, -1, 1}};
+    double worst0 = 0, worst1 = 0, worst_abs = 0, worst4[4] = {0, 0, 0, 0};
     for (u32 g = 0; g < lay.out_groups; g++) {
-        double s0q = 0, s1q = 0, sab = 0;
+        double s0q = 0, s1q = 0, sab = 0, sq4[4] = {0, 0, 0, 0};
         for (u32 kk = 0; kk < P->K; kk++) {
             u32 j = P->dw ? (kk / P->n_rot) * lay.out_groups + g : kk / P->n_rot, r = kk % P->n_rot;
             u32 tap = rl[r].tap, dg = rl[r].d;
             i64 s0, s1 = 0;
+            if (P->h4) {
+                // output class c = 2 row + parity e reads, through the copy (step, d), row
+                // (c >> 1) ^ d at parity e' = (e + step) mod 2 from offset (e + step - e') / 2
+                i64 v[4] = {0, 0, 0, 0};
+                for (u32 c = 0; c < 4; c++) {
+                    const i64 e = c & 1, es = (e + rl[r].step) & 1, o = (e + rl[r].step - es) / 2;
+                    for (auto& ta : tap_at)
+                        if (ta.first == o) v[c] = W(4 * g + c, 4 * j + 2 * ((c >> 1) ^ dg) + (u32)es, ta.second);
+                }
+                for (u32 b = 0; b < 4; b++) {
+                    i64 sb = 0;
+                    for (u32 c = 0; c < 4; c++) sb += H4_BASIS[b][c] * v[c];
+                    if (sb < -32768 || sb > 32767) fail(HE_EINVAL, "weights must satisfy |w| <= 8191 with c_n = 4");
+                    sc[((size_t)g * NR + b) * P->K + kk] = (int16_t)sb;
+                    sq4[b] += (double)sb * sb, sab += std::fabs((double)sb);
+                }
+                continue;
+            }
             if (P->packed) {
                 i64 v0 = dg == 0 ? W(2 * g, 2 * j, tap) : W(2 * g, 2 * j + 1, tap);
                 i64 v1 = dg == 0 ? W(2 * g + 1, 2 * j + 1, tap) : W(2 * g + 1, 2 * j, tap);
@@ -3174,8 +3218,10 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
             s0q += (double)s0 * s0, s1q += (double)s1 * s1, sab += std::fabs((double)s0) + std::fabs((double)s1);
         }
         worst0 = std::max(worst0, s0q), worst1 = std::max(worst1, s1q), worst_abs = std::max(worst_abs, sab);
+        for (u32 b = 0; b < 4; b++) worst4[b] = std::max(worst4[b], sq4[b]);
     }
-    double est = estimate_noise_log2(p, p->w, worst0, worst1, worst_abs, P->packed);
+    double est = P->h4 ? estimate_noise_log2_h4(p, p->w, worst4, worst_abs)
+                       : estimate_noise_log2(p, p->w, worst0, worst1, worst_abs, P->packed);
     if (est >= p->log2_delta - 1.0) fail(HE_ENOISE, "estimated noise exceeds Delta/2 for this layer");
     // tensor-core contraction: exact while |s| <= 16 (fp32 sums of 2048-term segments below 2^24)
     int max_abs_s = 0;
@@ -3184,7 +3230,9 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     // five 10-bit chunks carry a residue only while every limb is below 2^50
     bool limbs_fit = true;
     for (u64 qi : p->q) limbs_fit = limbs_fit && qi < (1ull << (10 * TC_CHUNKS));
-    const bool tc_ok = !P->dw && max_abs_s <= TC_SMAX && limbs_fit;
+    if (P->h4 && impl != 0 && impl != 1)
+        fail(HE_EINVAL, "c_n = 4 runs on the CUDA-core MAC only (mac_impl 0 or 1)");
+    const bool tc_ok = !P->dw && !P->h4 && max_abs_s <= TC_SMAX && limbs_fit;
     if ((impl == 2 || impl >= 4) && !tc_ok)
         fail(HE_EINVAL, "tensor-core MAC needs |s| <= 16, limbs below 2^50 and a non-depthwise layer");
     if (impl == 3 && P->dw) fail(HE_EINVAL, "the eager MAC is not built for depthwise layers");
@@ -3194,7 +3242,11 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     P->eager = impl == 3;
     P->use_tc = tc_ok && impl != 1 && impl != 3;
     P->in_pad = (lay.in_groups + 7) / 8 * 8;
-    if (tune && tune->mac_groups) P->mac_groups = tune->mac_groups;
+    if (tune && tune->mac_groups) {
+        const u32 mg = tune->mac_groups;
+        if (mg > 16 || (mg & (mg - 1))) fail(HE_EINVAL, "mac_groups must be 1, 2, 4, 8 or 16");
+        P->mac_groups = mg;
+    }
     const u32 tc_rows_req = tune ? tune->tc_rows : 0;
     if (tc_rows_req && (tc_rows_req % 16 || tc_rows_req > (u32)TC_NMAX))
         fail(HE_EINVAL, "tc_rows must be a multiple of 16, at most 96");
@@ -3256,20 +3308,35 @@ static std::unique_ptr<he_plan> build_plan(const he_params* p, const he_galkeys*
     CUDA_OK(cudaMemcpy(P->d_rots_all, rots_all.data(), rots_all.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
     CUDA_OK(cudaMalloc(&P->d_scal, sc.size() * sizeof(int16_t)));
     CUDA_OK(cudaMemcpy(P->d_scal, sc.data(), sc.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-    // NTT(P_k): P_k = kh (X^(N/4) + X^(3N/4)) lifted into every limb
-    if (P->packed) {
-        std::vector<u64> pk((size_t)p->L * p->N, 0);
-        for (u32 k = 0; k < p->L; k++) {
-            u64 v = p->mod[k].from_signed(p->kh);
-            pk[(size_t)k * p->N + p->N / 4] = v;
-            pk[(size_t)k * p->N + 3 * p->N / 4] = v;
-            p->ntt[k].forward(pk.data() + (size_t)k * p->N);
-        }
+    // NTT(P_k): P_k = kh (X^(N/4) + X^(3N/4)) lifted into every limb; with c_n = 4 the three
+    // k4-scaled patterns [3][L][N], their centred coefficients lifted the same way
+    if (P->packed || P->h4) {
+        const u32 nb = P->h4 ? 3 : 1;
+        std::vector<u64> pk((size_t)nb * p->L * p->N, 0);
+        for (u32 b = 0; b < nb; b++)
+            for (u32 k = 0; k < p->L; k++) {
+                u64* row = pk.data() + ((size_t)b * p->L + k) * p->N;
+                if (P->h4) {
+                    for (u32 j = 0; j < p->N; j++) {
+                        const i64 a = p->pat4[(size_t)b * p->N + j];
+                        if (!a) continue;
+                        i64 v = (i64)(((__int128)a * (i64)p->k4) % (i64)p->t);
+                        if (v > (i64)(p->t / 2)) v -= (i64)p->t;
+                        if (v < -(i64)(p->t / 2)) v += (i64)p->t;
+                        row[j] = p->mod[k].from_signed(v);
+                    }
+                } else {
+                    const u64 v = p->mod[k].from_signed(p->kh);
+                    row[p->N / 4] = v;
+                    row[3 * p->N / 4] = v;
+                }
+                p->ntt[k].forward(row);
+            }
         CUDA_OK(cudaMalloc(&P->d_pk, pk.size() * 8));
         CUDA_OK(cudaMemcpy(P->d_pk, pk.data(), pk.size() * 8, cudaMemcpyHostToDevice));
         std::vector<u64> pksh(pk.size());
         for (size_t i = 0; i < pk.size(); i++) {
-            const u64 q = p->q[i / p->N];
+            const u64 q = p->q[(i / p->N) % p->L];
             pksh[i] = (u64)((((unsigned __int128)pk[i]) << 64) / q);
         }
         CUDA_OK(cudaMalloc(&P->d_pksh, pksh.size() * 8));

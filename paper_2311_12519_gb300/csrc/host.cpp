@@ -432,6 +432,8 @@ static void finish_params(he_params* P) {
     }
 }
 
+static void hadamard4_setup(he_params* P);
+
 extern "C" int he_params_create(const he_param_req* req, he_params** out) {
     return guard([&] {
         if (!req || !out) fail(HE_EINVAL, "null argument");
@@ -470,6 +472,7 @@ extern "C" int he_params_create(const he_param_req* req, he_params** out) {
             u64 v = P->mod_t.mul(best_k, P->h);
             P->kh = v > P->t / 2 ? (i64)v - (i64)P->t : (i64)v;
         }
+        hadamard4_setup(P.get());
         // decomposition base
         u32 sb = 0;
         for (u64 qi : P->q) sb = std::max(sb, (u32)bitlen(qi));
@@ -506,7 +509,7 @@ extern "C" int he_params_info(const he_params* p, he_param_info* o) {
         if (!p || !o) fail(HE_EINVAL, "null argument");
         std::memset(o, 0, sizeof(*o));
         o->N = p->N, o->L = p->L, o->w = p->w, o->l = p->l;
-        o->t = p->t, o->zeta = p->zeta, o->h = p->h, o->k = p->k, o->kh = p->kh;
+        o->t = p->t, o->zeta = p->zeta, o->h = p->h, o->k = p->k, o->kh = p->kh, o->k4 = p->k4;
         o->log2_delta = p->log2_delta;
         o->est_noise_log2 = p->est_noise_log2;
         for (u32 k = 0; k < p->L; k++) o->q[k] = p->q[k];
@@ -517,15 +520,20 @@ extern "C" void he_params_destroy(he_params* p) { delete p; }
 
 // ------------------------------------------------------------------ noise estimate
 namespace hy {
-double estimate_noise_log2(const he_params* p, u32 w, double sum_s0_sq, double sum_s1_sq, double sum_abs_s,
-                           bool packed) {
+// variance of a rotated copy's noise: the key switch sums L*l digit polynomials times sigma(d) * e,
+// N terms per coefficient, plus the input's own noise
+static double key_switch_variance(const he_params* p, u32 w) {
     u32 sb = 0;
     for (u64 qi : p->q) sb = std::max(sb, (u32)bitlen(qi));
     double l = (double)((sb + w - 1) / w);
     double sigma2 = (double)SIGMA2_NUM / (double)SIGMA2_DEN;
     double d2 = std::ldexp(1.0, (int)(2 * w)) / 3.0;  // E[d^2], d uniform in [0, 2^w)
-    // key switch: sum over L*l digit polynomials of sigma(d) * e, N terms per coefficient
-    double var_ks = (double)p->L * l * (double)p->N * d2 * sigma2 + sigma2;
+    return (double)p->L * l * (double)p->N * d2 * sigma2 + sigma2;
+}
+
+double estimate_noise_log2(const he_params* p, u32 w, double sum_s0_sq, double sum_s1_sq, double sum_abs_s,
+                           bool packed) {
+    double var_ks = key_switch_variance(p, w);
     double k = (double)p->k, kh = (double)std::llabs(p->kh), t = (double)p->t;
     double var_out, extra;
     if (packed) {
@@ -535,6 +543,27 @@ double estimate_noise_log2(const he_params* p, u32 w, double sum_s0_sq, double s
         var_out = var_ks * sum_s0_sq;
         extra = t * sum_abs_s;
     }
+    return std::log2(6.0 * std::sqrt(var_out) + extra + 1.0);
+}
+
+// PMult by the k4-scaled pattern b multiplies a noise coefficient by each of its (one or two)
+// non-zero coefficients: variance x their sum of squares, worst case x their absolute sum
+double estimate_noise_log2_h4(const he_params* p, u32 w, const double sum_sq[4], double sum_abs_s) {
+    const double var_ks = key_switch_variance(p, w), k = (double)p->k4, t = (double)p->t;
+    double var_out = k * k * var_ks * sum_sq[0], l1 = 0;
+    for (u32 b = 0; b < 3; b++) {
+        double l2 = 0;
+        for (u32 j = 0; j < p->N; j++) {
+            const i64 a = p->pat4[(size_t)b * p->N + j];
+            if (!a) continue;
+            i64 v = (i64)(((__int128)a * (i64)p->k4) % (i64)p->t);
+            if (v > (i64)(p->t / 2)) v -= (i64)p->t;
+            if (v < -(i64)(p->t / 2)) v += (i64)p->t;
+            l2 += (double)v * (double)v, l1 += std::fabs((double)v);
+        }
+        var_out += l2 * var_ks * sum_sq[b + 1];
+    }
+    const double extra = t * ((k + l1) * sum_abs_s + l1);
     return std::log2(6.0 * std::sqrt(var_out) + extra + 1.0);
 }
 }  // namespace hy
@@ -629,6 +658,40 @@ static void encode_slots(const he_params* p, const int64_t* slots, std::vector<u
 static void decode_slots(const he_params* p, std::vector<u64>& m, int64_t* slots) {
     p->ntt_t.forward(m.data());
     for (u32 s = 0; s < p->N; s++) slots[s] = (int64_t)m[p->slot_index[s]];
+}
+
+// c_n = 4 (Sec. 3.1's 4 x 4 Walsh-Hadamard basis over the slot classes c = 2 row + (index mod 2)):
+// the patterns holding H4[b][c] in the slots of class c, b = 1, 2, 3, as centred coefficients,
+// and k4, the k in [1, min(t - 1, 2^20)] minimising k + sum |[k a]_t| over their non-zero
+// coefficients a (the noise-growth bound of CMult by k and the three PMults; ties -> smallest k).
+static const int H4_BASIS[4][4] = {{1, 1, 1, 1}, {1, -1, 1, -1}, {1, 1, -1, -1}, {1, -1, -1, 1}};
+static void hadamard4_setup(he_params* P) {
+    const u32 N = P->N, half = N / 2;
+    P->pat4.assign(3 * (size_t)N, 0);
+    std::vector<int64_t> slots(N);
+    std::vector<u64> m, nz;
+    for (int b = 1; b < 4; b++) {
+        for (u32 s = 0; s < N; s++) slots[s] = H4_BASIS[b][2 * (s / half) + (s & 1)];
+        encode_slots(P, slots.data(), m);
+        for (u32 j = 0; j < N; j++) {
+            P->pat4[(size_t)(b - 1) * N + j] = m[j] > P->t / 2 ? (i64)m[j] - (i64)P->t : (i64)m[j];
+            if (m[j]) nz.push_back(m[j]);
+        }
+    }
+    const u64 kmax = std::min<u64>(P->t - 1, 1ull << 20);
+    std::vector<u64> ka(nz.size(), 0);  // [k a]_t, stepped by a
+    u64 best = ~0ull, best_k = 1;
+    for (u64 k = 1; k <= kmax; k++) {
+        u64 G = k;
+        for (size_t i = 0; i < nz.size(); i++) {
+            u64 v = ka[i] + nz[i];
+            if (v >= P->t) v -= P->t;
+            ka[i] = v;
+            G += std::min(v, P->t - v);
+        }
+        if (G < best) best = G, best_k = k;
+    }
+    P->k4 = best_k;
 }
 static void encrypt_poly(const he_params* p, const he_seckey* sk, const std::vector<u64>& m, u64 seed, u64 index,
                          u64* ct) {
@@ -738,12 +801,14 @@ void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* o) {
     if (!d->C_in || !d->C_out || !d->H || !d->W || !d->n_images) fail(HE_EINVAL, "empty layer");
     if (d->kh % 2 == 0 || d->kh > 7) fail(HE_EINVAL, "kernel must be odd, at most 7");
     if (d->stride < 1 || d->stride > 2) fail(HE_EINVAL, "stride must be 1 or 2");
-    if (d->c_n != 1 && d->c_n != 2) fail(HE_EINVAL, "c_n must be 1 or 2");
+    if (d->c_n != 1 && d->c_n != 2 && d->c_n != 4) fail(HE_EINVAL, "c_n must be 1, 2 or 4");
     if (d->depthwise && d->C_in != d->C_out) fail(HE_EINVAL, "depthwise needs C_in == C_out");
     if (d->polyphase > 1 || (d->polyphase && (d->stride != 2 || d->kh != 3)))
         fail(HE_EINVAL, "polyphase packing is for 3x3 stride-2 layers (polyphase 0 or 1)");
+    if (d->c_n == 4 && d->polyphase) fail(HE_EINVAL, "polyphase packing is built for c_n 1 and 2");
     std::memset(o, 0, sizeof(*o));
-    const u32 half = p->N / 2, P = (d->kh - 1) / 2;
+    // block positions of a slot row: N/2, or N/4 with c_n = 4 (two slot parities per position)
+    const u32 half = d->c_n == 4 ? p->N / 4 : p->N / 2, P = (d->kh - 1) / 2;
     u32 Hp, Wp, S, Cp;
     plane_geometry(d, &Hp, &Wp, &S, &Cp);
     o->P = P;
@@ -751,7 +816,8 @@ void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* o) {
         const u32 th = d->tile_h, tw = d->tile_w;
         if (!th || !tw || th > Hp || tw > Wp) fail(HE_EINVAL, "tile must be given in both directions, within the image");
         if ((th % S && th != Hp) || (tw % S && tw != Wp)) fail(HE_EINVAL, "tile sides must be multiples of the stride");
-        if ((u64)(th + 2 * P) * (tw + 2 * P) > half) fail(HE_EINVAL, "padded tile does not fit N/2 slots");
+        if ((u64)(th + 2 * P) * (tw + 2 * P) > half)
+            fail(HE_EINVAL, "padded tile does not fit a slot row (N/2 positions, N/4 with c_n = 4)");
         o->T_h = th, o->T_w = tw;
     } else {
         choose_tile(half, Hp, Wp, P, S, &o->T_h, &o->T_w);
@@ -770,7 +836,7 @@ void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* o) {
     o->n_ct_out = o->row_units * o->out_groups;
     o->Ho = (Hp - 1) / S + 1;
     o->Wo = (Wp - 1) / S + 1;
-    o->scale = d->c_n == 2 ? (2 * p->k) % p->t : 1;
+    o->scale = d->c_n == 4 ? (4 * p->k4) % p->t : d->c_n == 2 ? (2 * p->k) % p->t : 1;
     std::vector<RotEntry> rl = rotation_list(p, d, *o);
     std::vector<u32> gs;
     for (auto& r : rl)
@@ -782,8 +848,27 @@ void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* o) {
 std::vector<RotEntry> rotation_list(const he_params* p, const he_conv_desc* d, const he_layout& lay) {
     std::vector<RotEntry> out;
     const i64 P = lay.P;
-    const u32 ndiag = (d->c_n == 2 && !d->depthwise) ? 2 : 1;
+    const u32 ndiag = (d->c_n != 1 && !d->depthwise) ? 2 : 1;
     const u32 swap = 2 * p->N - 1;
+    if (d->c_n == 4) {
+        // steps 2o for every tap offset o = dy W_b + dx and, unless depthwise (an output class then
+        // reads only its own class), the parity-changing steps 2o - 1 and 2o + 1; ascending
+        std::vector<i64> steps;
+        for (i64 dy = -P; dy <= P; dy++)
+            for (i64 dx = -P; dx <= P; dx++) {
+                const i64 o = dy * (i64)lay.W_b + dx;
+                steps.push_back(2 * o);
+                if (!d->depthwise) steps.push_back(2 * o - 1), steps.push_back(2 * o + 1);
+            }
+        std::sort(steps.begin(), steps.end());
+        steps.erase(std::unique(steps.begin(), steps.end()), steps.end());
+        for (i64 st : steps) {
+            const u32 g = rotation_galois(p, st);
+            for (u32 dg = 0; dg < ndiag; dg++)
+                out.push_back({~0u, dg, dg ? (u32)((u64)g * swap % (2ULL * p->N)) : g, st});
+        }
+        return out;
+    }
     u32 tap = 0;
     for (i64 dy = -P; dy <= P; dy++)
         for (i64 dx = -P; dx <= P; dx++, tap++) {
@@ -792,7 +877,7 @@ std::vector<RotEntry> rotation_list(const he_params* p, const he_conv_desc* d, c
             u32 g = rotation_galois(p, dy * (i64)lay.W_b + dx);
             for (u32 dg = 0; dg < ndiag; dg++) {
                 u32 gg = dg ? (u32)((u64)g * swap % (2ULL * p->N)) : g;
-                out.push_back({tap, dg, gg});
+                out.push_back({tap, dg, gg, dy * (i64)lay.W_b + dx});
             }
         }
     return out;
@@ -823,12 +908,21 @@ extern "C" int he_layer_galois(const he_params* p, const he_conv_desc* d, uint32
     });
 }
 
-// slot of block-local position (yl, xl) of the u-th tile held by a ciphertext
+// row and position of block-local position (yl, xl) of the u-th tile held by a ciphertext
 static void slot_of(const he_conv_desc* d, const he_layout& lay, u32 u, u32 yl, u32 xl, u32* row, u32* pos) {
     u32 B = lay.blocks_per_row, b;
-    if (d->c_n == 2) *row = 0, b = u;
-    else *row = u / B, b = u % B;
+    if (d->c_n == 1) *row = u / B, b = u % B;
+    else *row = 0, b = u;
     *pos = b * lay.block_slots + yl * lay.W_b + xl;
+}
+
+// flat slot of channel r (0 .. c_n - 1) of a ciphertext at (row, pos): c_n = 1 uses the row,
+// c_n = 2 puts channel r in row r, c_n = 4 in row r >> 1 at slot parity r & 1
+static u32 flat_slot(const he_conv_desc* d, u32 N, u32 row, u32 pos, u32 r) {
+    const u32 half = N / 2;
+    if (d->c_n == 1) return row * half + pos;
+    if (d->c_n == 2) return r * half + pos;
+    return (r >> 1) * half + 2 * pos + (r & 1);
 }
 
 extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const he_conv_desc* d, const int64_t* act,
@@ -837,7 +931,7 @@ extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const h
         if (!p || !sk || !d || !act || !ct_out) fail(HE_EINVAL, "null argument");
         he_layout lay;
         compute_layout(p, d, &lay);
-        const u32 N = p->N, half = N / 2, P = lay.P;
+        const u32 N = p->N, P = lay.P;
         const u32 per_ct = lay.blocks_per_row * (d->c_n == 1 ? 2 : 1);
         u32 Hp, Wp, S, Cplanes;
         plane_geometry(d, &Hp, &Wp, &S, &Cplanes);
@@ -866,13 +960,9 @@ extern "C" int he_encrypt_image(const he_params* p, const he_seckey* sk, const h
                     slot_of(d, lay, u, yl, xl, &row, &pos);
                     for (u32 j = 0; j < lay.in_groups; j++) {
                         int64_t* sv = slots.data() + (size_t)(ru * lay.in_groups + j) * N;
-                        if (d->c_n == 2) {
-                            for (u32 r = 0; r < 2; r++) {
-                                u32 c = 2 * j + r;
-                                if (c < Cplanes) sv[r * half + pos] = A(img, c, Y, X);
-                            }
-                        } else {
-                            sv[row * half + pos] = A(img, j, Y, X);
+                        for (u32 r = 0; r < d->c_n; r++) {
+                            const u32 c = d->c_n * j + r;
+                            if (c < Cplanes) sv[flat_slot(d, N, row, pos, r)] = A(img, c, Y, X);
                         }
                     }
                 }
@@ -895,7 +985,7 @@ extern "C" int he_decrypt_image(const he_params* p, const he_seckey* sk, const h
         compute_layout(p, d, &lay);
         u32 Hp, Wp, S, Cplanes;
         plane_geometry(d, &Hp, &Wp, &S, &Cplanes);
-        const u32 N = p->N, half = N / 2, P = lay.P;
+        const u32 N = p->N, P = lay.P;
         const u32 per_ct = lay.blocks_per_row * (d->c_n == 1 ? 2 : 1);
         const size_t ctw = 2ULL * p->L * N;
         std::vector<int64_t> slots((size_t)lay.n_ct_out * N);
@@ -924,12 +1014,8 @@ extern "C" int he_decrypt_image(const he_params* p, const he_seckey* sk, const h
                             out[(((size_t)img * d->C_out + c) * lay.Ho + Y / S) * lay.Wo + X / S] =
                                 (int64_t)p->mod_t.mul((u64)v, inv);
                         };
-                        if (d->c_n == 2) {
-                            for (u32 r = 0; r < 2; r++)
-                                if (2 * g + r < d->C_out) put(2 * g + r, sv[r * half + pos]);
-                        } else {
-                            put(g, sv[row * half + pos]);
-                        }
+                        for (u32 r = 0; r < d->c_n; r++)
+                            if (d->c_n * g + r < d->C_out) put(d->c_n * g + r, sv[flat_slot(d, N, row, pos, r)]);
                     }
                 }
             }

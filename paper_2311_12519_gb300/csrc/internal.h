@@ -126,6 +126,10 @@ struct he_params {
     hy::u32 N = 0, L = 0, logN = 0, w = 0, l = 0;
     hy::u64 t = 0, zeta = 0, h = 0, k = 1;
     hy::i64 kh = 0;
+    // c_n = 4: k of the three Walsh-Hadamard patterns and their centred coefficients [3][N]
+    // (b = 1, 2, 3: slot parity, row, their product; unscaled +-1 patterns)
+    hy::u64 k4 = 1;
+    std::vector<hy::i64> pat4;
     std::vector<hy::u64> q, psi;
     std::vector<hy::Modulus> mod;
     std::vector<hy::HostNtt> ntt;  // one per limb
@@ -164,6 +168,7 @@ namespace hy {
 // Layout and rotation list of a layer.
 struct RotEntry {
     u32 tap, d, galois;
+    i64 step;  // left-rotation step before the row swap d (c_n = 4 keys its scalars on it)
 };
 void compute_layout(const he_params* p, const he_conv_desc* d, he_layout* out);
 // plane height, width, stride and channel count the slots of a layer hold (polyphase: the phase planes)
@@ -173,5 +178,7 @@ u32 rotation_galois(const he_params* p, i64 step);
 // log2 of the estimated worst output noise (6 sigma + rounding terms).
 double estimate_noise_log2(const he_params* p, u32 w, double sum_s0_sq, double sum_s1_sq, double sum_abs_s,
                            bool packed);
+// The same for c_n = 4: sum_sq[b] = sum of s_b^2 over a row's terms, out = k4 A0 + sum_b A_b (k4 pattern_b).
+double estimate_noise_log2_h4(const he_params* p, u32 w, const double sum_sq[4], double sum_abs_s);
 const DeviceTables& device_tables(const he_params* p);
 }  // namespace hy

@@ -32,7 +32,7 @@ class he_param_req(ctypes.Structure):
 class he_param_info(ctypes.Structure):
     _fields_ = [("N", u32), ("L", u32), ("w", u32), ("l", u32), ("t", u64), ("zeta", u64), ("h", u64), ("k", u64),
                 ("kh", i64), ("log2_delta", ctypes.c_double), ("est_noise_log2", ctypes.c_double),
-                ("q", u64 * HE_MAX_LIMBS)]
+                ("q", u64 * HE_MAX_LIMBS), ("k4", u64)]
 
 
 class he_conv_desc(ctypes.Structure):

@@ -178,6 +178,33 @@ def test_mac_group_tiling_is_invisible(small, groups):
     small.layer(spec, mac_groups=groups)
 
 
+# ---------------------------------------------------------------- c_n = 4 (4 x 4 Walsh-Hadamard basis)
+CN4 = [
+    dict(C_in=5, C_out=7, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=4),    # ragged channels
+    dict(C_in=8, C_out=8, H=7, W=9, kh=3, stride=1, depthwise=True, n_images=3, c_n=4),     # depthwise
+    dict(C_in=8, C_out=12, H=9, W=10, kh=3, stride=2, depthwise=False, n_images=1, c_n=4),  # stride 2
+    dict(C_in=2, C_out=4, H=30, W=40, kh=3, stride=1, depthwise=False, n_images=1, c_n=4),  # strips, ragged tail
+    dict(C_in=6, C_out=4, H=5, W=5, kh=1, stride=1, depthwise=False, n_images=2, c_n=4),    # pointwise
+    dict(C_in=4, C_out=4, H=6, W=6, kh=5, stride=1, depthwise=False, n_images=1, c_n=4),    # 5x5
+    dict(C_in=20, C_out=18, H=5, W=5, kh=3, stride=1, depthwise=False, n_images=5, c_n=4),  # groups x images
+    dict(C_in=3, C_out=4, H=10, W=9, kh=3, stride=1, depthwise=False, n_images=2, c_n=4, tile_h=4, tile_w=5),
+]
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("spec", CN4)
+def test_cn4_layer_matches_oracle(small, spec, impl):
+    """c_n = 4 layers (the CUDA-core MAC with four rows per output group and the three pattern
+    PMults in its epilogue) word for word against the oracle, and decrypted against the convolution."""
+    small.layer(spec, mac_impl=impl)
+
+
+@pytest.mark.parametrize("groups", [1, 2, 4, 8])
+def test_cn4_mac_group_tiling_is_invisible(small, groups):
+    small.layer(dict(C_in=6, C_out=22, H=5, W=5, kh=3, stride=1, depthwise=False, n_images=2, c_n=4),
+                mac_groups=groups)
+
+
 # ---------------------------------------------------------------- the 16-channel layer, N = 4096
 def test_single_layer_16_channels():
     S = Setup(4096, 2, 25)
@@ -224,6 +251,15 @@ def test_resnet20_layer_matches_oracle(resnet, resnet_stack, li):
     dec = H.he_decrypt_image(resnet.p, resnet.sk, r["d"], out)
     sp = r["spec"]
     assert (dec == conv.conv_plain(r["act"], r["wt"], sp["stride"], 1, False, resnet.P.t)).all()
+
+
+@pytest.mark.parametrize("spec", [
+    dict(C_in=16, C_out=16, H=32, W=32, kh=3, stride=1, depthwise=False, n_images=1, c_n=4),
+    dict(C_in=32, C_out=64, H=16, W=16, kh=3, stride=2, depthwise=False, n_images=1, c_n=4),
+])
+def test_cn4_resnet20_shapes_match_oracle(resnet, spec):
+    """ResNet-20 layer shapes with c_n = 4 at N = 8192, L = 3: every output ciphertext."""
+    resnet.layer(spec)
 
 
 # ---------------------------------------------------------------- largest ring
@@ -411,9 +447,10 @@ def _plan_and_inputs(S, spec, label, mac_impl=0):
 
 
 def test_batch_equals_single_layers(small):
-    """One launch per stage over mixed layers (packed, unpacked, depthwise, 1x1, all three MAC kinds)."""
-    specs = [SMALL[0], SMALL[1], SMALL[2], SMALL[3], SMALL[7], SMALL[11], SMALL[5], SMALL[4], SMALL[8]]
-    impls = [0, 1, 0, 0, 2, 1, 0, 3, 3]
+    """One launch per stage over mixed layers (c_n 1, 2 and 4, depthwise, 1x1, all three MAC kinds)."""
+    specs = [SMALL[0], SMALL[1], SMALL[2], SMALL[3], SMALL[7], SMALL[11], SMALL[5], SMALL[4], SMALL[8], CN4[0], CN4[1],
+             CN4[6]]
+    impls = [0, 1, 0, 0, 2, 1, 0, 3, 3, 0, 1, 1]
     items = [_plan_and_inputs(small, sp, i, impl) for i, (sp, impl) in enumerate(zip(specs, impls))]
     plans = [it[0] for it in items]
     refs, d_ins, d_outs = [], [], []

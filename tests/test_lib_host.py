@@ -38,6 +38,7 @@ def test_params_match_oracle(N, L, w):
     P = prm.make_params(N=N, L=L, w=w)
     assert info.t == P.t and info.zeta == P.zeta and info.h == P.h % P.t and info.k == P.k
     assert info.kh == P.kh and info.l == P.l
+    assert info.k4 == conv.k4_select(P)
     assert [info.q[i] for i in range(L)] == P.q
     assert abs(info.log2_delta - np.log2(float(P.delta))) < 1e-6
     H.he_params_destroy(p)
@@ -117,6 +118,14 @@ LAYERS = [
     dict(C_in=3, C_out=4, H=10, W=9, kh=3, stride=1, depthwise=False, n_images=2, c_n=2, tile_h=4, tile_w=5),
     dict(C_in=2, C_out=2, H=30, W=40, kh=3, stride=1, depthwise=False, n_images=1, c_n=1, tile_h=7, tile_w=40),
     dict(C_in=4, C_out=4, H=12, W=13, kh=3, stride=2, depthwise=True, n_images=2, c_n=2, tile_h=6, tile_w=13),
+    # c_n = 4: N/4 positions per row, channel classes row x slot parity
+    dict(C_in=5, C_out=7, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=2, c_n=4),
+    dict(C_in=8, C_out=8, H=6, W=6, kh=3, stride=1, depthwise=False, n_images=3, c_n=4),
+    dict(C_in=8, C_out=8, H=7, W=9, kh=3, stride=2, depthwise=True, n_images=3, c_n=4),
+    dict(C_in=6, C_out=4, H=5, W=5, kh=1, stride=1, depthwise=False, n_images=2, c_n=4),
+    dict(C_in=2, C_out=4, H=30, W=40, kh=3, stride=1, depthwise=False, n_images=1, c_n=4),
+    dict(C_in=4, C_out=4, H=6, W=6, kh=5, stride=1, depthwise=False, n_images=1, c_n=4),
+    dict(C_in=3, C_out=4, H=10, W=9, kh=3, stride=1, depthwise=False, n_images=2, c_n=4, tile_h=4, tile_w=5),
 ]
 
 
@@ -164,6 +173,7 @@ def test_tile_override_rejected_like_the_oracle(tile, why):
     (dict(C_in=4, C_out=6, H=8, W=8, depthwise=True), "depthwise with C_in != C_out"),
     (dict(C_in=4, C_out=4, H=8, W=8, stride=3), "stride 3"),
     (dict(C_in=4, C_out=4, H=8, W=8, c_n=3), "c_n = 3"),
+    (dict(C_in=4, C_out=4, H=8, W=8, stride=2, c_n=4, polyphase=1), "polyphase with c_n = 4"),
     (dict(C_in=4, C_out=4, H=8, W=8, kh=9), "kernel 9"),
     (dict(C_in=0, C_out=4, H=8, W=8), "no input channels"),
     (dict(C_in=4, C_out=4, H=0, W=8), "empty image"),
@@ -176,6 +186,22 @@ def test_plan_checks_refuse_invalid_layers(desc, why):
     kh = desc.get("kh", 3)
     w = np.ones((max(1, desc["C_out"]), cw, kh, kh), dtype=np.int32)
     assert H.he_conv_check(p, d, w) == H.HE_EINVAL, why
+    H.he_params_destroy(p)
+
+
+def test_cn4_runs_on_the_cuda_core_mac_only():
+    """c_n = 4 plans take the CUDA-core MAC (auto or mac_impl 1); every other form is refused, and
+    mac_groups must be a power of two up to 16."""
+    p = H.he_params_create(1024, 2, decomp_bits=25)
+    d = H.conv_desc(C_in=8, C_out=8, H=6, W=6, kh=3, stride=1, n_images=1, c_n=4)
+    w = np.ones((8, 8, 3, 3), dtype=np.int32)
+    assert H.he_conv_check(p, d, w) == H.HE_OK
+    assert H.he_conv_check(p, d, w, mac_impl=1) == H.HE_OK
+    assert H.he_conv_check(p, d, w, mac_impl=1, mac_groups=8) == H.HE_OK
+    for impl in (2, 3, 4, 5, 6, 7, 8):
+        assert H.he_conv_check(p, d, w, mac_impl=impl) == H.HE_EINVAL, impl
+    for mg in (3, 6, 32):
+        assert H.he_conv_check(p, d, w, mac_groups=mg) == H.HE_EINVAL, mg
     H.he_params_destroy(p)
 
 

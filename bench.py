@@ -56,7 +56,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "network_samples.json")
 # (kernel_source_digest), per workload; reported as roofline traffic only while the kernels are unchanged
 PROFILED_TRAFFIC = {
     # profiles/vgg16_stack_batched_launches.md: the key-switch stage's 4 launches of one forward
-    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("11a1931d13bc8197", 41487433856),
+    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("326c3143f1cbf5c2", 41486645856),
 }
 
 

@@ -336,7 +336,9 @@ int he_batch_graph_launch(he_batch* b, const uint64_t* const* d_in, uint64_t* co
  * half its own graph, so that one half's copies overlap the other's kernels.
  * A batch of several waves runs its waves in order on `stream`, while the
  * inputs stream in ahead of them and a finished wave's outputs stream out
- * during the next wave, on two more streams the batch owns.  Outputs equal
+ * during the next wave, on two more streams the batch owns; the first wave's
+ * input NTTs run one layer at a time, each as soon as its own input has
+ * landed, so that only the first layer's copy is exposed.  Outputs equal
  * he_batch_forward's.  Host buffers: on a GB300 with many separately pinned
  * multi-GB buffers live at once, host-to-device copies from them ran at about
  * a quarter of the rate of buffers that are views of one pinned allocation. */

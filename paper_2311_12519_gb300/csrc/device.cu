@@ -2934,8 +2934,10 @@ void launch_stage(const he_params* p, const KP& kp, int stage, const std::vector
 
 // Runs the four stages over a list of layers.  Layers of one MAC variant share a launch.
 void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>& layers, cudaStream_t s, bool timed,
-                bool do_mac = true, const cudaEvent_t* marks = nullptr) {
+                bool do_mac = true, const cudaEvent_t* marks = nullptr, const cudaEvent_t* input_ready = nullptr) {
     // marks (optional): five events recorded at the stage boundaries
+    // input_ready (optional): one event per layer; the input NTTs then run layer by layer, each
+    // after its own event (its input's copy), so that they overlap the copies of the later inputs
     auto mark = [&](int i) {
         if (marks) CUDA_OK(cudaEventRecord(marks[i], s));
     };
@@ -2949,7 +2951,14 @@ void run_layers(const he_params* p, const KP& kp, const std::vector<StageLayer>&
     };
     {
         StageTimer t(HE_STAGE_NTT_IN, s, timed);
-        go(ST_NTT, all);
+        if (input_ready) {
+            for (size_t i = 0; i < layers.size(); i++) {
+                CUDA_OK(cudaStreamWaitEvent(s, input_ready[i], 0));
+                launch_stage<1>(p, kp, ST_NTT, {&layers[i]}, s);
+            }
+        } else {
+            go(ST_NTT, all);
+        }
     }
     mark(1);
     {
@@ -3569,11 +3578,13 @@ struct he_batch {
     cudaStream_t s2 = nullptr, s3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_done;  // per wave: inputs copied, kernels done
+    std::vector<cudaEvent_t> ev_first;        // per layer of the first wave: its input copied
     ~he_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         for (auto e : ev_in) cudaEventDestroy(e);
+        for (auto e : ev_first) cudaEventDestroy(e);
         for (auto e : ev_done) cudaEventDestroy(e);
         if (s2) cudaStreamDestroy(s2);
         if (s3) cudaStreamDestroy(s3);
@@ -3750,7 +3761,8 @@ extern "C" int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, u
         if (b->waves.size() > 1) {
             // waves run one after another on s (they share the workspace region); the inputs of
             // every wave stream in on s2 ahead of its kernels, the outputs of a finished wave leave
-            // on s3 while the next wave computes
+            // on s3 while the next wave computes.  The first wave's input NTTs run layer by layer as
+            // their inputs land, so that only the first layer's copy is exposed
             const size_t nw = b->waves.size();
             if (!b->s2) {
                 CUDA_OK(cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking));
@@ -3765,18 +3777,27 @@ extern "C" int he_batch_forward_host(he_batch* b, const uint64_t* const* h_in, u
                 CUDA_OK(cudaEventCreateWithFlags(&c, cudaEventDisableTiming));
                 b->ev_done.push_back(c);
             }
+            while (b->ev_first.size() < b->waves[0].size()) {
+                cudaEvent_t a;
+                CUDA_OK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+                b->ev_first.push_back(a);
+            }
             CUDA_OK(cudaEventRecord(b->ev_fork, s));
             CUDA_OK(cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
             CUDA_OK(cudaStreamWaitEvent(b->s3, b->ev_fork, 0));
             for (size_t w = 0; w < nw; w++) {
-                for (u32 i : b->waves[w])
+                for (size_t q = 0; q < b->waves[w].size(); q++) {
+                    const u32 i = b->waves[w][q];
                     CUDA_OK(cudaMemcpyAsync(d_in[i], h_in[i], b->plans[i]->lay.n_ct_in * ctw * 8, cudaMemcpyHostToDevice,
                                             b->s2));
+                    if (w == 0) CUDA_OK(cudaEventRecord(b->ev_first[q], b->s2));
+                }
                 CUDA_OK(cudaEventRecord(b->ev_in[w], b->s2));
             }
             for (size_t w = 0; w < nw; w++) {
-                CUDA_OK(cudaStreamWaitEvent(s, b->ev_in[w], 0));
-                run_layers(b->p, b->plans[0]->kp, b->layers(b->waves[w], d_in, d_out, (char*)d_ws), s, true);
+                if (w > 0) CUDA_OK(cudaStreamWaitEvent(s, b->ev_in[w], 0));
+                run_layers(b->p, b->plans[0]->kp, b->layers(b->waves[w], d_in, d_out, (char*)d_ws), s, true, true,
+                           nullptr, w == 0 ? b->ev_first.data() : nullptr);
                 CUDA_OK(cudaEventRecord(b->ev_done[w], s));
                 CUDA_OK(cudaStreamWaitEvent(b->s3, b->ev_done[w], 0));
                 for (u32 i : b->waves[w])

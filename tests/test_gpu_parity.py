@@ -498,6 +498,20 @@ def test_batch_equals_single_layers(small):
                             s.cuda_stream)
     for i in range(len(plans)):
         assert torch.equal(h_outs[i], refs[i].cpu()), f"layer {i} differs through the host path in waves"
+    # waves of several layers (the first wave's input NTTs run layer by layer behind its copies)
+    sizes = sorted((H.he_conv_sizes(pl)[2] + 255) // 256 * 256 for pl in plans)
+    b2 = H.he_batch_create_limited(plans, sizes[-1] + sizes[-2])  # the two largest share the first wave
+    assert 2 <= H.he_batch_waves(b2) < len(plans)
+    ws2 = torch.empty(H.he_batch_workspace_bytes(b2) // 8 + 1, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        for t in h_outs:
+            t.fill_(-1)
+        H.he_batch_forward_host(b2, [t.data_ptr() for t in h_ins], [t.data_ptr() for t in h_outs],
+                                [t.data_ptr() for t in d_ins], [t.data_ptr() for t in d_outs], ws2.data_ptr(),
+                                s.cuda_stream)
+        for i in range(len(plans)):
+            assert torch.equal(h_outs[i], refs[i].cpu()), f"layer {i} differs through the host path in multi-layer waves"
+    H.he_batch_destroy(b2)
     H.he_batch_destroy(b1)
     H.he_batch_destroy(b)
     for plan, gk, _ in items:

@@ -2,7 +2,9 @@
 
 Default workload: the 13 3x3 convolutions of VGG-16 on 8 images of 224x224
 per GPU, N = 16384, L = 4 RNS limbs of 50 bits, t = 786433, Hyena packing
-(c_n = 2): 6128 input and 8704 output ciphertexts per step.  A step runs all
+where it saves ciphertexts (c_n = 2 for the 28x28 and 14x14 layers; the 224 to
+56 layers, whose tiles fill the slot rows, unpacked with c_n = 1; --packing 2
+packs all): 6100 input and 8704 output ciphertexts per step.  A step runs all
 13 layers once on synthetic ciphertexts resident in HBM.  value = layers/s
 over all ranks of the batched form (one launch per stage for all layers of a
 workspace wave, replayed as a CUDA graph); the plain per-layer form
@@ -54,9 +56,12 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "network_samples.json")
 # DRAM bytes (read + write) of one launch of each kernel of the batched step, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source with this digest prefix
 # (kernel_source_digest), per workload; reported as roofline traffic only while the kernels are unchanged
+# keyed by the line's full workload description (packing and layer choices included)
 PROFILED_TRAFFIC = {
-    # profiles/vgg16_stack_batched_launches.md: the key-switch stage's 4 launches of one forward
-    ("vgg16", "k_keyswitch + k_keyswitch_img"): ("326c3143f1cbf5c2", 41486645856),
+    # profiles/vgg16_stack_batched_launches.md (every layer packed, --packing 2): the key-switch
+    # stage's 4 launches of one forward
+    ("vgg16-3x3-stack (13 convs), 224x224, 8 images/GPU, N=16384, L=4x50-bit, t=786433, c_n=2",
+     "k_keyswitch + k_keyswitch_img"): ("326c3143f1cbf5c2", 41486645856),
 }
 
 
@@ -80,22 +85,48 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def layer_specs(workload, layers=None, polyphase=False):
+def layer_specs(workload, layers=None, polyphase=False, dw_cn4=False):
     """The stack's layer descriptions (all, or the listed layer indices), ring and images; with
-    `polyphase`, its 3x3 stride-2 layers use polyphase packing."""
+    `polyphase`, its 3x3 stride-2 layers use polyphase packing; with `dw_cn4`, its other depthwise
+    layers pack four channels per ciphertext."""
     shapes, N, L, images = synth.STACKS[workload]
     idx = range(len(shapes())) if layers is None else layers
-    return [synth.stack_layer(workload, i, polyphase) for i in idx], N, L, images
+    return [synth.stack_layer(workload, i, polyphase, dw_cn4) for i in idx], N, L, images
+
+
+# c_n of the stack layers: "2" packs every layer (the pair of Eq. 1); "fill" packs a layer only
+# where packing saves ciphertexts (fill_packing)
+PACKING_DESC = {"2": "c_n=2", "fill": "c_n per layer (1 where its tiles fill the slot rows, else 2)"}
+
+
+def workload_name(wl, packing):
+    return WORKLOADS[wl][1].replace("c_n=2", PACKING_DESC[packing])
+
+
+def fill_packing(specs, counts):
+    """c_n per layer.  The paper packs c_n = n / n_i channels only while an image leaves slots
+    empty (Sec. 3.1) and runs its large inputs unpacked (Sec. 4); with many tiles per ciphertext
+    the same holds per layer: a layer whose tiles fill the slot rows gets c_n = 1 (no more input
+    and output ciphertexts than the pair, half its Hadamard rows and no row-swap rotations), the
+    others keep c_n = 2.  `counts(spec)` gives (n_ct_in, n_ct_out) of a layer description."""
+    out = []
+    for s in specs:
+        if s["c_n"] == 2:
+            a, b = counts(dict(s, c_n=1)), counts(s)
+            if a[0] <= b[0] and a[1] <= b[1]:
+                s = dict(s, c_n=1)
+        out.append(s)
+    return out
 
 
 def layer_counts(spec, lay, L, l, N):
     """Algorithmic counts of one layer (one image batch): conv and key-switch modMACs, and the
     bytes of Sec. 8(d)'s rooflines for each stage."""
-    packed = spec["c_n"] == 2
+    rows = spec["c_n"]  # MAC rows per output group: 1, 2 or 4
     n_rot = lay.n_galois + 1  # the rotated copies of an input ciphertext, identity included
     # a depthwise output reads one ciphertext per phase plane (four with polyphase packing)
     K = (lay.in_groups // lay.out_groups) * n_rot if spec["depthwise"] else lay.in_groups * n_rot
-    conv = lay.row_units * lay.out_groups * (2 if packed else 1) * K * 2 * L * N
+    conv = lay.row_units * lay.out_groups * rows * K * 2 * L * N
     ks = lay.n_ct_in * lay.n_galois * 2 * L * l * L * N
     w8 = N * 8
     return {
@@ -194,7 +225,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) sample
-def oracle_layer_estimate(workload, i, threads, keys_cache):
+def oracle_layer_estimate(workload, i, threads, keys_cache, packing="2"):
     """Seconds the CPU oracle (oracle/conv.he_conv on `threads` host threads) needs for layer i of
     the stack, from a bounded sample: the layer with its input channels cut to `threads` channel
     groups (same ring, kernel, images and output channels), of which `threads` output ciphertexts
@@ -212,6 +243,8 @@ def oracle_layer_estimate(workload, i, threads, keys_cache):
         keys_cache[(N, L)] = (P, bfv.keygen(P, synth.SEED_KEYS), {})
     P, s, ksk = keys_cache[(N, L)]
     sp = synth.stack_layer(workload, i)
+    if packing == "fill":
+        sp = fill_packing([sp], lambda x: (lambda o: (o.n_ct_in, o.n_ct_out))(conv.Layout(N=N, **x)))[0]
     lay = conv.Layout(N=N, **sp)
     groups = min(threads, lay.in_groups)
     sub = dict(sp, C_in=min(sp["C_in"], 2 * groups))
@@ -238,11 +271,11 @@ def oracle_layer_estimate(workload, i, threads, keys_cache):
     return est, tm["rotations"] + tm["sums"], {"layer": i, "input_cts": rot_in, "output_cts": n_out, "terms": k_s}
 
 
-def oracle_sample(workload, layers, threads):
+def oracle_sample(workload, layers, threads, packing="2"):
     """Estimated oracle seconds for each sampled layer, wall seconds spent, and a description."""
     cache, est, spent, parts = {}, [], 0.0, []
     for i in layers:
-        e, w, info = oracle_layer_estimate(workload, i, threads, cache)
+        e, w, info = oracle_layer_estimate(workload, i, threads, cache, packing)
         est.append(e)
         spent += w
         parts.append(info)
@@ -265,7 +298,7 @@ def run_reference(args, rank):
     cache, est = {}, []
     t0 = time.perf_counter()
     for st in range(warm + steps):
-        e, _, _ = oracle_layer_estimate(wl, st % n_layers, threads, cache)
+        e, _, _ = oracle_layer_estimate(wl, st % n_layers, threads, cache, args.packing)
         if st >= warm:
             est.append(e)
     wall = time.perf_counter() - t0
@@ -276,7 +309,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": 1000 * sum(est) / len(est), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[wl][1]},
+            "config": {"workload": workload_name(wl, args.packing)},
             "wall_seconds": round(wall, 1),
             "cpu_baseline": {"value": value, "unit": "layers/s", "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -301,17 +334,22 @@ def verify_outputs(H, p, sk, info, workload, specs, descs, d_outs, rank, index):
         golden = None
     try:
         poly = {r["layer"]: r for r in json.load(open(GOLDEN)).get(workload + "-polyphase", {}).get("samples", [])}
+        dwcn4 = {r["layer"]: r for r in json.load(open(GOLDEN)).get(workload + "-dwcn4", {}).get("samples", [])}
+        cn1 = {r["layer"]: r for r in json.load(open(GOLDEN)).get(workload + "-cn1", {}).get("samples", [])}
     except OSError:
-        poly = {}
+        poly, dwcn4, cn1 = {}, {}, {}
     if golden and (golden["N"], golden["L"]) == (N, L):
         ok, bad, skipped = 0, [], []
         for i, li in enumerate(index):
             row = golden["samples"][li]
-            if specs[i].get("polyphase"):
-                if li not in poly:
+            alt = poly if specs[i].get("polyphase") else {4: dwcn4, 1: cn1}.get(specs[i]["c_n"])
+            if specs[i].get("polyphase") and specs[i]["c_n"] != 2:
+                alt = {}  # phase planes without the pair: no stored sample
+            if alt is not None:
+                if li not in alt:
                     skipped.append(li)
                     continue
-                row = poly[li]
+                row = alt[li]
             c = row["ct"]
             words = d_outs[i][c * ctw:(c + 1) * ctw].cpu().numpy().view(np.uint64)
             if hashlib.sha256(np.ascontiguousarray(words, dtype="<u8").tobytes()).hexdigest() == row["sha256"]:
@@ -409,18 +447,22 @@ def run_gpu(args, rank, world):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     wl = args.workload
-    ws_limit, workload = WORKLOADS[wl]
-    specs, n_ring, n_limbs, images = layer_specs(wl, args.layers, args.polyphase)
+    ws_limit, workload = WORKLOADS[wl][0], workload_name(wl, args.packing)
+    specs, n_ring, n_limbs, images = layer_specs(wl, args.layers, args.polyphase, args.dw_cn4)
     index = list(range(len(specs))) if args.layers is None else list(args.layers)
     if args.layers is not None:
         workload += f", layers {index} only"
     if args.polyphase:
         workload += ", 3x3 stride-2 layers with polyphase packing"
+    if args.dw_cn4:
+        workload += ", depthwise layers" + (" not so packed" if args.polyphase else "") + " with c_n=4"
     t_setup = time.perf_counter()
     p = H.he_params_create(n_ring, n_limbs, limb_bits=LIMB_BITS, decomp_bits=50)
     info = H.he_params_info(p)
     N, L, l = info.N, info.L, info.l
     sk = H.he_keygen(p, synth.SEED_KEYS)
+    if args.packing == "fill":
+        specs = fill_packing(specs, lambda x: (lambda o: (o.n_ct_in, o.n_ct_out))(H.he_layout_for_layer(p, H.conv_desc(**x))))
     tunes = [{} for _ in specs]
     if args.mac_impl or args.tc_cluster:
         # a forced MAC form or cluster size where the layer admits it (depthwise layers take no
@@ -601,7 +643,7 @@ def run_gpu(args, rank, world):
     top = max((k for k in stages_b if roofs[k]), key=lambda k: stages_b[k][0])
     roof = {k: v for k, v in roofs[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
     src = kernel_source_digest().hexdigest()
-    prof = PROFILED_TRAFFIC.get((wl, kname[top]))
+    prof = PROFILED_TRAFFIC.get((workload, kname[top]))
     roof["traffic"] = prof[1] if prof and src.startswith(prof[0]) else None
     roof.update(kernel=kname[top], per_launch="one launch per stage and wave; achieved = algorithmic units of the "
                 "step / the kernel's event-timed time in the step",
@@ -613,7 +655,7 @@ def run_gpu(args, rank, world):
     if world == 1 and not args.no_cpu_baseline:
         layers = sorted({index[min(1, len(index) - 1)], index[-1]})
         threads = host_cores()
-        est, spent, desc, parts = oracle_sample(wl, layers, threads)
+        est, spent, desc, parts = oracle_sample(wl, layers, threads, args.packing)
         # every layer of these stacks costs the oracle per input ciphertext and per term alike
         # (one ring, one rotation set per kernel size), so the sampled layers' unit costs give the
         # stack's layers/s over its own layer mix
@@ -883,7 +925,7 @@ def run_forms(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    specs, N, L, images = layer_specs(args.workload, args.layers, args.polyphase)
+    specs, N, L, images = layer_specs(args.workload, args.layers, args.polyphase, args.dw_cn4)
     index = list(range(len(specs))) if args.layers is None else list(args.layers)
     p = H.he_params_create(N, L, limb_bits=LIMB_BITS, decomp_bits=50)
     for i, s in zip(index, specs):
@@ -913,6 +955,12 @@ def main():
                          "(32 images) stack")
     ap.add_argument("--polyphase", action="store_true",
                     help="pack the 3x3 stride-2 layers' inputs as phase planes (stride-1 layers on them)")
+    ap.add_argument("--packing", default="fill", choices=["fill", "2"],
+                    help="c_n of the stack layers: 'fill' packs a layer (c_n = 2) only where its tiles leave "
+                         "slot rows empty and runs the others unpacked (c_n = 1); '2' packs every layer")
+    ap.add_argument("--dw-cn4", action="store_true",
+                    help="pack the depthwise layers (those not packed as phase planes) four channels per "
+                         "ciphertext (c_n = 4)")
     ap.add_argument("--tc-cluster", type=int, default=0,
                     help="run the image-form MAC of layers wider than one row tile in clusters of this many CTAs")
     ap.add_argument("--mac-impl", type=int, default=0,

@@ -118,15 +118,18 @@ STACKS = {
 }
 
 
-def stack_layer(stack: str, i: int, polyphase: bool = False) -> dict:
+def stack_layer(stack: str, i: int, polyphase: bool = False, dw_cn4: bool = False) -> dict:
     """Layer i of a stack as a layer description (3x3 or 1x1, Hyena packing c_n = 2); with
-    `polyphase`, a 3x3 stride-2 layer is marked for polyphase packing."""
+    `polyphase`, a 3x3 stride-2 layer is marked for polyphase packing; with `dw_cn4`, a depthwise
+    layer not so marked packs four channels per ciphertext (c_n = 4)."""
     shapes, _, _, images = STACKS[stack]
     s = shapes()[i]
     d = dict(C_in=s.C_in, C_out=s.C_out, H=s.H, W=s.W, kh=s.k, stride=s.stride, depthwise=s.depthwise,
              n_images=images, c_n=2)
     if polyphase and s.stride == 2 and s.k == 3:
         d["polyphase"] = 1
+    elif dw_cn4 and s.depthwise:
+        d["c_n"] = 4
     return d
 
 

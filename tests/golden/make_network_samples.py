@@ -13,8 +13,11 @@ A deep layer's output ciphertext depends on all input ciphertexts of its row-uni
 here, each rotated 17 times), which takes the oracle minutes per layer even on all cores; the
 stored digests let the GPU tests compare every layer's sample word for word in seconds.
 
-Usage: python tests/golden/make_network_samples.py [--stacks vgg16,mobilenet] [--polyphase]
-(--polyphase: the 3x3 stride-2 layers only, with polyphase packing, as entries '<stack>-polyphase').
+Usage: python tests/golden/make_network_samples.py [--stacks vgg16,mobilenet] [--polyphase | --dw-cn4 | --cn1]
+(--polyphase: the 3x3 stride-2 layers only, with polyphase packing, as entries '<stack>-polyphase';
+--dw-cn4: the depthwise layers only, packed four channels per ciphertext, as '<stack>-dwcn4';
+--cn1: the layers whose tiles fill the slot rows, unpacked (c_n = 1: no more input or output
+ciphertexts than with c_n = 2), as '<stack>-cn1').
 """
 from __future__ import annotations
 
@@ -42,8 +45,19 @@ def digest(ct: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(ct, dtype="<u8").tobytes()).hexdigest()
 
 
-def sample_layer(P, s, ksk, stack, i, polyphase=False):
-    sp = synth.stack_layer(stack, i, polyphase)
+def fills_rows(N, sp):
+    """True if the layer packed one channel per ciphertext (c_n = 1) needs no more input and output
+    ciphertexts than with c_n = 2: its tiles already fill the slot rows, so packing would only add
+    Hadamard rows and row-swap rotations (the paper packs only when an image leaves slots empty)."""
+    a = conv.Layout(N=N, **dict(sp, c_n=1))
+    b = conv.Layout(N=N, **dict(sp, c_n=2))
+    return a.n_ct_in <= b.n_ct_in and a.n_ct_out <= b.n_ct_out
+
+
+def sample_layer(P, s, ksk, stack, i, polyphase=False, dw_cn4=False, c_n=None):
+    sp = synth.stack_layer(stack, i, polyphase, dw_cn4)
+    if c_n is not None:
+        sp["c_n"] = c_n
     act, wt, enc_seed = synth.stack_inputs(stack, i, P.t)
     poly = sp.get("polyphase", 0)
     if poly:
@@ -80,6 +94,10 @@ def main():
     ap.add_argument("--stacks", default="vgg16,mobilenet")
     ap.add_argument("--polyphase", action="store_true",
                     help="sample the 3x3 stride-2 layers with polyphase packing (entries '<stack>-polyphase')")
+    ap.add_argument("--dw-cn4", action="store_true",
+                    help="sample the depthwise layers packed with c_n = 4 (entries '<stack>-dwcn4')")
+    ap.add_argument("--cn1", action="store_true",
+                    help="sample the layers whose tiles fill the rows, with c_n = 1 (entries '<stack>-cn1')")
     args = ap.parse_args()
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for stack in args.stacks.split(","):
@@ -91,10 +109,14 @@ def main():
         for i, sh in enumerate(shapes()):
             if args.polyphase and not (sh.stride == 2 and sh.k == 3):
                 continue
+            if args.dw_cn4 and not sh.depthwise:
+                continue
+            if args.cn1 and not fills_rows(N, synth.stack_layer(stack, i)):
+                continue
             t0 = time.time()
-            rows.append(sample_layer(P, s, ksk, stack, i, args.polyphase))
+            rows.append(sample_layer(P, s, ksk, stack, i, args.polyphase, args.dw_cn4, 1 if args.cn1 else None))
             print(f"{stack} layer {i}: ct {rows[-1]['ct']} in {time.time() - t0:.0f} s", flush=True)
-        key = stack + ("-polyphase" if args.polyphase else "")
+        key = stack + ("-polyphase" if args.polyphase else "-dwcn4" if args.dw_cn4 else "-cn1" if args.cn1 else "")
         data[key] = {"N": N, "L": L, "w": 50, "images": images, "seeds": "keys 1, encryption 2 + layer, "
                      "activations label = layer, weights label = layer", "samples": rows}
         with open(OUT, "w") as f:

@@ -293,3 +293,25 @@ def test_polyphase_layout_and_encryption_match_the_oracle_derived_layer(spec):
     with pytest.raises(H.HyenaError):
         H.he_layout_for_layer(p, H.conv_desc(**dict(spec, stride=1)))
     H.he_params_destroy(p)
+
+
+def test_fill_packing_agrees_between_library_and_oracle_layouts():
+    """bench.py's per-layer packing rule (c_n = 1 where the tiles fill the slot rows) gives the
+    same choice on the library's layouts as the stored-sample generator's copy on the oracle's."""
+    import importlib.util
+    import os
+
+    import bench
+    import synth
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("mns", os.path.join(here, "golden", "make_network_samples.py"))
+    mns = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mns)
+    for wl in ("vgg16", "mobilenet", "resnet20"):
+        specs, N, L, _ = bench.layer_specs(wl)
+        p = H.he_params_create(N, L, limb_bits=bench.LIMB_BITS, decomp_bits=50)
+        lib = bench.fill_packing(specs, lambda x: (lambda o: (o.n_ct_in, o.n_ct_out))(
+            H.he_layout_for_layer(p, H.conv_desc(**x))))
+        ora = [1 if mns.fills_rows(N, s) else 2 for s in specs]
+        assert [s["c_n"] for s in lib] == ora, wl
+        H.he_params_destroy(p)

@@ -315,3 +315,26 @@ def test_fill_packing_agrees_between_library_and_oracle_layouts():
         ora = [1 if mns.fills_rows(N, s) else 2 for s in specs]
         assert [s["c_n"] for s in lib] == ora, wl
         H.he_params_destroy(p)
+
+
+def test_stored_samples_cover_the_per_layer_packing():
+    """Every layer the default packing runs unpacked has a stored oracle sample ('<stack>-cn1')
+    whose output ciphertext count is the library's for that layout, and every packed layer has
+    one in the stack's own entry: the bench can check each layer of its default line."""
+    import json
+    import os
+
+    import bench
+    golden = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                         "network_samples.json")))
+    for wl in ("vgg16", "mobilenet"):
+        specs, N, L, _ = bench.layer_specs(wl)
+        p = H.he_params_create(N, L, limb_bits=bench.LIMB_BITS, decomp_bits=50)
+        filled = bench.fill_packing(specs, lambda x: (lambda o: (o.n_ct_in, o.n_ct_out))(
+            H.he_layout_for_layer(p, H.conv_desc(**x))))
+        cn1 = {r["layer"]: r for r in golden[wl + "-cn1"]["samples"]}
+        packed = {r["layer"]: r for r in golden[wl]["samples"]}
+        for i, s in enumerate(filled):
+            row = cn1[i] if s["c_n"] == 1 else packed[i]
+            assert row["n_ct_out"] == H.he_layout_for_layer(p, H.conv_desc(**s)).n_ct_out, (wl, i)
+        H.he_params_destroy(p)

@@ -247,7 +247,7 @@ def oracle_layer_estimate(workload, i, threads, keys_cache, packing="2"):
         sp = fill_packing([sp], lambda x: (lambda o: (o.n_ct_in, o.n_ct_out))(conv.Layout(N=N, **x)))[0]
     lay = conv.Layout(N=N, **sp)
     groups = min(threads, lay.in_groups)
-    sub = dict(sp, C_in=min(sp["C_in"], 2 * groups))
+    sub = dict(sp, C_in=min(sp["C_in"], sp["c_n"] * groups))
     if sp["depthwise"]:
         sub["C_out"] = sub["C_in"]
     lay_s = conv.Layout(N=N, **sub)
